@@ -1,0 +1,325 @@
+"""Benchmark of the GB300 FMM hot path: one JSON line on stdout.
+
+A step is one whole pass of the hot path on one batch of synthetic bodies:
+fmm_build (bounding cube, keys, sort, octree, dual traversal, lists,
+operators), fmm_evaluate (P2M, M2M, M2L, L2L, P2P, L2P: potential + force)
+and fmm_backward (adjoint of sum w_i phi_i), with the inputs resident in HBM.
+`value` is particles per second over the whole job (all ranks); `e2e` is
+the same through fmm_solve_host with pinned host buffers (copies included).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
+  python bench.py --impl reference ...   # the double-precision CPU oracle
+
+With N > 1 (torchrun) every rank runs an independent replica (the method is
+not sharded across GPUs); the time is the maximum over ranks.
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "FMM particles/sec (pot+force) at N=1M, rel-L2 err vs FP64 direct; P2P % FP32 peak"
+UNIT = "particles/s"
+L2_FLUSH_BYTES = 512 << 20  # > 129 MB L2
+CPU_SAMPLE_N = 65536
+
+
+# ------------------------------------------------------------------ helpers
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", str(rank)))
+    return rank, world, local
+
+
+def reduce_max(x: float, device) -> float:
+    """Maximum of a host float over all ranks (identity without a process group)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate(n_per_rank: int, steps: int, world: int, max_seconds: float) -> float:
+    """Whole-job throughput: all ranks' particles over the slowest rank's time."""
+    return n_per_rank * steps * world / max_seconds
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason samples during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.lines = []
+        self.t = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+            return
+        self.t = threading.Thread(target=self._read, daemon=True)
+        self.t.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.t:
+            self.t.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        return json.load(open(path))
+    except (OSError, ValueError):
+        return {}
+
+
+# --------------------------------------------------------------- GPU arm
+
+def run_gpu(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+    from paper_1405_7487_gb300 import build_lib
+    if rank == 0:
+        build_lib.build()
+    if world > 1:
+        dist.barrier()
+    from paper_1405_7487_gb300 import fmm as F
+    from paper_1405_7487_gb300 import workloads as W
+
+    spec = W.WORKLOADS[args.workload]
+    p, theta, ncrit = spec["p"], spec["theta"], spec["ncrit"]
+    x_h = W.make(args.workload, n=args.n)
+    N = x_h.shape[0]
+    w_h = W.weights(N, spec.get("wseed", 40))
+    x = torch.from_numpy(x_h).to(dev)
+    w = torch.from_numpy(w_h).to(dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        T = F.Tree(x, p, theta, ncrit, F.FMM_FLAG_TIMING)
+        pot, force = T.evaluate()
+        dq, dx = T.backward(w)
+        st = T.stats()
+        T.close()
+        return st, pot, force
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize(dev)
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    step_ms, m2l_ms, p2p_ms, stats = [], [], [], None
+    launches0 = F.launch_count()
+    for _ in range(args.steps):
+        flush.zero_()  # L2 flush between timed steps (not timed)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        stats, pot, force = step()
+        e1.record(stream)
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        m2l_ms.append(stats["ms"]["m2l"])
+        p2p_ms.append(stats["ms"]["p2p"])
+    torch.cuda.synchronize(dev)
+    if world > 1:
+        dist.barrier()
+    launches = F.launch_count() - launches0
+    clk = clocks.stop()
+    total_s = sum(step_ms) / 1e3
+    max_s = reduce_max(total_s, dev)
+    value = aggregate(N, args.steps, world, max_s)
+
+    # accuracy against the double direct sum on 4096 sampled targets
+    idx = torch.from_numpy(W.sample_targets(N, 4096)).to(dev)
+    pd, fd = F.direct_f64(x, idx)
+    ii = idx.long()
+    err_pot = float(torch.linalg.norm(pot[ii].double() - pd) / torch.linalg.norm(pd))
+    err_force = float(torch.linalg.norm(force[ii].double() - fd) / torch.linalg.norm(fd))
+
+    # end to end through host buffers (pinned), copies inside the timed region
+    xh = torch.from_numpy(x_h).pin_memory().numpy()
+    wh = torch.from_numpy(w_h).pin_memory().numpy()
+    F.solve_host(xh, wh, p, theta, ncrit)
+    if world > 1:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        F.solve_host(xh, wh, p, theta, ncrit)
+    e2e_s = reduce_max(time.perf_counter() - t0, dev)
+    e2e = {"value": aggregate(N, args.steps, world, e2e_s), "unit": UNIT,
+           "h2d_bytes_per_step": int(x_h.nbytes + w_h.nbytes),
+           "d2h_bytes_per_step": int(N * 4 + N * 12 + N * 4 + N * 12)}
+
+    # roofline of the dominant kernel (both are FP32 ALU bound)
+    props = torch.cuda.get_device_properties(dev)
+    sm_mhz = clk["sm_mhz"] or measured_peaks().get("sm_max_mhz", 2070.0)
+    fp32_peak_tflops = props.multi_processor_count * 128 * 2 * sm_mhz * 1e6 / 1e12
+    m2l_avg = statistics.mean(m2l_ms)
+    p2p_avg = statistics.mean(p2p_ms)
+    K = stats["K"]
+    p2p_flops = 20.0 * stats["n_p2p_body_pairs"]
+    m2l_flops = 2.0 * K * K * stats["n_m2l"]
+    p2p_tf = p2p_flops / (p2p_avg * 1e-3) / 1e12
+    m2l_tf = m2l_flops / (m2l_avg * 1e-3) / 1e12
+    if m2l_avg >= p2p_avg:
+        dom = {"kernel": "k_m2l_cc", "bound": "alu", "achieved": m2l_tf, "ms": m2l_avg}
+    else:
+        dom = {"kernel": "k_p2p", "bound": "alu", "achieved": p2p_tf, "ms": p2p_avg}
+    roofline = {"bound": dom["bound"], "kernel": dom["kernel"], "achieved": round(dom["achieved"], 3),
+                "peak": round(fp32_peak_tflops, 3), "unit": "TFLOP/s",
+                "frac": round(dom["achieved"] / fp32_peak_tflops, 4), "traffic": None,
+                "peak_source": "FP32 spec formula SMs x 128 lanes x 2 x median SM clock under load",
+                "avg_launch_ms": round(dom["ms"], 4)}
+
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": max_s * 1e3 / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": args.workload, "distribution": spec["dist"], "N": N, "p": p, "theta": theta,
+                   "ncrit": ncrit, "step": "fmm_build + fmm_evaluate (pot, force) + fmm_backward",
+                   "l2": "flushed between timed steps (512 MiB write)", "parallelism": f"replicas x{world}"},
+        "e2e": e2e, "gpu_launches": int(launches), "roofline": roofline,
+        "p2p_frac_fp32_peak": round(p2p_tf / fp32_peak_tflops, 4),
+        "m2l_tflops": round(m2l_tf, 3), "p2p_tflops": round(p2p_tf, 3),
+        "err_vs_direct": {"pot": err_pot, "force": err_force, "targets": 4096},
+        "phase_ms": {k: round(v, 4) for k, v in stats["ms"].items()},
+        "tree": {k: stats[k] for k in ("n_cells", "n_leaves", "n_levels", "n_m2l", "n_p2p_body_pairs",
+                                       "n_m2l_classes", "m2l_engine")},
+        "clocks": clk,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(args.workload, steps=1)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+# ---------------------------------------------------------- oracle (CPU)
+
+def cpu_baseline(workload: str, steps: int) -> dict:
+    """The double-precision oracle, as it stands, on the host cores: a bounded
+    sample (the first CPU_SAMPLE_N bodies of the same workload, same p, theta,
+    ncrit); each step = oracle build + forward + backward."""
+    import numpy as np
+
+    import oracle
+    from paper_1405_7487_gb300 import workloads as W
+    spec = W.WORKLOADS[workload]
+    oracle.build()
+    cores = oracle.set_threads(0)
+    x = W.make(workload)[:CPU_SAMPLE_N]
+    w = W.weights(x.shape[0], spec.get("wseed", 40)).astype(np.float64)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        T = oracle.OracleTree(x, spec["p"], spec["theta"], spec["ncrit"])
+        T.backward(w)  # evaluates with q (forward) and with w (adjoint)
+        del T
+    dt = time.perf_counter() - t0
+    return {"value": x.shape[0] * steps / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"first {x.shape[0]} bodies of {workload}, same p/theta/ncrit; "
+                      f"build + forward + backward, {steps} step(s), {dt:.2f} s"}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    from paper_1405_7487_gb300 import workloads as W
+    spec = W.WORKLOADS[args.workload]
+    for _ in range(args.warmup):
+        cpu_baseline(args.workload, 1)
+    cb = cpu_baseline(args.workload, args.steps)
+    out = {"metric": METRIC, "value": cb["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": CPU_SAMPLE_N / cb["value"] * 1e3, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+           "config": {"workload": args.workload, "distribution": spec["dist"], "N": CPU_SAMPLE_N,
+                      "p": spec["p"], "theta": spec["theta"], "ncrit": spec["ncrit"],
+                      "step": "oracle build + forward + backward"},
+           "cpu_baseline": cb,
+           "e2e": {"value": cb["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gbfmm", choices=["gbfmm", "reference"])
+    ap.add_argument("--workload", default="cube1m_p10")
+    ap.add_argument("--n", type=int, default=None, help="bodies (default: the workload's size)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,433 @@
+// api.cu -- the C ABI (gbfmm.h): argument checks, the tree handle, and the
+// order of the passes of one evaluation (Sec. II.A / II.C: upward pass
+// P2M -> M2M, then M2L, downward pass L2L -> L2P; P2P alongside).
+#include <cmath>
+#include <cstring>
+#include <new>
+
+#include "kernels.cuh"
+
+using namespace gbfmm;
+
+namespace {
+
+int to_code(const Error& e) { return e.code; }
+
+void release_tree(fmm_tree* t) {
+  if (!t) return;
+  if (t->side) {
+    cudaStreamSynchronize(t->side);
+    cudaStreamDestroy(t->side);
+  }
+  if (t->fork) cudaEventDestroy(t->fork);
+  if (t->join) cudaEventDestroy(t->join);
+  for (auto& e : t->ev)
+    if (e) cudaEventDestroy(e);
+  t->arena.release_all();
+  cudaStreamSynchronize(t->stream);
+  cudaGetLastError();
+  delete t;
+}
+
+template <class R>
+void create_tree(fmm_tree* t, const R* xyzq) {
+  const bool f64 = sizeof(R) == 8;
+  t->precision = f64 ? 64 : 32;
+  t->K = t->p * t->p;
+  t->Kp = (t->K + 15) / 16 * 16;
+  t->m2l_engine = 0;
+  GB_CK(cudaStreamCreateWithFlags(&t->side, cudaStreamNonBlocking));
+  GB_CK(cudaEventCreateWithFlags(&t->fork, cudaEventDisableTiming));
+  GB_CK(cudaEventCreateWithFlags(&t->join, cudaEventDisableTiming));
+  if (t->flags & FMM_FLAG_TIMING)
+    for (auto& e : t->ev) GB_CK(cudaEventCreate(&e));
+  Arena& a = t->arena;
+  cudaStream_t s = t->stream;
+  if (t->flags & FMM_FLAG_TIMING) GB_CK(cudaEventRecord(t->ev[2 * FMM_PH_BUILD_TOTAL], s));
+  build_tree(t, xyzq, f64);
+  build_lists(t);
+  build_m2l_plan(t);
+  build_operators(t);
+  const size_t rs = sizeof(R);
+  t->M = a.alloc(rs * (size_t)t->ncell * t->Kp);
+  t->L = a.alloc(rs * (size_t)t->ncell * t->Kp);
+  GB_CK(cudaMemsetAsync(t->M, 0, rs * (size_t)t->ncell * t->Kp, s));
+  t->near = a.alloc(rs * 4 * (size_t)t->N);
+  t->grad_q = a.alloc(rs * 4 * (size_t)t->N);
+  t->q_last = a.alloc(rs * (size_t)t->N);
+  t->check_rec = alloc_n<unsigned long long>(a, 4);
+  GB_CK(cudaMemsetAsync(t->check_rec, 0, 4 * sizeof(unsigned long long), s));
+  t->lim = Lim{t->N, t->ncell, t->nleaf, t->Kp, t->ntile, t->nentry, t->nclass, t->n_p2p_ranges, t->check_rec};
+  if (t->flags & FMM_FLAG_TIMING) GB_CK(cudaEventRecord(t->ev[2 * FMM_PH_BUILD_TOTAL + 1], s));
+  GB_CK(cudaStreamSynchronize(s));
+  if (t->flags & FMM_FLAG_TIMING)
+    cudaEventElapsedTime(&t->ms[FMM_PH_BUILD_TOTAL], t->ev[2 * FMM_PH_BUILD_TOTAL],
+                         t->ev[2 * FMM_PH_BUILD_TOTAL + 1]);
+}
+
+template <class R>
+int build_common(const R* xyzq, int64_t n, int p, double theta, int ncrit, uint32_t flags,
+                 const fmm_allocator* alloc, fmm_stream stream, fmm_tree** out) {
+  if (out) *out = nullptr;
+  if (!xyzq || !out || n < 1 || n > 0x7fffffffll || p < 1 || p > kMaxP || !(theta > 0.0) ||
+      !(theta < 1.0) || ncrit < 1)
+    return FMM_ERR_ARG;
+  if (alloc && (!alloc->alloc || !alloc->free)) return FMM_ERR_ARG;
+  fmm_tree* t = new (std::nothrow) fmm_tree();
+  if (!t) return FMM_ERR_OOM;
+  t->N = n;
+  t->p = p;
+  t->theta = theta;
+  t->ncrit = ncrit;
+  t->flags = flags;
+  t->stream = (cudaStream_t)stream;
+  t->arena.stream = t->stream;
+  if (alloc) {
+    t->arena.user = *alloc;
+    t->arena.has_user = true;
+  }
+  try {
+    create_tree<R>(t, xyzq);
+  } catch (const Error& e) {
+    release_tree(t);
+    return to_code(e);
+  } catch (const std::bad_alloc&) {
+    release_tree(t);
+    return FMM_ERR_OOM;
+  }
+  *out = t;
+  return FMM_OK;
+}
+
+struct PhaseTimer {
+  fmm_tree* t;
+  cudaStream_t s;
+  bool on;
+  void begin(int ph) {
+    if (on) cudaEventRecord(t->ev[2 * ph], s);
+  }
+  void end(int ph) {
+    if (on) cudaEventRecord(t->ev[2 * ph + 1], s);
+  }
+};
+
+// One FMM pass with the charges currently in t->work.
+template <class R>
+void run_pass(fmm_tree* t, cudaStream_t s, int mode, R* a, R* b) {
+  const bool timing = (t->flags & FMM_FLAG_TIMING) != 0;
+  PhaseTimer T{t, s, timing};
+  PhaseTimer Ts{t, t->side, timing};
+  T.begin(FMM_PH_EVAL_TOTAL);
+  // near field on the side stream, concurrently with the far field
+  GB_CK(cudaEventRecord(t->fork, s));
+  GB_CK(cudaStreamWaitEvent(t->side, t->fork, 0));
+  Ts.begin(FMM_PH_P2P);
+  launch_p2p<R>(t, t->side);
+  Ts.end(FMM_PH_P2P);
+  GB_CK(cudaEventRecord(t->join, t->side));
+  // far field
+  GB_CK(cudaMemsetAsync(t->L, 0, sizeof(R) * (size_t)t->ncell * t->Kp, s));
+  T.begin(FMM_PH_P2M);
+  launch_p2m<R>(t, s);
+  T.end(FMM_PH_P2M);
+  T.begin(FMM_PH_M2M);
+  for (int l = t->nlevel - 2; l >= 0; --l) launch_m2m<R>(t, l, s);
+  T.end(FMM_PH_M2M);
+  T.begin(FMM_PH_M2L);
+  launch_m2l_cuda_core<R>(t, s);
+  T.end(FMM_PH_M2L);
+  T.begin(FMM_PH_L2L);
+  for (int l = 1; l < t->nlevel; ++l) launch_l2l<R>(t, l, s);
+  T.end(FMM_PH_L2L);
+  GB_CK(cudaStreamWaitEvent(s, t->join, 0));
+  T.begin(FMM_PH_L2P);
+  launch_l2p_finalize<R>(t, mode, a, b, s);
+  T.end(FMM_PH_L2P);
+  T.end(FMM_PH_EVAL_TOTAL);
+}
+
+template <class R>
+int evaluate_common(fmm_tree* t, const R* q, R* pot, R* force, fmm_stream stream) {
+  if (!t || !pot) return FMM_ERR_ARG;
+  if (t->precision != (int)(8 * sizeof(R))) return FMM_ERR_STATE;
+  cudaStream_t s = (cudaStream_t)stream;
+  try {
+    if (q) launch_set_charges<R>(t, q, s);
+    else GB_CK(cudaMemcpyAsync(t->work, t->bodies, sizeof(R) * 4 * (size_t)t->N, cudaMemcpyDeviceToDevice, s));
+    run_pass<R>(t, s, 0, pot, force);
+    t->evaluations++;
+  } catch (const Error& e) {
+    return to_code(e);
+  }
+  return FMM_OK;
+}
+
+template <class R>
+int backward_common(fmm_tree* t, const R* w, R* dq, R* dx, fmm_stream stream) {
+  if (!t || !w || !dq || !dx) return FMM_ERR_ARG;
+  if (t->precision != (int)(8 * sizeof(R))) return FMM_ERR_STATE;
+  if (t->evaluations == 0) return FMM_ERR_STATE;
+  cudaStream_t s = (cudaStream_t)stream;
+  try {
+    launch_set_charges<R>(t, w, s);
+    run_pass<R>(t, s, 1, dq, dx);
+  } catch (const Error& e) {
+    return to_code(e);
+  }
+  return FMM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int fmm_build(const float* xyzq, int64_t n, int p, double theta, int ncrit, uint32_t flags,
+              const fmm_allocator* alloc, fmm_stream stream, fmm_tree** out) {
+  return build_common<float>(xyzq, n, p, theta, ncrit, flags, alloc, stream, out);
+}
+
+int fmm_build_f64(const double* xyzq, int64_t n, int p, double theta, int ncrit, uint32_t flags,
+                  const fmm_allocator* alloc, fmm_stream stream, fmm_tree** out) {
+  return build_common<double>(xyzq, n, p, theta, ncrit, flags, alloc, stream, out);
+}
+
+int fmm_evaluate(fmm_tree* t, const float* q, float* pot, float* force, fmm_stream stream) {
+  return evaluate_common<float>(t, q, pot, force, stream);
+}
+
+int fmm_evaluate_f64(fmm_tree* t, const double* q, double* pot, double* force, fmm_stream stream) {
+  return evaluate_common<double>(t, q, pot, force, stream);
+}
+
+int fmm_backward(fmm_tree* t, const float* w, float* dq, float* dx, fmm_stream stream) {
+  return backward_common<float>(t, w, dq, dx, stream);
+}
+
+int fmm_backward_f64(fmm_tree* t, const double* w, double* dq, double* dx, fmm_stream stream) {
+  return backward_common<double>(t, w, dq, dx, stream);
+}
+
+int fmm_solve_host(const float* xyzq_h, const float* w_h, int64_t n, int p, double theta, int ncrit,
+                   uint32_t flags, float* pot_h, float* force_h, float* dq_h, float* dx_h,
+                   fmm_stream stream) {
+  if (!xyzq_h || !pot_h || n < 1 || n > 0x7fffffffll) return FMM_ERR_ARG;
+  if (w_h && (!dq_h || !dx_h)) return FMM_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  float *d_x = nullptr, *d_w = nullptr, *d_pot = nullptr, *d_force = nullptr, *d_dq = nullptr, *d_dx = nullptr;
+  fmm_tree* t = nullptr;
+  int rc = FMM_OK;
+  auto mal = [&](float** p, size_t count) {
+    if (rc != FMM_OK) return;
+    if (cudaMallocAsync((void**)p, sizeof(float) * count, s) != cudaSuccess) {
+      cudaGetLastError();
+      rc = FMM_ERR_OOM;
+    }
+  };
+  mal(&d_x, 4 * (size_t)n);
+  mal(&d_pot, (size_t)n);
+  if (force_h) mal(&d_force, 3 * (size_t)n);
+  if (w_h) {
+    mal(&d_w, (size_t)n);
+    mal(&d_dq, (size_t)n);
+    mal(&d_dx, 3 * (size_t)n);
+  }
+  if (rc == FMM_OK && cudaMemcpyAsync(d_x, xyzq_h, sizeof(float) * 4 * n, cudaMemcpyHostToDevice, s) != cudaSuccess)
+    rc = FMM_ERR_CUDA;
+  if (rc == FMM_OK && w_h && cudaMemcpyAsync(d_w, w_h, sizeof(float) * n, cudaMemcpyHostToDevice, s) != cudaSuccess)
+    rc = FMM_ERR_CUDA;
+  if (rc == FMM_OK) rc = fmm_build(d_x, n, p, theta, ncrit, flags, nullptr, stream, &t);
+  if (rc == FMM_OK) rc = fmm_evaluate(t, nullptr, d_pot, d_force, stream);
+  if (rc == FMM_OK && w_h) rc = fmm_backward(t, d_w, d_dq, d_dx, stream);
+  auto back = [&](float* h, const float* d, size_t count) {
+    if (rc == FMM_OK && h && cudaMemcpyAsync(h, d, sizeof(float) * count, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+      rc = FMM_ERR_CUDA;
+  };
+  back(pot_h, d_pot, (size_t)n);
+  if (force_h) back(force_h, d_force, 3 * (size_t)n);
+  if (w_h) {
+    back(dq_h, d_dq, (size_t)n);
+    back(dx_h, d_dx, 3 * (size_t)n);
+  }
+  if (t) fmm_destroy(t);
+  float* all[6] = {d_x, d_w, d_pot, d_force, d_dq, d_dx};
+  for (float* p : all)
+    if (p) cudaFreeAsync(p, s);
+  if (cudaStreamSynchronize(s) != cudaSuccess && rc == FMM_OK) rc = FMM_ERR_CUDA;
+  cudaGetLastError();
+  return rc;
+}
+
+int fmm_get_stats(const fmm_tree* tc, fmm_stats* o) {
+  if (!tc || !o) return FMM_ERR_ARG;
+  fmm_tree* t = const_cast<fmm_tree*>(tc);
+  std::memset(o, 0, sizeof(*o));
+  o->n_bodies = t->N;
+  o->n_cells = t->ncell;
+  o->n_leaves = t->nleaf;
+  o->n_levels = t->nlevel;
+  o->n_p2p = t->n_p2p;
+  o->n_p2p_ranges = t->n_p2p_ranges;
+  o->n_p2p_body_pairs = t->p2p_body_pairs;
+  o->n_m2l = t->n_m2l;
+  o->n_m2l_classes = t->nclass;
+  o->n_m2l_tiles = t->ntile;
+  o->n_m2l_slots = t->nentry * kTile;
+  o->p = t->p;
+  o->K = t->K;
+  o->ncrit = t->ncrit;
+  o->precision_bits = t->precision;
+  o->theta = t->theta;
+  o->flags = t->flags;
+  o->m2l_engine = t->m2l_engine;
+  o->workspace_bytes = (int64_t)t->arena.bytes;
+  o->evaluations = t->evaluations;
+  if ((t->flags & FMM_FLAG_TIMING) && t->evaluations > 0) {
+    if (cudaEventSynchronize(t->ev[2 * FMM_PH_EVAL_TOTAL + 1]) != cudaSuccess) {
+      cudaGetLastError();
+      return FMM_ERR_CUDA;
+    }
+    cudaEventSynchronize(t->ev[2 * FMM_PH_P2P + 1]);
+    for (int ph = 0; ph < FMM_PH_COUNT; ++ph) {
+      if (ph == FMM_PH_BUILD_TOTAL) continue;
+      float ms = 0.0f;
+      if (cudaEventElapsedTime(&ms, t->ev[2 * ph], t->ev[2 * ph + 1]) == cudaSuccess) t->ms[ph] = ms;
+      else cudaGetLastError();
+    }
+  }
+  for (int ph = 0; ph < FMM_PH_COUNT; ++ph) o->ms[ph] = t->ms[ph];
+  return FMM_OK;
+}
+
+int fmm_destroy(fmm_tree* t) {
+  if (!t) return FMM_OK;
+  // the caller's streams of earlier calls: wait for all of the device's work
+  // on this tree's buffers before they are released
+  cudaError_t e = cudaDeviceSynchronize();
+  release_tree(t);
+  return e == cudaSuccess ? FMM_OK : FMM_ERR_CUDA;
+}
+
+const char* fmm_strerror(int code) {
+  switch (code) {
+    case FMM_OK: return "ok";
+    case FMM_ERR_ARG: return "invalid argument";
+    case FMM_ERR_NONFINITE: return "non-finite position or charge";
+    case FMM_ERR_OOM: return "out of device memory";
+    case FMM_ERR_CUDA: return "CUDA error";
+    case FMM_ERR_TIMEOUT: return "bounded device wait timed out";
+    case FMM_ERR_STATE: return "call out of order or wrong precision";
+    case FMM_ERR_RANGE: return "operator not representable in the working precision";
+    default: return "unknown error";
+  }
+}
+
+int fmm_get_root(const fmm_tree* t, double* out) {
+  if (!t || !out) return FMM_ERR_ARG;
+  for (int k = 0; k < 3; ++k) {
+    out[k] = t->root.lo[k];
+    out[3 + k] = t->root.hi[k];
+    out[6 + k] = t->root.centre[k];
+    out[10 + k] = t->root.corner[k];
+  }
+  out[9] = t->root.H;
+  return FMM_OK;
+}
+
+int fmm_get_keys(const fmm_tree* t, uint64_t* keys, int32_t* perm, fmm_stream stream) {
+  if (!t || !keys || !perm) return FMM_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (cudaMemcpyAsync(keys, t->keys, sizeof(uint64_t) * t->N, cudaMemcpyDeviceToDevice, s) != cudaSuccess ||
+      cudaMemcpyAsync(perm, t->perm, sizeof(int32_t) * t->N, cudaMemcpyDeviceToDevice, s) != cudaSuccess) {
+    cudaGetLastError();
+    return FMM_ERR_CUDA;
+  }
+  return FMM_OK;
+}
+
+int fmm_get_cells(const fmm_tree* t, int32_t* cells, fmm_stream stream) {
+  if (!t || !cells) return FMM_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int32_t* rows[9] = {t->c.level, t->c.ix, t->c.iy, t->c.iz, t->c.bbeg, t->c.bend, t->c.cbeg, t->c.nch, t->c.parent};
+  for (int r = 0; r < 9; ++r)
+    if (cudaMemcpyAsync(cells + (int64_t)r * t->ncell, rows[r], sizeof(int32_t) * t->ncell,
+                        cudaMemcpyDeviceToDevice, s) != cudaSuccess) {
+      cudaGetLastError();
+      return FMM_ERR_CUDA;
+    }
+  return FMM_OK;
+}
+
+int fmm_get_lists(const fmm_tree* t, int32_t* p2p_tgt, int32_t* p2p_src, int32_t* m2l_tgt, int32_t* m2l_src,
+                  fmm_stream stream) {
+  if (!t || !p2p_tgt || !p2p_src || (t->n_m2l && (!m2l_tgt || !m2l_src))) return FMM_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  bool ok = cudaMemcpyAsync(p2p_tgt, t->p2p_tgt, sizeof(int32_t) * t->n_p2p, cudaMemcpyDeviceToDevice, s) == cudaSuccess &&
+            cudaMemcpyAsync(p2p_src, t->p2p_src, sizeof(int32_t) * t->n_p2p, cudaMemcpyDeviceToDevice, s) == cudaSuccess;
+  if (ok && t->n_m2l)
+    ok = cudaMemcpyAsync(m2l_tgt, t->m2l_tgt, sizeof(int32_t) * t->n_m2l, cudaMemcpyDeviceToDevice, s) == cudaSuccess &&
+         cudaMemcpyAsync(m2l_src, t->m2l_src, sizeof(int32_t) * t->n_m2l, cudaMemcpyDeviceToDevice, s) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    return FMM_ERR_CUDA;
+  }
+  return FMM_OK;
+}
+
+int fmm_get_expansions(const fmm_tree* t, void* M, void* L, fmm_stream stream) {
+  if (!t) return FMM_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t rs = t->precision == 64 ? 8 : 4;
+  // rows are stored with a padded stride Kp; copy out K per row
+  if (M && cudaMemcpy2DAsync(M, rs * t->K, t->M, rs * t->Kp, rs * t->K, t->ncell, cudaMemcpyDeviceToDevice, s) != cudaSuccess) {
+    cudaGetLastError();
+    return FMM_ERR_CUDA;
+  }
+  if (L && cudaMemcpy2DAsync(L, rs * t->K, t->L, rs * t->Kp, rs * t->K, t->ncell, cudaMemcpyDeviceToDevice, s) != cudaSuccess) {
+    cudaGetLastError();
+    return FMM_ERR_CUDA;
+  }
+  return FMM_OK;
+}
+
+int fmm_debug_checks(const fmm_tree* t, int64_t* out) {
+  if (!t || !out) return FMM_ERR_ARG;
+  unsigned long long h[4] = {0, 0, 0, 0};
+  if (cudaMemcpy(h, t->check_rec, sizeof(h), cudaMemcpyDeviceToHost) != cudaSuccess) {
+    cudaGetLastError();
+    return FMM_ERR_CUDA;
+  }
+  for (int k = 0; k < 4; ++k) out[k] = (int64_t)h[k];
+#ifdef GBFMM_CHECKED
+  return 1;
+#else
+  return FMM_OK;
+#endif
+}
+
+int fmm_get_plan(const fmm_tree* t, int32_t* tile_tgt, int32_t* tile_eptr, int32_t* entry_class,
+                 int32_t* entry_src, int32_t* p2p_rptr, int32_t* p2p_ranges, fmm_stream stream) {
+  if (!t) return FMM_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  struct Cp {
+    void* dst;
+    const void* src;
+    size_t bytes;
+  } cps[6] = {
+      {tile_tgt, t->tile_tgt, sizeof(int32_t) * (size_t)t->ntile * kTile},
+      {tile_eptr, t->tile_eptr, sizeof(int32_t) * (size_t)(t->ntile + 1)},
+      {entry_class, t->entry_class, sizeof(int32_t) * (size_t)t->nentry},
+      {entry_src, t->entry_src, sizeof(int32_t) * (size_t)t->nentry * kTile},
+      {p2p_rptr, t->p2p_rptr, sizeof(int32_t) * (size_t)(t->nleaf + 1)},
+      {p2p_ranges, t->p2p_ranges, sizeof(int2) * (size_t)t->n_p2p_ranges},
+  };
+  for (auto& c : cps) {
+    if (!c.dst || !c.src || c.bytes == 0) continue;
+    if (cudaMemcpyAsync(c.dst, c.src, c.bytes, cudaMemcpyDeviceToDevice, s) != cudaSuccess) {
+      cudaGetLastError();
+      return FMM_ERR_CUDA;
+    }
+  }
+  return FMM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,153 @@
+// common.cuh -- internal declarations shared by the gbfmm CUDA sources.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "gbfmm.h"
+
+namespace gbfmm {
+
+constexpr int kMaxLevel = 21;   // 63-bit Morton keys, 3 bits per level (Sec. II.B)
+constexpr int kMaxP = 16;       // expansion terms supported (K = p*p <= 256)
+constexpr int kTile = 128;      // targets per M2L tile (rows of one MMA / one CTA)
+
+struct Error {
+  int code;
+  std::string what;
+};
+
+[[noreturn]] void fail(int code, const char* what);
+void check_cuda(cudaError_t e, const char* what);
+void count_launch();
+#define GB_CK(call) ::gbfmm::check_cuda((call), #call)
+// after every kernel launch: count it and surface a launch error
+#define GB_LAUNCH(what) (::gbfmm::count_launch(), ::gbfmm::check_cuda(cudaGetLastError(), what))
+
+// Stream-ordered device memory through the caller's allocator or
+// cudaMallocAsync.  Every allocation of a tree is recorded for release.
+struct Arena {
+  fmm_allocator user{};
+  bool has_user = false;
+  cudaStream_t stream = nullptr;
+  std::vector<void*> live;
+  void* alloc(size_t bytes);
+  void release(void* p);
+  void release_all();
+  size_t bytes = 0;
+};
+
+template <class T>
+T* alloc_n(Arena& a, size_t n) {
+  return static_cast<T*>(a.alloc(sizeof(T) * (n ? n : 1)));
+}
+
+// ---------------------------------------------------------------- device prims
+// Exclusive scan of n int64 values in place; returns the total (synchronises
+// the stream to read it back when `total` is requested).
+void scan_exclusive_i64(Arena& a, int64_t* d, int64_t n, cudaStream_t s);
+int64_t scan_exclusive_i64_total(Arena& a, int64_t* d, int64_t n, cudaStream_t s);
+
+// LSD radix sort of (key, value) pairs on bits [0, bits) of the key; stable.
+// keys/vals are replaced by the sorted arrays (ping-pong buffers from the arena).
+void radix_sort_pairs(Arena& a, uint64_t*& keys, int32_t*& vals, int64_t n, int bits,
+                      cudaStream_t s);
+void radix_sort_keys(Arena& a, uint64_t*& keys, int64_t n, int bits, cudaStream_t s);
+
+// Root cube of the bounding box (Sec. II.C "local bounding box").
+struct RootBox {
+  double lo[3], hi[3], centre[3], H, corner[3];
+  int nonfinite;
+};
+
+// ------------------------------------------------------------------- the tree
+// Array sizes of a tree, passed to the evaluation kernels (bounds of the
+// self-checking build) and the record of the first violation.
+struct Lim {
+  long long N, ncell, nleaf, Kp, ntile, nentry, nclass, nranges;
+  unsigned long long* rec;
+};
+
+struct Cells {
+  int32_t *level = nullptr, *ix = nullptr, *iy = nullptr, *iz = nullptr;
+  int32_t *bbeg = nullptr, *bend = nullptr, *cbeg = nullptr, *nch = nullptr, *parent = nullptr;
+};
+
+}  // namespace gbfmm
+
+struct fmm_tree {
+  int precision = 32;  // 32 or 64 (bits of the working real type)
+  int64_t N = 0;
+  int p = 0, K = 0, Kp = 0, ncrit = 0;
+  double theta = 0.0;
+  uint32_t flags = 0;
+  gbfmm::Arena arena;
+  cudaStream_t stream = nullptr;  // build stream (workspace is ordered on it)
+
+  gbfmm::RootBox root{};
+  double* d_root = nullptr;  // lo3 hi3 centre3 H corner3
+
+  void* bodies = nullptr;    // sorted (x, y, z, q) as float4 / double4
+  void* work = nullptr;      // sorted bodies with the charges of the current pass
+  uint64_t* keys = nullptr;  // sorted keys
+  int32_t* perm = nullptr;   // sorted position -> input index
+
+  int ncell = 0, nleaf = 0, nlevel = 0;
+  std::vector<int> level_begin;  // host: first cell of each level, + end
+  gbfmm::Cells c;
+  int32_t* leaves = nullptr;  // leaf cell ids in cell order
+  int32_t* leaf_of_cell = nullptr;  // cell -> leaf index or -1
+
+  int64_t n_p2p = 0, n_m2l = 0, n_p2p_ranges = 0, p2p_body_pairs = 0;
+  int32_t *p2p_tgt = nullptr, *p2p_src = nullptr, *m2l_tgt = nullptr, *m2l_src = nullptr;
+  int32_t* p2p_rptr = nullptr;  // per leaf: ranges [rptr[l], rptr[l+1])
+  int2* p2p_ranges = nullptr;   // (begin, end) sorted body ranges, self excluded
+
+  // M2L engine: targets tiled kTile at a time, per tile one entry per
+  // translation operator with the source of each tile row (or -1).
+  int nclass = 0, ntile = 0;
+  int64_t nentry = 0;
+  int32_t* class_desc = nullptr;   // 4 per class: level_src - level_tgt, dx, dy, dz
+  int32_t* tile_tgt = nullptr;     // ntile x kTile target cells (-1 = empty row)
+  int32_t* tile_eptr = nullptr;    // ntile + 1
+  int32_t* entry_class = nullptr;  // nentry
+  int32_t* entry_src = nullptr;    // nentry x kTile
+  void* m2l_ops = nullptr;         // nclass x Kp x Kp (out-major), working precision
+  float* m2l_ops_lo = nullptr;     // low parts for the 3xTF32 engine
+  int m2l_engine = 0;
+  void* m2m_ops = nullptr;  // 8 x Kp x Kp
+  void* l2l_ops = nullptr;  // 8 x Kp x Kp
+
+  void* M = nullptr;  // ncell x Kp
+  void* L = nullptr;  // ncell x Kp
+  float* M_lo = nullptr;  // split copy of M for the 3xTF32 engine
+  void* near = nullptr;   // N x 4 (phi, grad) sorted, P2P part
+  void* grad_q = nullptr; // N x 4 (phi, grad) sorted, of the last evaluate
+  void* q_last = nullptr; // N sorted charges of the last evaluate
+  int evaluations = 0;
+
+  unsigned long long* check_rec = nullptr;  // self-check record (checked build)
+  gbfmm::Lim lim{};
+  cudaStream_t side = nullptr;  // P2P runs here, concurrently with the far field
+  cudaEvent_t fork = nullptr, join = nullptr;
+  cudaEvent_t ev[2 * FMM_PH_COUNT] = {};
+  float ms[FMM_PH_COUNT] = {};
+};
+
+namespace gbfmm {
+
+// Tree construction (tree.cu)
+void build_tree(fmm_tree* t, const void* xyzq, bool f64);
+// Traversal and lists (traverse.cu)
+void build_lists(fmm_tree* t);
+// M2L tiles and operator tables (ops.cu)
+void build_m2l_plan(fmm_tree* t);
+void build_operators(fmm_tree* t);
+// Evaluation passes (fmm.cu)
+void evaluate_pass(fmm_tree* t, const void* q_input, void* pot, void* force, cudaStream_t s,
+                   bool for_backward_w, const void* w, void* dq, void* dx);
+
+}  // namespace gbfmm

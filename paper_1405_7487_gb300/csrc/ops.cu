@@ -1,0 +1,480 @@
+// ops.cu -- translation operators (set up in double precision) and the M2L
+// plan: targets tiled kTile at a time, interactions grouped by translation
+// operator.
+//
+// Expansions (Sec. II.A: P2M, M2M, M2L, L2L, L2P; the mathematics is that of
+// the solid-harmonic FMM the paper cites):
+//   Ups_n^m(r) = r^n P_n^m(cos t) e^{i m phi} / (n+m)!      (regular)
+//   Th_n^m(r)  = (n-m)! P_n^m(cos t) e^{i m phi} / r^{n+1}   (irregular)
+//   (Condon-Shortley phase, X_n^{-m} = (-1)^m conj(X_n^m)), so that
+//   1/|x - y| = sum conj(Ups_n^m(y)) Th_n^m(x),
+//   Ups(a + b) = sum Ups_k^l(a) Ups_{n-k}^{m-l}(b),
+//   Th_n^m(x - y) = sum conj(Ups_k^l(y)) Th_{n+k}^{m+l}(x).
+// Stored expansions are scaled by the cell half side R so that every
+// operator depends only on the relative geometry:
+//   M~_n^m = M_n^m / R_A^n,   L~_k^l = L_k^l R_B^{k+1}.
+//   M2M  M~_n^m(P) = sum M~_k^l(C) 2^{-k} conj(Ups_{n-k}^{m-l}(t)),   t = (c_C - c_P)/R_P
+//   L2L  L~_j^i(C) = sum L~_k^l(P) 2^{-(j+1)} conj(Ups_{k-j}^{l-i}(t))
+//   M2L  L~_k^l(B) = (-1)^k sum M~_n^m(A) (R_B/r)^{k+1} (R_A/r)^n Th_{n+k}^{m+l}((c_B - c_A)/r),
+//        r = min(R_A, R_B), so (c_B - c_A)/r is an integer vector.
+// Each complex operator acts on the real packing of the m >= 0 coefficients
+// (index n*n for Re X_n^0, n*n + 2m - 1 / n*n + 2m for Re / Im X_n^m) and is
+// written out as a real Kp x Kp matrix.
+#include <algorithm>
+#include <cfloat>
+
+#include "common.cuh"
+
+namespace gbfmm {
+namespace {
+
+constexpr int kThreads = 256;
+inline unsigned blocks(int64_t n) { return (unsigned)((n + kThreads - 1) / kThreads); }
+
+struct cd {
+  double re, im;
+};
+__device__ __forceinline__ cd cmul(cd a, cd b) { return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re}; }
+__device__ __forceinline__ cd cconj(cd a) { return {a.re, -a.im}; }
+__device__ __forceinline__ cd cscale(cd a, double s) { return {a.re * s, a.im * s}; }
+
+__device__ __forceinline__ int tri(int n, int m) { return n * (n + 1) / 2 + m; }
+
+// X_n^m for any -n <= m <= n from the m >= 0 triangle.
+__device__ __forceinline__ cd hget(const cd* X, int n, int m) {
+  if (m >= 0) return X[tri(n, m)];
+  cd v = X[tri(n, -m)];
+  v.im = -v.im;
+  if ((-m) & 1) {
+    v.re = -v.re;
+    v.im = -v.im;
+  }
+  return v;
+}
+
+// Regular harmonics, degrees < P, into the m >= 0 triangle (one thread).
+__device__ void regular_tri(double x, double y, double z, int P, cd* U) {
+  const double r2 = x * x + y * y + z * z;
+  U[0] = {1.0, 0.0};
+  for (int m = 1; m < P; ++m) U[tri(m, m)] = cscale(cmul(U[tri(m - 1, m - 1)], {-x, -y}), 1.0 / (2.0 * m));
+  for (int m = 0; m < P; ++m)
+    for (int n = m + 1; n < P; ++n) {
+      cd a = U[tri(n - 1, m)];
+      cd b = n - 2 >= m ? U[tri(n - 2, m)] : cd{0.0, 0.0};
+      double f = 1.0 / ((double)(n + m) * (double)(n - m));
+      U[tri(n, m)] = {((2.0 * n - 1.0) * z * a.re - r2 * b.re) * f, ((2.0 * n - 1.0) * z * a.im - r2 * b.im) * f};
+    }
+}
+
+// Irregular harmonics, degrees < P, into the m >= 0 triangle (one thread).
+__device__ void irregular_tri(double x, double y, double z, int P, cd* T) {
+  const double r2 = x * x + y * y + z * z;
+  const double ir2 = 1.0 / r2;
+  T[0] = {1.0 / sqrt(r2), 0.0};
+  for (int m = 1; m < P; ++m)
+    T[tri(m, m)] = cscale(cmul(T[tri(m - 1, m - 1)], {x, y}), -(2.0 * m - 1.0) * ir2);
+  for (int m = 0; m < P; ++m)
+    for (int n = m + 1; n < P; ++n) {
+      cd a = T[tri(n - 1, m)];
+      cd b = n - 2 >= m ? T[tri(n - 2, m)] : cd{0.0, 0.0};
+      double c1 = (2.0 * n - 1.0) * z, c2 = (double)(n + m - 1) * (double)(n - m - 1);
+      T[tri(n, m)] = {(c1 * a.re - c2 * b.re) * ir2, (c1 * a.im - c2 * b.im) * ir2};
+    }
+}
+
+__device__ __forceinline__ int ridx(int n, int m, int part) { return n * n + (m == 0 ? 0 : 2 * m - 1 + part); }
+
+enum Kind { kM2M = 0, kL2L = 1, kM2L = 2 };
+
+// Complex coefficient C(out (a, b), in (c, d)) for -c <= d <= c.
+struct Coef {
+  int kind;
+  double sA, sB;  // M2L: R_A / r and R_B / r
+  const cd* X;
+  __device__ cd operator()(int a, int b, int c, int d) const {
+    if (kind == kM2L) {
+      // out (k = a, l = b), in (n = c, m = d)
+      cd t = hget(X, a + c, d + b);
+      double f = ((a & 1) ? -1.0 : 1.0) * pow(sB, a + 1) * pow(sA, c);
+      return cscale(t, f);
+    }
+    if (kind == kM2M) {
+      // out (n = a, m = b), in (k = c, l = d)
+      if (c > a) return {0.0, 0.0};
+      int dm = b - d;
+      if (dm < -(a - c) || dm > (a - c)) return {0.0, 0.0};
+      return cscale(cconj(hget(X, a - c, dm)), ldexp(1.0, -c));
+    }
+    // L2L: out (j = a, i = b), in (k = c, l = d)
+    if (c < a) return {0.0, 0.0};
+    int dl = d - b;
+    if (dl < -(c - a) || dl > (c - a)) return {0.0, 0.0};
+    return cscale(cconj(hget(X, c - a, dl)), ldexp(1.0, -(a + 1)));
+  }
+};
+
+template <class R>
+__device__ __forceinline__ void put(R* op, int Kp, bool out_major, int ro, int ri, double v, int* range_bad) {
+  if (out_major) op[(int64_t)ro * Kp + ri] = (R)v;
+  else op[(int64_t)ri * Kp + ro] = (R)v;
+  if (sizeof(R) == 4 && !(fabs(v) <= (double)FLT_MAX)) *range_bad = 1;
+}
+
+// Real Kp x Kp matrices of one operator per block.  geom: per operator
+// (x, y, z, sA, sB) in double; X built in shared memory.
+template <class R>
+__global__ void k_build_ops(int kind, int p, int Kp, const double* __restrict__ geom, int nops,
+                            R* __restrict__ ops, float* __restrict__ ops_lo, bool out_major,
+                            int* __restrict__ range_bad) {
+  extern __shared__ cd X[];
+  const int op = blockIdx.x;
+  if (op >= nops) return;
+  const double* g = geom + 5 * (int64_t)op;
+  const int P = kind == kM2L ? 2 * p - 1 : p;
+  if (threadIdx.x == 0) {
+    if (kind == kM2L) irregular_tri(g[0], g[1], g[2], P, X);
+    else regular_tri(g[0], g[1], g[2], P, X);
+  }
+  __syncthreads();
+  Coef C{kind, g[3], g[4], X};
+  R* o = ops + (int64_t)op * Kp * Kp;
+  float* olo = ops_lo ? ops_lo + (int64_t)op * Kp * Kp : nullptr;
+  // zero (padding rows/columns stay zero)
+  for (int i = threadIdx.x; i < Kp * Kp; i += blockDim.x) {
+    o[i] = (R)0;
+    if (olo) olo[i] = 0.0f;
+  }
+  __syncthreads();
+  const int nt = p * (p + 1) / 2;
+  for (int w = threadIdx.x; w < nt * nt; w += blockDim.x) {
+    const int oi = w / nt, ii = w % nt;
+    int a = 0;
+    while ((a + 1) * (a + 2) / 2 <= oi) ++a;
+    const int b = oi - a * (a + 1) / 2;
+    int c = 0;
+    while ((c + 1) * (c + 2) / 2 <= ii) ++c;
+    const int d = ii - c * (c + 1) / 2;
+    double vals[4];  // (Re out, Im out) x (Re in, Im in)
+    if (d == 0) {
+      cd cp = C(a, b, c, 0);
+      vals[0] = cp.re;
+      vals[1] = 0.0;
+      vals[2] = cp.im;
+      vals[3] = 0.0;
+    } else {
+      cd cp = C(a, b, c, d), cn = C(a, b, c, -d);
+      const double s = (d & 1) ? -1.0 : 1.0;
+      // input M = u + i v:  cp M + cn (-1)^d conj(M)
+      vals[0] = cp.re + s * cn.re;   // Re out <- u
+      vals[1] = -cp.im + s * cn.im;  // Re out <- v
+      vals[2] = cp.im + s * cn.im;   // Im out <- u
+      vals[3] = cp.re - s * cn.re;   // Im out <- v
+    }
+    const int nout = b == 0 ? 1 : 2, nin = d == 0 ? 1 : 2;
+    for (int po = 0; po < nout; ++po)
+      for (int pi = 0; pi < nin; ++pi) {
+        const double v = vals[2 * po + pi];
+        const int ro = ridx(a, b, po), ri = ridx(c, d, pi);
+        put<R>(o, Kp, out_major, ro, ri, v, range_bad);
+        if (olo) {
+          // 3xTF32 split: hi rounded to TF32 (round to nearest), lo the rest
+          float hf = (float)v;
+          uint32_t hb;
+          asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(hb) : "f"(hf));
+          float hi = __uint_as_float(hb);
+          float lo = (float)(v - (double)hi);
+          int64_t at = out_major ? (int64_t)ro * Kp + ri : (int64_t)ri * Kp + ro;
+          o[at] = (R)hi;
+          olo[at] = lo;
+        }
+      }
+  }
+}
+
+// ------------------------------------------------------------- M2L plan
+struct CellView {
+  const int32_t *level, *ix, *iy, *iz;
+};
+
+__global__ void k_target_flags(const int32_t* __restrict__ tgt, int64_t n, int32_t* __restrict__ has) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  if (i == 0 || tgt[i] != tgt[i - 1]) has[tgt[i]] = 1;
+}
+
+// Targets ordered by (octant within the parent, cell): cells sharing an
+// octant see the same relative source pattern, so a tile of them needs few
+// distinct operators.
+__global__ void k_target_keys(const int32_t* __restrict__ has, CellView c, int ncell,
+                              uint64_t* __restrict__ key, unsigned long long* __restrict__ count) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= ncell) return;
+  if (has[i]) {
+    const uint64_t oct = ((c.ix[i] & 1) << 2) | ((c.iy[i] & 1) << 1) | (c.iz[i] & 1);
+    key[i] = (oct << 32) | (uint32_t)i;
+    atomicAdd(count, 1ull);
+  } else {
+    key[i] = ~0ull;
+  }
+}
+
+__global__ void k_target_rank(const uint64_t* __restrict__ key, int64_t ntgt, int64_t padded,
+                              int32_t* __restrict__ tile_tgt, int32_t* __restrict__ rank_of) {
+  const int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (r >= padded) return;
+  if (r < ntgt) {
+    const int cell = (int)(key[r] & 0xffffffffu);
+    tile_tgt[r] = cell;
+    rank_of[cell] = (int32_t)r;
+  } else {
+    tile_tgt[r] = -1;
+  }
+}
+
+__global__ void k_class_keys(const int32_t* __restrict__ tgt, const int32_t* __restrict__ src,
+                             int64_t n, CellView c, uint64_t* __restrict__ key, int32_t* __restrict__ val) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int A = src[i], B = tgt[i];
+  const int la = c.level[A], lb = c.level[B];
+  const int lmax = la > lb ? la : lb;
+  const int sh = kMaxLevel - lmax;
+  int64_t d[3];
+  d[0] = (((2ll * c.ix[A] + 1) << (kMaxLevel - la)) - ((2ll * c.ix[B] + 1) << (kMaxLevel - lb))) >> sh;
+  d[1] = (((2ll * c.iy[A] + 1) << (kMaxLevel - la)) - ((2ll * c.iy[B] + 1) << (kMaxLevel - lb))) >> sh;
+  d[2] = (((2ll * c.iz[A] + 1) << (kMaxLevel - la)) - ((2ll * c.iz[B] + 1) << (kMaxLevel - lb))) >> sh;
+  const int64_t lim = 1ll << 18;
+  const bool regular = d[0] > -lim && d[0] < lim && d[1] > -lim && d[1] < lim && d[2] > -lim && d[2] < lim;
+  if (regular) {
+    key[i] = ((uint64_t)(la - lb + 32) << 57) | ((uint64_t)(d[0] + lim) << 38) |
+             ((uint64_t)(d[1] + lim) << 19) | (uint64_t)(d[2] + lim);
+  } else {
+    key[i] = (1ull << 63) | (uint64_t)i;
+  }
+  val[i] = (int32_t)i;
+}
+
+__global__ void k_unique_flags(const uint64_t* __restrict__ key, int64_t n, int shift,
+                               int64_t* __restrict__ f) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  f[i] = (i == 0 || (key[i] >> shift) != (key[i - 1] >> shift)) ? 1 : 0;
+}
+
+// Class id of every pair and the descriptor (dl, dx, dy, dz) of every class.
+__global__ void k_class_assign(const uint64_t* __restrict__ key, const int32_t* __restrict__ val,
+                               const int64_t* __restrict__ excl, int64_t n,
+                               const int32_t* __restrict__ tgt, const int32_t* __restrict__ src,
+                               CellView c, int32_t* __restrict__ class_of, int32_t* __restrict__ desc) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const bool first = i == 0 || key[i] != key[i - 1];
+  const int64_t cid = excl[i] + (first ? 0 : -1);
+  class_of[val[i]] = (int32_t)cid;
+  if (!first) return;
+  const int pi = val[i];
+  const int A = src[pi], B = tgt[pi];
+  const int la = c.level[A], lb = c.level[B];
+  const int lmax = la > lb ? la : lb;
+  const int sh = kMaxLevel - lmax;
+  desc[4 * cid + 0] = la - lb;
+  desc[4 * cid + 1] = (int32_t)((((2ll * c.ix[A] + 1) << (kMaxLevel - la)) - ((2ll * c.ix[B] + 1) << (kMaxLevel - lb))) >> sh);
+  desc[4 * cid + 2] = (int32_t)((((2ll * c.iy[A] + 1) << (kMaxLevel - la)) - ((2ll * c.iy[B] + 1) << (kMaxLevel - lb))) >> sh);
+  desc[4 * cid + 3] = (int32_t)((((2ll * c.iz[A] + 1) << (kMaxLevel - la)) - ((2ll * c.iz[B] + 1) << (kMaxLevel - lb))) >> sh);
+}
+
+__global__ void k_entry_keys(const int32_t* __restrict__ tgt, const int32_t* __restrict__ src,
+                             const int32_t* __restrict__ class_of, const int32_t* __restrict__ rank_of,
+                             int64_t n, uint64_t* __restrict__ key, int32_t* __restrict__ val) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const uint64_t r = (uint64_t)rank_of[tgt[i]];
+  const uint64_t tile = r / kTile, slot = r % kTile;
+  key[i] = (tile << 39) | ((uint64_t)(uint32_t)class_of[i] << 7) | slot;
+  val[i] = src[i];
+}
+
+__global__ void k_entry_fill(const uint64_t* __restrict__ key, const int32_t* __restrict__ val,
+                             const int64_t* __restrict__ excl, int64_t n, int32_t* __restrict__ entry_class,
+                             int32_t* __restrict__ entry_src, uint64_t* __restrict__ entry_key) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const bool first = i == 0 || (key[i] >> 7) != (key[i - 1] >> 7);
+  const int64_t e = excl[i] + (first ? 0 : -1);
+  entry_src[e * kTile + (key[i] & (kTile - 1))] = val[i];
+  if (first) {
+    entry_class[e] = (int32_t)((key[i] >> 7) & 0xffffffffu);
+    entry_key[e] = key[i] >> 39;  // tile
+  }
+}
+
+__global__ void k_tile_ptr(const uint64_t* __restrict__ etile, int64_t ne, int ntile,
+                           int32_t* __restrict__ ptr) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t > ntile) return;
+  int64_t lo = 0, hi = ne;
+  while (lo < hi) {
+    int64_t mid = (lo + hi) >> 1;
+    if (etile[mid] < (uint64_t)t) lo = mid + 1;
+    else hi = mid;
+  }
+  ptr[t] = (int32_t)lo;
+}
+
+__global__ void k_m2l_geom(const int32_t* __restrict__ desc, int n, double* __restrict__ geom) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int dl = desc[4 * i];
+  // (c_B - c_A) / r = -(dx, dy, dz); R_A / r = 2^max(0, -dl), R_B / r = 2^max(0, dl)
+  geom[5 * i + 0] = -(double)desc[4 * i + 1];
+  geom[5 * i + 1] = -(double)desc[4 * i + 2];
+  geom[5 * i + 2] = -(double)desc[4 * i + 3];
+  geom[5 * i + 3] = ldexp(1.0, dl < 0 ? -dl : 0);
+  geom[5 * i + 4] = ldexp(1.0, dl > 0 ? dl : 0);
+}
+
+}  // namespace
+
+void build_m2l_plan(fmm_tree* t) {
+  Arena& a = t->arena;
+  cudaStream_t s = t->stream;
+  const int64_t nm = t->n_m2l;
+  CellView cv{t->c.level, t->c.ix, t->c.iy, t->c.iz};
+  if (nm == 0) {
+    t->nclass = 0;
+    t->ntile = 0;
+    t->nentry = 0;
+    t->tile_eptr = alloc_n<int32_t>(a, 1);
+    GB_CK(cudaMemsetAsync(t->tile_eptr, 0, sizeof(int32_t), s));
+    return;
+  }
+  // --- targets and tiles
+  int32_t* has = alloc_n<int32_t>(a, t->ncell);
+  GB_CK(cudaMemsetAsync(has, 0, sizeof(int32_t) * t->ncell, s));
+  k_target_flags<<<blocks(nm), kThreads, 0, s>>>(t->m2l_tgt, nm, has);
+  GB_LAUNCH("k_target_flags");
+  uint64_t* tkey = alloc_n<uint64_t>(a, t->ncell);
+  unsigned long long* d_cnt = alloc_n<unsigned long long>(a, 1);
+  GB_CK(cudaMemsetAsync(d_cnt, 0, sizeof(unsigned long long), s));
+  k_target_keys<<<blocks(t->ncell), kThreads, 0, s>>>(has, cv, t->ncell, tkey, d_cnt);
+  GB_LAUNCH("k_target_keys");
+  radix_sort_keys(a, tkey, t->ncell, 64, s);
+  unsigned long long ntgt = 0;
+  GB_CK(cudaMemcpyAsync(&ntgt, d_cnt, sizeof(ntgt), cudaMemcpyDeviceToHost, s));
+  GB_CK(cudaStreamSynchronize(s));
+  t->ntile = (int)((ntgt + kTile - 1) / kTile);
+  const int64_t padded = (int64_t)t->ntile * kTile;
+  t->tile_tgt = alloc_n<int32_t>(a, padded);
+  int32_t* rank_of = alloc_n<int32_t>(a, t->ncell);
+  k_target_rank<<<blocks(padded), kThreads, 0, s>>>(tkey, (int64_t)ntgt, padded, t->tile_tgt, rank_of);
+  GB_LAUNCH("k_target_rank");
+  a.release(tkey);
+  a.release(has);
+  a.release(d_cnt);
+
+  // --- translation classes
+  uint64_t* ckey = alloc_n<uint64_t>(a, nm);
+  int32_t* cval = alloc_n<int32_t>(a, nm);
+  k_class_keys<<<blocks(nm), kThreads, 0, s>>>(t->m2l_tgt, t->m2l_src, nm, cv, ckey, cval);
+  GB_LAUNCH("k_class_keys");
+  radix_sort_pairs(a, ckey, cval, nm, 64, s);
+  int64_t* flag = alloc_n<int64_t>(a, nm);
+  k_unique_flags<<<blocks(nm), kThreads, 0, s>>>(ckey, nm, 0, flag);
+  GB_LAUNCH("k_unique_flags");
+  const int64_t ncls = scan_exclusive_i64_total(a, flag, nm, s);
+  if (ncls > 0x7fffffff) fail(FMM_ERR_ARG, "too many translation classes");
+  t->nclass = (int)ncls;
+  t->class_desc = alloc_n<int32_t>(a, 4 * ncls);
+  int32_t* class_of = alloc_n<int32_t>(a, nm);
+  k_class_assign<<<blocks(nm), kThreads, 0, s>>>(ckey, cval, flag, nm, t->m2l_tgt, t->m2l_src, cv,
+                                                 class_of, t->class_desc);
+  GB_LAUNCH("k_class_assign");
+  a.release(ckey);
+  a.release(cval);
+  a.release(flag);
+
+  // --- entries: (tile, class) with the source of every tile row
+  uint64_t* ekey = alloc_n<uint64_t>(a, nm);
+  int32_t* eval = alloc_n<int32_t>(a, nm);
+  k_entry_keys<<<blocks(nm), kThreads, 0, s>>>(t->m2l_tgt, t->m2l_src, class_of, rank_of, nm, ekey, eval);
+  GB_LAUNCH("k_entry_keys");
+  a.release(class_of);
+  a.release(rank_of);
+  radix_sort_pairs(a, ekey, eval, nm, 63, s);
+  int64_t* eflag = alloc_n<int64_t>(a, nm);
+  k_unique_flags<<<blocks(nm), kThreads, 0, s>>>(ekey, nm, 7, eflag);
+  GB_LAUNCH("k_unique_flags");
+  const int64_t ne = scan_exclusive_i64_total(a, eflag, nm, s);
+  t->nentry = ne;
+  t->entry_class = alloc_n<int32_t>(a, ne);
+  t->entry_src = alloc_n<int32_t>(a, ne * kTile);
+  GB_CK(cudaMemsetAsync(t->entry_src, 0xff, sizeof(int32_t) * ne * kTile, s));
+  uint64_t* etile = alloc_n<uint64_t>(a, ne);
+  k_entry_fill<<<blocks(nm), kThreads, 0, s>>>(ekey, eval, eflag, nm, t->entry_class, t->entry_src, etile);
+  GB_LAUNCH("k_entry_fill");
+  t->tile_eptr = alloc_n<int32_t>(a, t->ntile + 1);
+  k_tile_ptr<<<blocks(t->ntile + 1), kThreads, 0, s>>>(etile, ne, t->ntile, t->tile_eptr);
+  GB_LAUNCH("k_tile_ptr");
+  a.release(ekey);
+  a.release(eval);
+  a.release(eflag);
+  a.release(etile);
+}
+
+void build_operators(fmm_tree* t) {
+  Arena& a = t->arena;
+  cudaStream_t s = t->stream;
+  const bool f64 = t->precision == 64;
+  const size_t rs = f64 ? sizeof(double) : sizeof(float);
+  const int p = t->p, Kp = t->Kp;
+  int* bad = alloc_n<int>(a, 1);
+  GB_CK(cudaMemsetAsync(bad, 0, sizeof(int), s));
+  // M2M / L2L: 8 octants, child offset (c_C - c_P)/R_P = (bx, by, bz) - 1/2
+  double hgeom[8 * 5];
+  for (int o = 0; o < 8; ++o) {
+    hgeom[5 * o + 0] = ((o >> 2) & 1) - 0.5;
+    hgeom[5 * o + 1] = ((o >> 1) & 1) - 0.5;
+    hgeom[5 * o + 2] = (o & 1) - 0.5;
+    hgeom[5 * o + 3] = 1.0;
+    hgeom[5 * o + 4] = 1.0;
+  }
+  double* g8 = alloc_n<double>(a, 40);
+  GB_CK(cudaMemcpyAsync(g8, hgeom, sizeof(hgeom), cudaMemcpyHostToDevice, s));
+  t->m2m_ops = a.alloc(rs * 8 * Kp * Kp);
+  t->l2l_ops = a.alloc(rs * 8 * Kp * Kp);
+  const size_t sm_reg = sizeof(double) * 2 * (size_t)p * (p + 1) / 2;
+  const int Pt = 2 * p - 1;
+  const size_t sm_irr = sizeof(double) * 2 * (size_t)Pt * (Pt + 1) / 2;
+  if (f64) {
+    k_build_ops<double><<<8, 256, sm_reg, s>>>(kM2M, p, Kp, g8, 8, (double*)t->m2m_ops, nullptr, false, bad);
+    k_build_ops<double><<<8, 256, sm_reg, s>>>(kL2L, p, Kp, g8, 8, (double*)t->l2l_ops, nullptr, false, bad);
+  } else {
+    k_build_ops<float><<<8, 256, sm_reg, s>>>(kM2M, p, Kp, g8, 8, (float*)t->m2m_ops, nullptr, false, bad);
+    k_build_ops<float><<<8, 256, sm_reg, s>>>(kL2L, p, Kp, g8, 8, (float*)t->l2l_ops, nullptr, false, bad);
+  }
+  GB_LAUNCH("k_build_ops m2m/l2l");
+  if (t->nclass > 0) {
+    double* geom = alloc_n<double>(a, 5 * (size_t)t->nclass);
+    k_m2l_geom<<<blocks(t->nclass), kThreads, 0, s>>>(t->class_desc, t->nclass, geom);
+    GB_LAUNCH("k_m2l_geom");
+    t->m2l_ops = a.alloc(rs * (size_t)t->nclass * Kp * Kp);
+    if (f64) {
+      k_build_ops<double><<<t->nclass, 256, sm_irr, s>>>(kM2L, p, Kp, geom, t->nclass, (double*)t->m2l_ops,
+                                                         nullptr, true, bad);
+    } else {
+      if (t->m2l_engine == 1) t->m2l_ops_lo = alloc_n<float>(a, (size_t)t->nclass * Kp * Kp);
+      k_build_ops<float><<<t->nclass, 256, sm_irr, s>>>(kM2L, p, Kp, geom, t->nclass, (float*)t->m2l_ops,
+                                                        t->m2l_ops_lo, true, bad);
+    }
+    GB_LAUNCH("k_build_ops m2l");
+    a.release(geom);
+  }
+  int hbad = 0;
+  GB_CK(cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, s));
+  GB_CK(cudaStreamSynchronize(s));
+  a.release(bad);
+  a.release(g8);
+  if (hbad) fail(FMM_ERR_RANGE, "translation operator overflows the working precision");
+}
+
+}  // namespace gbfmm

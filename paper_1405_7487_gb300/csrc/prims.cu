@@ -1,0 +1,275 @@
+// prims.cu -- error handling, workspace arena, device scan and radix sort.
+#include <cstdio>
+#include <cstring>
+#include <atomic>
+
+#include "common.cuh"
+
+namespace gbfmm {
+
+void fail(int code, const char* what) { throw Error{code, what ? what : ""}; }
+
+std::atomic<long long> g_launches{0};
+
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+void check_cuda(cudaError_t e, const char* what) {
+  if (e == cudaSuccess) return;
+  cudaGetLastError();  // clear a sticky launch error of this thread
+  if (e == cudaErrorMemoryAllocation) fail(FMM_ERR_OOM, what);
+  fail(FMM_ERR_CUDA, what);
+}
+
+void* Arena::alloc(size_t n) {
+  void* p = nullptr;
+  if (has_user) {
+    p = user.alloc(n, (fmm_stream)stream, user.ctx);
+    if (!p) fail(FMM_ERR_OOM, "user allocator");
+  } else {
+    cudaError_t e = cudaMallocAsync(&p, n, stream);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      fail(e == cudaErrorMemoryAllocation ? FMM_ERR_OOM : FMM_ERR_CUDA, "cudaMallocAsync");
+    }
+  }
+  live.push_back(p);
+  bytes += n;
+  return p;
+}
+
+void Arena::release(void* p) {
+  if (!p) return;
+  for (size_t i = 0; i < live.size(); ++i)
+    if (live[i] == p) {
+      live[i] = live.back();
+      live.pop_back();
+      break;
+    }
+  if (has_user) user.free(p, (fmm_stream)stream, user.ctx);
+  else cudaFreeAsync(p, stream);
+}
+
+void Arena::release_all() {
+  for (void* p : live) {
+    if (has_user) user.free(p, (fmm_stream)stream, user.ctx);
+    else cudaFreeAsync(p, stream);
+  }
+  live.clear();
+  bytes = 0;
+}
+
+// ------------------------------------------------------------------- scan
+namespace {
+
+constexpr int kScanThreads = 256;
+constexpr int kScanItems = 8;
+constexpr int kScanTile = kScanThreads * kScanItems;
+
+// Block-wide exclusive scan of one value per thread; returns the block total.
+__device__ int64_t block_exclusive_scan(int64_t v, int64_t* total) {
+  __shared__ int64_t warp_sums[kScanThreads / 32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  int64_t x = v;
+  for (int o = 1; o < 32; o <<= 1) {
+    int64_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) warp_sums[wid] = x;
+  __syncthreads();
+  if (wid == 0) {
+    int64_t w = lane < kScanThreads / 32 ? warp_sums[lane] : 0;
+    int64_t s = w;
+    for (int o = 1; o < 32; o <<= 1) {
+      int64_t y = __shfl_up_sync(0xffffffffu, s, o);
+      if (lane >= o) s += y;
+    }
+    if (lane < kScanThreads / 32) warp_sums[lane] = s - w;
+    if (lane == kScanThreads / 32 - 1) *total = s;
+  }
+  __syncthreads();
+  int64_t r = warp_sums[wid] + x - v;
+  __syncthreads();
+  return r;
+}
+
+__global__ void k_block_sums(const int64_t* __restrict__ d, int64_t n, int64_t* __restrict__ sums) {
+  const int64_t base = (int64_t)blockIdx.x * kScanTile;
+  int64_t s = 0;
+  for (int i = threadIdx.x; i < kScanTile; i += kScanThreads) {
+    int64_t k = base + i;
+    if (k < n) s += d[k];
+  }
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  __shared__ int64_t ws[kScanThreads / 32];
+  if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int64_t t = 0;
+    for (int w = 0; w < kScanThreads / 32; ++w) t += ws[w];
+    sums[blockIdx.x] = t;
+  }
+}
+
+// In-place exclusive scan of one tile per block, plus the block's offset.
+__global__ void k_scan_apply(int64_t* __restrict__ d, int64_t n, const int64_t* __restrict__ offs,
+                             int64_t* __restrict__ total) {
+  const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
+  int64_t v[kScanItems];
+  int64_t s = 0;
+#pragma unroll
+  for (int i = 0; i < kScanItems; ++i) {
+    v[i] = (base + i < n) ? d[base + i] : 0;
+    s += v[i];
+  }
+  __shared__ int64_t btotal;
+  int64_t ex = block_exclusive_scan(s, &btotal);
+  int64_t run = ex + (offs ? offs[blockIdx.x] : 0);
+#pragma unroll
+  for (int i = 0; i < kScanItems; ++i) {
+    if (base + i < n) d[base + i] = run;
+    run += v[i];
+  }
+  if (total && threadIdx.x == 0) *total = btotal;
+}
+
+void scan_rec(Arena& a, int64_t* d, int64_t n, int64_t* total, cudaStream_t s) {
+  if (n <= 0) {
+    if (total) GB_CK(cudaMemsetAsync(total, 0, sizeof(int64_t), s));
+    return;
+  }
+  if (n <= kScanTile) {
+    k_scan_apply<<<1, kScanThreads, 0, s>>>(d, n, nullptr, total);
+    GB_LAUNCH("k_scan_apply");
+    return;
+  }
+  const int64_t nb = (n + kScanTile - 1) / kScanTile;
+  int64_t* sums = alloc_n<int64_t>(a, nb);
+  k_block_sums<<<(unsigned)nb, kScanThreads, 0, s>>>(d, n, sums);
+  GB_LAUNCH("k_block_sums");
+  scan_rec(a, sums, nb, total, s);
+  k_scan_apply<<<(unsigned)nb, kScanThreads, 0, s>>>(d, n, sums, nullptr);
+  GB_LAUNCH("k_scan_apply");
+  a.release(sums);
+}
+
+}  // namespace
+
+void scan_exclusive_i64(Arena& a, int64_t* d, int64_t n, cudaStream_t s) {
+  scan_rec(a, d, n, nullptr, s);
+}
+
+int64_t scan_exclusive_i64_total(Arena& a, int64_t* d, int64_t n, cudaStream_t s) {
+  int64_t* tot = alloc_n<int64_t>(a, 1);
+  scan_rec(a, d, n, tot, s);
+  int64_t h = 0;
+  GB_CK(cudaMemcpyAsync(&h, tot, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  GB_CK(cudaStreamSynchronize(s));
+  a.release(tot);
+  return h;
+}
+
+// ------------------------------------------------------------- radix sort
+// LSD radix sort, 8-bit digits.  Pass: per-tile digit histograms (digit-major
+// so that one exclusive scan gives every tile's output base per digit, in
+// stable order), then a stable scatter in which each tile is consumed in
+// rounds of 256 keys, ranked within the round by warp match and a per-warp
+// digit count prefix.
+namespace {
+
+constexpr int kSortThreads = 256;
+constexpr int kSortRounds = 8;
+constexpr int kSortTile = kSortThreads * kSortRounds;
+constexpr int kRadix = 256;
+
+__global__ void k_rs_hist(const uint64_t* __restrict__ keys, int64_t n, int shift, int ntile,
+                          int64_t* __restrict__ counts) {
+  __shared__ int h[kRadix];
+  h[threadIdx.x] = 0;
+  __syncthreads();
+  const int64_t base = (int64_t)blockIdx.x * kSortTile;
+  for (int i = threadIdx.x; i < kSortTile; i += kSortThreads) {
+    int64_t k = base + i;
+    if (k < n) atomicAdd(&h[(keys[k] >> shift) & 0xff], 1);
+  }
+  __syncthreads();
+  counts[(int64_t)threadIdx.x * ntile + blockIdx.x] = h[threadIdx.x];
+}
+
+__global__ void k_rs_scatter(const uint64_t* __restrict__ kin, const int32_t* __restrict__ vin,
+                             uint64_t* __restrict__ kout, int32_t* __restrict__ vout, int64_t n,
+                             int shift, int ntile, const int64_t* __restrict__ offs) {
+  __shared__ int64_t base_d[kRadix];
+  __shared__ int wcnt[kSortThreads / 32][kRadix];
+  __shared__ int rtot[kRadix];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  base_d[threadIdx.x] = offs[(int64_t)threadIdx.x * ntile + blockIdx.x];
+  const int64_t tbase = (int64_t)blockIdx.x * kSortTile;
+  for (int r = 0; r < kSortRounds; ++r) {
+    for (int w = 0; w < kSortThreads / 32; ++w) wcnt[w][threadIdx.x] = 0;
+    __syncthreads();
+    const int64_t k = tbase + (int64_t)r * kSortThreads + threadIdx.x;
+    const bool valid = k < n;
+    uint64_t key = valid ? kin[k] : 0;
+    int32_t val = (valid && vin) ? vin[k] : 0;
+    const int d = valid ? (int)((key >> shift) & 0xff) : kRadix;
+    const unsigned peers = __match_any_sync(0xffffffffu, d);
+    const int rank = __popc(peers & ((1u << lane) - 1u));
+    const int leader = __ffs(peers) - 1;
+    if (valid && lane == leader) wcnt[wid][d] = __popc(peers);
+    __syncthreads();
+    {
+      int run = 0;
+      for (int w = 0; w < kSortThreads / 32; ++w) {
+        int c = wcnt[w][threadIdx.x];
+        wcnt[w][threadIdx.x] = run;
+        run += c;
+      }
+      rtot[threadIdx.x] = run;
+    }
+    __syncthreads();
+    if (valid) {
+      const int64_t pos = base_d[d] + wcnt[wid][d] + rank;
+      kout[pos] = key;
+      if (vout) vout[pos] = val;
+    }
+    __syncthreads();
+    base_d[threadIdx.x] += rtot[threadIdx.x];
+    __syncthreads();
+  }
+}
+
+void sort_impl(Arena& a, uint64_t*& keys, int32_t** vals, int64_t n, int bits, cudaStream_t s) {
+  if (n <= 1 || bits <= 0) return;
+  const int ntile = (int)((n + kSortTile - 1) / kSortTile);
+  uint64_t* k2 = alloc_n<uint64_t>(a, n);
+  int32_t* v2 = vals ? alloc_n<int32_t>(a, n) : nullptr;
+  int64_t* counts = alloc_n<int64_t>(a, (size_t)kRadix * ntile);
+  for (int shift = 0; shift < bits; shift += 8) {
+    k_rs_hist<<<ntile, kSortThreads, 0, s>>>(keys, n, shift, ntile, counts);
+    GB_LAUNCH("k_rs_hist");
+    scan_exclusive_i64(a, counts, (int64_t)kRadix * ntile, s);
+    k_rs_scatter<<<ntile, kSortThreads, 0, s>>>(keys, vals ? *vals : nullptr, k2, v2, n, shift,
+                                                ntile, counts);
+    GB_LAUNCH("k_rs_scatter");
+    std::swap(keys, k2);
+    if (vals) std::swap(*vals, v2);
+  }
+  a.release(counts);
+  a.release(k2);
+  if (v2) a.release(v2);
+}
+
+}  // namespace
+
+void radix_sort_pairs(Arena& a, uint64_t*& keys, int32_t*& vals, int64_t n, int bits,
+                      cudaStream_t s) {
+  sort_impl(a, keys, &vals, n, bits, s);
+}
+
+void radix_sort_keys(Arena& a, uint64_t*& keys, int64_t n, int bits, cudaStream_t s) {
+  sort_impl(a, keys, nullptr, n, bits, s);
+}
+
+}  // namespace gbfmm
+
+extern "C" int64_t fmm_launch_count(void) { return (int64_t)gbfmm::g_launches.load(); }

@@ -1,0 +1,331 @@
+// traverse.cu -- dual tree traversal into explicit P2P and M2L lists.
+//
+// The paper's ExaFMM finds M2L and P2P interactions by a dual tree traversal
+// (Dehnen) without forming lists (Sec. II.C).  On the GPU the traversal runs
+// breadth first over a frontier of unordered cell pairs and records the
+// interactions as lists, which the evaluation and the backward pass reuse.
+// Rules for a pair {A, B}:
+//   A == B: a leaf takes P2P with itself; otherwise every unordered pair of
+//           its children joins the next frontier.
+//   MAC  theta |c_A - c_B| > R_A + R_B  (the bigger the cells, the further
+//           apart they must be; Sec. II.A): M2L both ways.
+//   two leaves: P2P both ways.
+//   otherwise: split the larger cell (smaller level) unless it is a leaf, in
+//           which case split the other; equal sizes, both split-table: every
+//           (child of A, child of B) pair.
+// The MAC is evaluated on exact integers (cube centres and radii in units of
+// H / 2^21), so the lists are reproducible bit for bit.
+#include <algorithm>
+
+#include "common.cuh"
+
+namespace gbfmm {
+namespace {
+
+constexpr int kThreads = 256;
+inline unsigned blocks(int64_t n) { return (unsigned)((n + kThreads - 1) / kThreads); }
+
+struct CellView {
+  const int32_t *level, *ix, *iy, *iz, *cbeg, *nch;
+};
+
+__device__ __forceinline__ bool mac(const CellView& c, int A, int B, double theta2, int circ) {
+  const int la = c.level[A], lb = c.level[B];
+  const int64_t dx = ((2ll * c.ix[A] + 1) << (kMaxLevel - la)) - ((2ll * c.ix[B] + 1) << (kMaxLevel - lb));
+  const int64_t dy = ((2ll * c.iy[A] + 1) << (kMaxLevel - la)) - ((2ll * c.iy[B] + 1) << (kMaxLevel - lb));
+  const int64_t dz = ((2ll * c.iz[A] + 1) << (kMaxLevel - la)) - ((2ll * c.iz[B] + 1) << (kMaxLevel - lb));
+  const int64_t D2 = dx * dx + dy * dy + dz * dz;
+  const int64_t rs = (1ll << (kMaxLevel - la)) + (1ll << (kMaxLevel - lb));
+  int64_t S2 = rs * rs;
+  if (circ) S2 *= 3;
+  return __dmul_rn(theta2, (double)D2) > (double)S2;
+}
+
+// Decision for one pair: kind 0 = self leaf P2P, 1 = self split, 2 = M2L,
+// 3 = P2P both ways, 4 = split A, 5 = split B, 6 = split both.
+__device__ __forceinline__ int decide(const CellView& c, int A, int B, double theta2, int circ) {
+  if (A == B) return c.nch[A] == 0 ? 0 : 1;
+  if (mac(c, A, B, theta2, circ)) return 2;
+  const bool la = c.nch[A] == 0, lb = c.nch[B] == 0;
+  if (la && lb) return 3;
+  if (c.level[A] < c.level[B]) return la ? 5 : 4;
+  if (c.level[B] < c.level[A]) return lb ? 4 : 5;
+  if (!la && !lb) return 6;
+  return la ? 5 : 4;
+}
+
+__global__ void k_trav_count(const int2* __restrict__ fr, int64_t n, CellView c, double theta2,
+                             int circ, int64_t* __restrict__ cnt) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int A = fr[i].x, B = fr[i].y;
+  const int k = decide(c, A, B, theta2, circ);
+  int64_t nn = 0, nm = 0, np = 0;
+  switch (k) {
+    case 0: np = 1; break;
+    case 1: nn = (int64_t)c.nch[A] * (c.nch[A] + 1) / 2; break;
+    case 2: nm = 2; break;
+    case 3: np = 2; break;
+    case 4: nn = c.nch[A]; break;
+    case 5: nn = c.nch[B]; break;
+    default: nn = (int64_t)c.nch[A] * c.nch[B]; break;
+  }
+  cnt[i] = nn;
+  cnt[n + i] = nm;
+  cnt[2 * n + i] = np;
+}
+
+__device__ __forceinline__ uint64_t pair_key(int tgt, int src) {
+  return ((uint64_t)(uint32_t)tgt << 32) | (uint32_t)src;
+}
+
+__global__ void k_trav_write(const int2* __restrict__ fr, int64_t n, CellView c, double theta2,
+                             int circ, const int64_t* __restrict__ off, int64_t base_m,
+                             int64_t base_p, int2* __restrict__ next, uint64_t* __restrict__ m2l,
+                             int64_t m2l_at, uint64_t* __restrict__ p2p, int64_t p2p_at) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int A = fr[i].x, B = fr[i].y;
+  const int k = decide(c, A, B, theta2, circ);
+  int64_t o = off[i];
+  switch (k) {
+    case 0: p2p[p2p_at + off[2 * n + i] - base_p] = pair_key(A, A); break;
+    case 1: {
+      const int a0 = c.cbeg[A], na = c.nch[A];
+      for (int x = 0; x < na; ++x)
+        for (int y = x; y < na; ++y) next[o++] = make_int2(a0 + x, a0 + y);
+      break;
+    }
+    case 2: {
+      const int64_t m = m2l_at + off[n + i] - base_m;
+      m2l[m] = pair_key(B, A);
+      m2l[m + 1] = pair_key(A, B);
+      break;
+    }
+    case 3: {
+      const int64_t m = p2p_at + off[2 * n + i] - base_p;
+      p2p[m] = pair_key(B, A);
+      p2p[m + 1] = pair_key(A, B);
+      break;
+    }
+    case 4: {
+      const int a0 = c.cbeg[A], na = c.nch[A];
+      for (int x = 0; x < na; ++x) next[o++] = make_int2(a0 + x, B);
+      break;
+    }
+    case 5: {
+      const int b0 = c.cbeg[B], nb = c.nch[B];
+      for (int y = 0; y < nb; ++y) next[o++] = make_int2(A, b0 + y);
+      break;
+    }
+    default: {
+      const int a0 = c.cbeg[A], na = c.nch[A], b0 = c.cbeg[B], nb = c.nch[B];
+      for (int x = 0; x < na; ++x)
+        for (int y = 0; y < nb; ++y) next[o++] = make_int2(a0 + x, b0 + y);
+      break;
+    }
+  }
+}
+
+__global__ void k_unpack_pairs(const uint64_t* __restrict__ k, int64_t n, int32_t* __restrict__ tgt,
+                               int32_t* __restrict__ src) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  tgt[i] = (int32_t)(k[i] >> 32);
+  src[i] = (int32_t)(k[i] & 0xffffffffu);
+}
+
+// P2P source ranges per target leaf: key (leaf index, body_begin of source),
+// self pairs dropped (the kernel treats a leaf's own bodies separately).
+__global__ void k_p2p_range_keys(const int32_t* __restrict__ tgt, const int32_t* __restrict__ src,
+                                 int64_t n, const int32_t* __restrict__ leaf_of,
+                                 const int32_t* __restrict__ bbeg, uint64_t* __restrict__ key,
+                                 int32_t* __restrict__ val, unsigned long long* __restrict__ pairs,
+                                 const int32_t* __restrict__ bend) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int t = tgt[i], s = src[i];
+  const int64_t nt = bend[t] - bbeg[t], ns = bend[s] - bbeg[s];
+  atomicAdd(pairs, (unsigned long long)(nt * ns));
+  if (t == s) {
+    key[i] = ~0ull;  // sorts last, ignored
+    val[i] = -1;
+    return;
+  }
+  key[i] = ((uint64_t)(uint32_t)leaf_of[t] << 32) | (uint32_t)bbeg[s];
+  val[i] = s;
+}
+
+// Position of the first key >= (leaf << 32) for every leaf (and the end).
+__global__ void k_leaf_entry_ptr(const uint64_t* __restrict__ key, int64_t n, int nleaf,
+                                 int64_t* __restrict__ ptr) {
+  const int l = blockIdx.x * blockDim.x + threadIdx.x;
+  if (l > nleaf) return;
+  const uint64_t want = (uint64_t)(uint32_t)l << 32;
+  int64_t lo = 0, hi = n;
+  while (lo < hi) {
+    int64_t mid = (lo + hi) >> 1;
+    if (key[mid] < want) lo = mid + 1;
+    else hi = mid;
+  }
+  ptr[l] = lo;
+}
+
+// Merge adjacent body ranges of one target leaf; count pass (out == null)
+// or write pass.
+__global__ void k_merge_ranges(const int64_t* __restrict__ eptr, const int32_t* __restrict__ val,
+                               const int32_t* __restrict__ bbeg, const int32_t* __restrict__ bend,
+                               int nleaf, int64_t* __restrict__ count,
+                               const int64_t* __restrict__ out_off, int2* __restrict__ out) {
+  const int l = blockIdx.x * blockDim.x + threadIdx.x;
+  if (l >= nleaf) return;
+  const int64_t e0 = eptr[l], e1 = eptr[l + 1];
+  int64_t m = 0;
+  int cb = -1, ce = -1;
+  int64_t o = out ? out_off[l] : 0;
+  for (int64_t e = e0; e < e1; ++e) {
+    const int s = val[e];
+    const int b = bbeg[s], en = bend[s];
+    if (cb >= 0 && b == ce) {
+      ce = en;
+    } else {
+      if (cb >= 0) {
+        if (out) out[o + m] = make_int2(cb, ce);
+        ++m;
+      }
+      cb = b;
+      ce = en;
+    }
+  }
+  if (cb >= 0) {
+    if (out) out[o + m] = make_int2(cb, ce);
+    ++m;
+  }
+  if (count) count[l] = m;
+}
+
+__global__ void k_i64_to_i32(const int64_t* __restrict__ a, int64_t n, int32_t* __restrict__ b) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) b[i] = (int32_t)a[i];
+}
+
+int bits_for(int64_t v) {
+  int b = 0;
+  while (b < 63 && (1ll << b) <= v) ++b;
+  return b;
+}
+
+}  // namespace
+
+void build_lists(fmm_tree* t) {
+  Arena& a = t->arena;
+  cudaStream_t s = t->stream;
+  CellView cv{t->c.level, t->c.ix, t->c.iy, t->c.iz, t->c.cbeg, t->c.nch};
+  const double theta2 = t->theta * t->theta;
+  const int circ = (t->flags & FMM_FLAG_CIRCUMSCRIBED) ? 1 : 0;
+
+  int64_t cap_m = std::max<int64_t>(1024, 64 * (int64_t)t->ncell);
+  int64_t cap_p = std::max<int64_t>(1024, 32 * (int64_t)t->nleaf);
+  uint64_t* m2l = alloc_n<uint64_t>(a, cap_m);
+  uint64_t* p2p = alloc_n<uint64_t>(a, cap_p);
+  int64_t nm = 0, np = 0;
+
+  int64_t nf = 1;
+  int2* fr = alloc_n<int2>(a, 1);
+  {
+    int2 h = make_int2(0, 0);
+    GB_CK(cudaMemcpyAsync(fr, &h, sizeof(int2), cudaMemcpyHostToDevice, s));
+  }
+  while (nf > 0) {
+    int64_t* cnt = alloc_n<int64_t>(a, 3 * nf);
+    k_trav_count<<<blocks(nf), kThreads, 0, s>>>(fr, nf, cv, theta2, circ, cnt);
+    GB_LAUNCH("k_trav_count");
+    // one scan over the three count segments; segment totals read back
+    int64_t* scanned = cnt;
+    const int64_t total = scan_exclusive_i64_total(a, scanned, 3 * nf, s);
+    int64_t seg[2];
+    GB_CK(cudaMemcpyAsync(&seg[0], scanned + nf, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    GB_CK(cudaMemcpyAsync(&seg[1], scanned + 2 * nf, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    GB_CK(cudaStreamSynchronize(s));
+    const int64_t n_next = seg[0], n_m = seg[1] - seg[0], n_p = total - seg[1];
+    auto grow = [&](uint64_t*& buf, int64_t& cap, int64_t used, int64_t need) {
+      if (used + need <= cap) return;
+      int64_t nc = std::max(2 * cap, used + need);
+      uint64_t* nb = alloc_n<uint64_t>(a, nc);
+      GB_CK(cudaMemcpyAsync(nb, buf, sizeof(uint64_t) * used, cudaMemcpyDeviceToDevice, s));
+      a.release(buf);
+      buf = nb;
+      cap = nc;
+    };
+    grow(m2l, cap_m, nm, n_m);
+    grow(p2p, cap_p, np, n_p);
+    int2* next = alloc_n<int2>(a, n_next);
+    k_trav_write<<<blocks(nf), kThreads, 0, s>>>(fr, nf, cv, theta2, circ, scanned, seg[0], seg[1],
+                                                 next, m2l, nm, p2p, np);
+    GB_LAUNCH("k_trav_write");
+    nm += n_m;
+    np += n_p;
+    a.release(cnt);
+    a.release(fr);
+    fr = next;
+    nf = n_next;
+  }
+  a.release(fr);
+
+  // --- sort the directed pairs by (target, source)
+  const int cbits = bits_for(t->ncell);
+  radix_sort_keys(a, m2l, nm, 32 + cbits, s);
+  radix_sort_keys(a, p2p, np, 32 + cbits, s);
+  t->n_m2l = nm;
+  t->n_p2p = np;
+  t->m2l_tgt = alloc_n<int32_t>(a, nm);
+  t->m2l_src = alloc_n<int32_t>(a, nm);
+  t->p2p_tgt = alloc_n<int32_t>(a, np);
+  t->p2p_src = alloc_n<int32_t>(a, np);
+  if (nm) {
+    k_unpack_pairs<<<blocks(nm), kThreads, 0, s>>>(m2l, nm, t->m2l_tgt, t->m2l_src);
+    GB_LAUNCH("k_unpack_pairs");
+  }
+  k_unpack_pairs<<<blocks(np), kThreads, 0, s>>>(p2p, np, t->p2p_tgt, t->p2p_src);
+  GB_LAUNCH("k_unpack_pairs");
+  a.release(m2l);
+  a.release(p2p);
+
+  // --- P2P body ranges per target leaf, merged where contiguous
+  uint64_t* rkey = alloc_n<uint64_t>(a, np);
+  int32_t* rval = alloc_n<int32_t>(a, np);
+  unsigned long long* d_pairs = alloc_n<unsigned long long>(a, 1);
+  GB_CK(cudaMemsetAsync(d_pairs, 0, sizeof(unsigned long long), s));
+  k_p2p_range_keys<<<blocks(np), kThreads, 0, s>>>(t->p2p_tgt, t->p2p_src, np, t->leaf_of_cell,
+                                                   t->c.bbeg, rkey, rval, d_pairs, t->c.bend);
+  GB_LAUNCH("k_p2p_range_keys");
+  radix_sort_pairs(a, rkey, rval, np, 64, s);
+  int64_t* eptr = alloc_n<int64_t>(a, t->nleaf + 1);
+  k_leaf_entry_ptr<<<blocks(t->nleaf + 1), kThreads, 0, s>>>(rkey, np, t->nleaf, eptr);
+  GB_LAUNCH("k_leaf_entry_ptr");
+  // the self entries (key ~0) sort last; cap the last leaf at the non-self count
+  int64_t* rcount = alloc_n<int64_t>(a, t->nleaf + 1);
+  GB_CK(cudaMemsetAsync(rcount, 0, sizeof(int64_t) * (t->nleaf + 1), s));
+  k_merge_ranges<<<blocks(t->nleaf), kThreads, 0, s>>>(eptr, rval, t->c.bbeg, t->c.bend, t->nleaf,
+                                                       rcount, nullptr, nullptr);
+  GB_LAUNCH("k_merge_ranges");
+  t->n_p2p_ranges = scan_exclusive_i64_total(a, rcount, t->nleaf + 1, s);
+  t->p2p_ranges = alloc_n<int2>(a, t->n_p2p_ranges);
+  k_merge_ranges<<<blocks(t->nleaf), kThreads, 0, s>>>(eptr, rval, t->c.bbeg, t->c.bend, t->nleaf,
+                                                       nullptr, rcount, t->p2p_ranges);
+  GB_LAUNCH("k_merge_ranges");
+  t->p2p_rptr = alloc_n<int32_t>(a, t->nleaf + 1);
+  k_i64_to_i32<<<blocks(t->nleaf + 1), kThreads, 0, s>>>(rcount, t->nleaf + 1, t->p2p_rptr);
+  GB_LAUNCH("k_i64_to_i32");
+  unsigned long long hp = 0;
+  GB_CK(cudaMemcpyAsync(&hp, d_pairs, sizeof(hp), cudaMemcpyDeviceToHost, s));
+  GB_CK(cudaStreamSynchronize(s));
+  t->p2p_body_pairs = (int64_t)hp - t->N;
+  a.release(d_pairs);
+  a.release(rkey);
+  a.release(rval);
+  a.release(eptr);
+  a.release(rcount);
+}
+
+}  // namespace gbfmm

@@ -1,0 +1,386 @@
+// tree.cu -- bounding cube, Morton keys, sort and level-wise octree
+// construction (Sec. II.B: three key bits per level, 21 levels in 64 bits;
+// Sec. II.C: a local tree built from the local bounding box; Sec. III.A:
+// N_crit is the maximum number of bodies per leaf).
+#include <algorithm>
+#include <cmath>
+
+#include "common.cuh"
+
+namespace gbfmm {
+namespace {
+
+constexpr int kThreads = 256;
+
+template <class R>
+struct Body4;
+template <>
+struct Body4<float> {
+  using type = float4;
+};
+template <>
+struct Body4<double> {
+  using type = double4_32a;
+};
+
+__device__ __forceinline__ bool finite4(double a, double b, double c, double d) {
+  return isfinite(a) && isfinite(b) && isfinite(c) && isfinite(d);
+}
+
+// Per-block min/max of each axis (exact: the inputs are widened to double)
+// and a non-finite flag.
+template <class R>
+__global__ void k_bbox_partial(const R* __restrict__ xyzq, int64_t n, double* __restrict__ part) {
+  double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+  double bad = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    double x = xyzq[4 * i], y = xyzq[4 * i + 1], z = xyzq[4 * i + 2], q = xyzq[4 * i + 3];
+    if (!finite4(x, y, z, q)) {
+      bad = 1.0;
+      continue;
+    }
+    lo[0] = fmin(lo[0], x); hi[0] = fmax(hi[0], x);
+    lo[1] = fmin(lo[1], y); hi[1] = fmax(hi[1], y);
+    lo[2] = fmin(lo[2], z); hi[2] = fmax(hi[2], z);
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    for (int a = 0; a < 3; ++a) {
+      lo[a] = fmin(lo[a], __shfl_down_sync(0xffffffffu, lo[a], o));
+      hi[a] = fmax(hi[a], __shfl_down_sync(0xffffffffu, hi[a], o));
+    }
+    bad = fmax(bad, __shfl_down_sync(0xffffffffu, bad, o));
+  }
+  __shared__ double s[kThreads / 32][7];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (lane == 0) {
+    for (int a = 0; a < 3; ++a) {
+      s[w][a] = lo[a];
+      s[w][3 + a] = hi[a];
+    }
+    s[w][6] = bad;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double r[7];
+    for (int k = 0; k < 7; ++k) r[k] = s[0][k];
+    for (int ww = 1; ww < kThreads / 32; ++ww) {
+      for (int a = 0; a < 3; ++a) {
+        r[a] = fmin(r[a], s[ww][a]);
+        r[3 + a] = fmax(r[3 + a], s[ww][3 + a]);
+      }
+      r[6] = fmax(r[6], s[ww][6]);
+    }
+    for (int k = 0; k < 7; ++k) part[7 * blockIdx.x + k] = r[k];
+  }
+}
+
+// Root cube: centre (lo+hi)/2, half side H = max_axis (hi-lo)/2 * (1 + 2^-20)
+// (H = 0.5 if all bodies coincide), corner = centre - H.  Explicitly rounded
+// double operations: no fused multiply-add may change the keys.
+__global__ void k_bbox_final(const double* __restrict__ part, int nb, double* __restrict__ root,
+                             int* __restrict__ nonfinite) {
+  if (threadIdx.x != 0) return;
+  double r[7];
+  for (int k = 0; k < 7; ++k) r[k] = part[k];
+  for (int b = 1; b < nb; ++b) {
+    for (int a = 0; a < 3; ++a) {
+      r[a] = fmin(r[a], part[7 * b + a]);
+      r[3 + a] = fmax(r[3 + a], part[7 * b + 3 + a]);
+    }
+    r[6] = fmax(r[6], part[7 * b + 6]);
+  }
+  *nonfinite = r[6] != 0.0;
+  double h = 0.0;
+  for (int a = 0; a < 3; ++a) {
+    root[a] = r[a];
+    root[3 + a] = r[3 + a];
+    root[6 + a] = __dmul_rn(__dadd_rn(r[a], r[3 + a]), 0.5);
+    h = fmax(h, __dmul_rn(__dsub_rn(r[3 + a], r[a]), 0.5));
+  }
+  double H = __dmul_rn(h, 1.0 + 0x1p-20);
+  if (H == 0.0) H = 0.5;
+  root[9] = H;
+  for (int a = 0; a < 3; ++a) root[10 + a] = __dsub_rn(root[6 + a], H);
+}
+
+__device__ __forceinline__ uint64_t spread_bits(uint64_t v) {
+  v &= 0x1fffffull;
+  v = (v | (v << 32)) & 0x1f00000000ffffull;
+  v = (v | (v << 16)) & 0x1f0000ff0000ffull;
+  v = (v | (v << 8)) & 0x100f00f00f00f00full;
+  v = (v | (v << 4)) & 0x10c30c30c30c30c3ull;
+  v = (v | (v << 2)) & 0x1249249249249249ull;
+  return v;
+}
+
+// Integer coordinate k = min(floor((x - corner) / (2H) * 2^21), 2^21 - 1) per
+// axis, interleaved x-major into a 63-bit key.
+template <class R>
+__global__ void k_keys(const R* __restrict__ xyzq, int64_t n, const double* __restrict__ root,
+                       uint64_t* __restrict__ keys, int32_t* __restrict__ idx) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double side = __dadd_rn(root[9], root[9]);
+  uint64_t key = 0;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    double d = __dsub_rn((double)xyzq[4 * i + a], root[10 + a]);
+    double s = __dmul_rn(__ddiv_rn(d, side), 2097152.0);
+    double f = floor(s);
+    int64_t k = (int64_t)f;
+    k = k < 0 ? 0 : (k > 2097151 ? 2097151 : k);
+    key |= spread_bits((uint64_t)k) << (2 - a);
+  }
+  keys[i] = key;
+  idx[i] = (int32_t)i;
+}
+
+template <class R>
+__global__ void k_gather_bodies(const R* __restrict__ xyzq, const int32_t* __restrict__ perm,
+                                int64_t n, typename Body4<R>::type* __restrict__ out) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int64_t j = perm[i];
+  typename Body4<R>::type b;
+  b.x = xyzq[4 * j];
+  b.y = xyzq[4 * j + 1];
+  b.z = xyzq[4 * j + 2];
+  b.w = xyzq[4 * j + 3];
+  out[i] = b;
+}
+
+// First position in [s, e) whose octant digit (at the given shift) is >= d.
+__device__ __forceinline__ int lower_digit(const uint64_t* __restrict__ keys, int s, int e, int shift,
+                                           int d) {
+  int lo = s, hi = e;
+  while (lo < hi) {
+    int mid = (lo + hi) >> 1;
+    if ((int)((keys[mid] >> shift) & 7ull) < d) lo = mid + 1;
+    else hi = mid;
+  }
+  return lo;
+}
+
+// Children of the cells of one level: a cell with more than ncrit bodies
+// (and below level 21) splits into its nonempty octants, in Morton order.
+__global__ void k_split_count(const uint64_t* __restrict__ keys, const int32_t* __restrict__ bbeg,
+                              const int32_t* __restrict__ bend, int ncell, int level, int ncrit,
+                              int64_t* __restrict__ nchild) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= ncell) return;
+  const int s = bbeg[c], e = bend[c];
+  int cnt = 0;
+  if (e - s > ncrit && level < kMaxLevel) {
+    const int shift = 3 * (kMaxLevel - level - 1);
+    int prev = s;
+    for (int d = 1; d <= 8; ++d) {
+      int b = d < 8 ? lower_digit(keys, s, e, shift, d) : e;
+      cnt += b > prev;
+      prev = b;
+    }
+  }
+  nchild[c] = cnt;
+}
+
+__global__ void k_split_write(const uint64_t* __restrict__ keys, const int32_t* __restrict__ bbeg,
+                              const int32_t* __restrict__ bend, const int32_t* __restrict__ ix,
+                              const int32_t* __restrict__ iy, const int32_t* __restrict__ iz,
+                              int ncell, int level, int ncrit, int first_cell, int first_child,
+                              const int64_t* __restrict__ off, int32_t* __restrict__ cbeg,
+                              int32_t* __restrict__ nch, int32_t* __restrict__ o_bbeg,
+                              int32_t* __restrict__ o_bend, int32_t* __restrict__ o_ix,
+                              int32_t* __restrict__ o_iy, int32_t* __restrict__ o_iz,
+                              int32_t* __restrict__ o_parent) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= ncell) return;
+  const int s = bbeg[c], e = bend[c];
+  int k = (int)off[c];
+  const int k0 = k;
+  if (e - s > ncrit && level < kMaxLevel) {
+    const int shift = 3 * (kMaxLevel - level - 1);
+    int prev = s;
+    for (int d = 0; d < 8; ++d) {
+      int b = d < 7 ? lower_digit(keys, s, e, shift, d + 1) : e;
+      if (b > prev) {
+        o_bbeg[k] = prev;
+        o_bend[k] = b;
+        o_ix[k] = 2 * ix[c] + ((d >> 2) & 1);
+        o_iy[k] = 2 * iy[c] + ((d >> 1) & 1);
+        o_iz[k] = 2 * iz[c] + (d & 1);
+        o_parent[k] = first_cell + c;
+        ++k;
+      }
+      prev = b;
+    }
+  }
+  cbeg[c] = k > k0 ? first_child + k0 : -1;
+  nch[c] = k - k0;
+}
+
+__global__ void k_fill_i32(int32_t* __restrict__ p, int64_t n, int32_t v) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) p[i] = v;
+}
+
+__global__ void k_leaf_flags(const int32_t* __restrict__ nch, int n, int64_t* __restrict__ f) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) f[i] = nch[i] == 0;
+}
+
+__global__ void k_leaf_compact(const int32_t* __restrict__ nch, const int64_t* __restrict__ off,
+                               int n, int32_t* __restrict__ leaves, int32_t* __restrict__ leaf_of) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  if (nch[i] == 0) {
+    leaves[off[i]] = i;
+    leaf_of[i] = (int32_t)off[i];
+  } else {
+    leaf_of[i] = -1;
+  }
+}
+
+inline unsigned blocks(int64_t n, int t = kThreads) { return (unsigned)((n + t - 1) / t); }
+
+struct LevelArrays {
+  int n = 0;
+  int32_t *bbeg, *bend, *ix, *iy, *iz, *parent, *cbeg, *nch;
+};
+
+template <class R>
+void build_tree_impl(fmm_tree* t, const R* xyzq) {
+  Arena& a = t->arena;
+  cudaStream_t s = t->stream;
+  const int64_t N = t->N;
+  // --- bounding cube
+  const int nb = (int)std::min<int64_t>(1024, (N + kThreads - 1) / kThreads);
+  double* part = alloc_n<double>(a, 7 * (size_t)nb);
+  t->d_root = alloc_n<double>(a, 13);
+  int* d_bad = alloc_n<int>(a, 1);
+  k_bbox_partial<R><<<nb, kThreads, 0, s>>>(xyzq, N, part);
+  GB_LAUNCH("k_bbox_partial");
+  k_bbox_final<<<1, 32, 0, s>>>(part, nb, t->d_root, d_bad);
+  GB_LAUNCH("k_bbox_final");
+  double hroot[13];
+  int hbad = 0;
+  GB_CK(cudaMemcpyAsync(hroot, t->d_root, sizeof(hroot), cudaMemcpyDeviceToHost, s));
+  GB_CK(cudaMemcpyAsync(&hbad, d_bad, sizeof(int), cudaMemcpyDeviceToHost, s));
+  GB_CK(cudaStreamSynchronize(s));
+  a.release(part);
+  a.release(d_bad);
+  if (hbad) fail(FMM_ERR_NONFINITE, "non-finite position or charge");
+  for (int k = 0; k < 3; ++k) {
+    t->root.lo[k] = hroot[k];
+    t->root.hi[k] = hroot[3 + k];
+    t->root.centre[k] = hroot[6 + k];
+    t->root.corner[k] = hroot[10 + k];
+  }
+  t->root.H = hroot[9];
+  // --- keys and stable sort (ties keep input order: LSD radix is stable and
+  // the initial order is the input order)
+  uint64_t* keys = alloc_n<uint64_t>(a, N);
+  int32_t* idx = alloc_n<int32_t>(a, N);
+  k_keys<R><<<blocks(N), kThreads, 0, s>>>(xyzq, N, t->d_root, keys, idx);
+  GB_LAUNCH("k_keys");
+  radix_sort_pairs(a, keys, idx, N, 63, s);
+  t->keys = keys;
+  t->perm = idx;
+  using B4 = typename Body4<R>::type;
+  B4* bodies = alloc_n<B4>(a, N);
+  k_gather_bodies<R><<<blocks(N), kThreads, 0, s>>>(xyzq, t->perm, N, bodies);
+  GB_LAUNCH("k_gather_bodies");
+  t->bodies = bodies;
+  t->work = alloc_n<B4>(a, N);
+  GB_CK(cudaMemcpyAsync(t->work, bodies, sizeof(B4) * N, cudaMemcpyDeviceToDevice, s));
+
+  // --- levels
+  std::vector<LevelArrays> lv;
+  LevelArrays root;
+  root.n = 1;
+  root.bbeg = alloc_n<int32_t>(a, 1);
+  root.bend = alloc_n<int32_t>(a, 1);
+  root.ix = alloc_n<int32_t>(a, 1);
+  root.iy = alloc_n<int32_t>(a, 1);
+  root.iz = alloc_n<int32_t>(a, 1);
+  root.parent = alloc_n<int32_t>(a, 1);
+  {
+    int32_t h[6] = {0, (int32_t)N, 0, 0, 0, -1};
+    int32_t* dst[6] = {root.bbeg, root.bend, root.ix, root.iy, root.iz, root.parent};
+    for (int k = 0; k < 6; ++k)
+      GB_CK(cudaMemcpyAsync(dst[k], &h[k], sizeof(int32_t), cudaMemcpyHostToDevice, s));
+    GB_CK(cudaStreamSynchronize(s));
+  }
+  lv.push_back(root);
+  int first = 0;
+  for (int l = 0;; ++l) {
+    LevelArrays& cur = lv[l];
+    cur.cbeg = alloc_n<int32_t>(a, cur.n);
+    cur.nch = alloc_n<int32_t>(a, cur.n);
+    int64_t* off = alloc_n<int64_t>(a, cur.n);
+    k_split_count<<<blocks(cur.n), kThreads, 0, s>>>(t->keys, cur.bbeg, cur.bend, cur.n, l, t->ncrit,
+                                                     off);
+    GB_LAUNCH("k_split_count");
+    const int64_t nnext = scan_exclusive_i64_total(a, off, cur.n, s);
+    if (nnext > 0x7fffffff - first - cur.n) fail(FMM_ERR_ARG, "too many cells");
+    LevelArrays nx;
+    nx.n = (int)nnext;
+    if (nnext > 0) {
+      nx.bbeg = alloc_n<int32_t>(a, nnext);
+      nx.bend = alloc_n<int32_t>(a, nnext);
+      nx.ix = alloc_n<int32_t>(a, nnext);
+      nx.iy = alloc_n<int32_t>(a, nnext);
+      nx.iz = alloc_n<int32_t>(a, nnext);
+      nx.parent = alloc_n<int32_t>(a, nnext);
+    }
+    k_split_write<<<blocks(cur.n), kThreads, 0, s>>>(
+        t->keys, cur.bbeg, cur.bend, cur.ix, cur.iy, cur.iz, cur.n, l, t->ncrit, first,
+        first + cur.n, off, cur.cbeg, cur.nch, nx.bbeg, nx.bend, nx.ix, nx.iy, nx.iz, nx.parent);
+    GB_LAUNCH("k_split_write");
+    a.release(off);
+    first += cur.n;
+    if (nnext == 0) break;
+    lv.push_back(nx);
+  }
+  // --- concatenate the levels (breadth-first cell order)
+  t->nlevel = (int)lv.size();
+  t->level_begin.assign(1, 0);
+  for (auto& L : lv) t->level_begin.push_back(t->level_begin.back() + L.n);
+  const int nc = t->level_begin.back();
+  t->ncell = nc;
+  Cells& c = t->c;
+  int32_t** fields[9] = {&c.level, &c.ix, &c.iy, &c.iz, &c.bbeg, &c.bend, &c.cbeg, &c.nch, &c.parent};
+  for (auto f : fields) *f = alloc_n<int32_t>(a, nc);
+  for (size_t l = 0; l < lv.size(); ++l) {
+    LevelArrays& L = lv[l];
+    const int o = t->level_begin[l];
+    k_fill_i32<<<blocks(L.n), kThreads, 0, s>>>(c.level + o, L.n, (int32_t)l);
+    GB_LAUNCH("k_fill_i32");
+    int32_t* src[8] = {L.ix, L.iy, L.iz, L.bbeg, L.bend, L.cbeg, L.nch, L.parent};
+    int32_t* dst[8] = {c.ix, c.iy, c.iz, c.bbeg, c.bend, c.cbeg, c.nch, c.parent};
+    for (int k = 0; k < 8; ++k)
+      GB_CK(cudaMemcpyAsync(dst[k] + o, src[k], sizeof(int32_t) * L.n, cudaMemcpyDeviceToDevice, s));
+  }
+  for (auto& L : lv) {
+    int32_t* all[8] = {L.ix, L.iy, L.iz, L.bbeg, L.bend, L.cbeg, L.nch, L.parent};
+    for (auto p : all) a.release(p);
+  }
+  // --- leaves
+  int64_t* flag = alloc_n<int64_t>(a, nc);
+  k_leaf_flags<<<blocks(nc), kThreads, 0, s>>>(c.nch, nc, flag);
+  GB_LAUNCH("k_leaf_flags");
+  t->nleaf = (int)scan_exclusive_i64_total(a, flag, nc, s);
+  t->leaves = alloc_n<int32_t>(a, t->nleaf);
+  t->leaf_of_cell = alloc_n<int32_t>(a, nc);
+  k_leaf_compact<<<blocks(nc), kThreads, 0, s>>>(c.nch, flag, nc, t->leaves, t->leaf_of_cell);
+  GB_LAUNCH("k_leaf_compact");
+  a.release(flag);
+}
+
+}  // namespace
+
+void build_tree(fmm_tree* t, const void* xyzq, bool f64) {
+  if (f64) build_tree_impl<double>(t, static_cast<const double*>(xyzq));
+  else build_tree_impl<float>(t, static_cast<const float*>(xyzq));
+}
+
+}  // namespace gbfmm

@@ -1,0 +1,65 @@
+"""Host-side checks of the C ABI library (no GPU needed, no compute calls)."""
+
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "gbfmm.h")
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(fmm_[a-z0-9_]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def libpath():
+    from paper_1405_7487_gb300 import build_lib
+    return build_lib.build()
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for n in ("fmm_build", "fmm_evaluate", "fmm_backward", "fmm_destroy", "fmm_get_stats", "fmm_strerror"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(libpath):
+    L = ctypes.CDLL(libpath)
+    for n in declared_functions():
+        assert hasattr(L, n), n
+
+
+def test_strerror_without_gpu(libpath):
+    L = ctypes.CDLL(libpath)
+    L.fmm_strerror.restype = ctypes.c_char_p
+    assert L.fmm_strerror(0) == b"ok"
+    assert b"argument" in L.fmm_strerror(-1)
+
+
+def test_null_arguments_rejected_before_any_gpu_work(libpath):
+    L = ctypes.CDLL(libpath)
+    h = ctypes.c_void_p()
+    assert L.fmm_build(None, ctypes.c_int64(10), 4, ctypes.c_double(0.4), 8, 0, None, None, ctypes.byref(h)) == -1
+    assert L.fmm_destroy(None) == 0
+
+
+def test_binding_fails_loudly_without_library(monkeypatch, tmp_path):
+    from paper_1405_7487_gb300 import fmm
+    monkeypatch.setattr(fmm, "LIB_PATH", str(tmp_path / "missing.so"))
+    monkeypatch.setattr(fmm, "_lib", None)
+    with pytest.raises(RuntimeError, match="missing"):
+        fmm.lib()
+
+
+def test_product_does_not_import_the_oracle():
+    pkg = os.path.join(ROOT, "paper_1405_7487_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h")):
+                txt = open(os.path.join(dirpath, f)).read()
+                assert "import oracle" not in txt and "from oracle" not in txt and "fmm_oracle" not in txt, f

@@ -285,6 +285,12 @@ def test_traversal_covers_every_pair_exactly_once(orc):
     p2p = set(zip(L["p2p_tgt"].tolist(), L["p2p_src"].tolist()))
     assert all((s, t) in p2p for t, s in p2p)
     R = c["level"]
+    # the larger cell is the one split (Dehnen): two non-leaves meeting in an
+    # M2L differ by at most one level
+    leaf = c["child_count"] == 0
+    for t, s in m2l:
+        if not leaf[t] and not leaf[s]:
+            assert abs(int(R[t]) - int(R[s])) <= 1
     for t, s in m2l:
         ct = (2 * np.array([c["ix"][t], c["iy"][t], c["iz"][t]], np.int64) + 1) << (21 - R[t])
         cs = (2 * np.array([c["ix"][s], c["iy"][s], c["iz"][s]], np.int64) + 1) << (21 - R[s])
