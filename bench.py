@@ -225,15 +225,30 @@ def run_gpu(args):
     m2l_flops = 2.0 * K * K * stats["n_m2l"]
     p2p_tf = p2p_flops / (p2p_avg * 1e-3) / 1e12
     m2l_tf = m2l_flops / (m2l_avg * 1e-3) / 1e12
+    # TF32 dense tensor peak: the measured bf16 burst x the nominal tf32/bf16
+    # ratio (1.1 / 2.25 PFLOP/s)
+    mp = measured_peaks()
+    tf32_peak_tflops = mp.get("bf16_tflops", 1900.0) * (1.1 / 2.25)
     if m2l_avg >= p2p_avg:
-        dom = {"kernel": "k_m2l_cc", "bound": "alu", "achieved": m2l_tf, "ms": m2l_avg}
+        if stats["m2l_engine"] == 1:
+            dom = {"kernel": "k_m2l_tc (+k_m2l_reduce)", "bound": "tensor", "achieved": m2l_tf, "ms": m2l_avg,
+                   "peak": tf32_peak_tflops,
+                   "peak_source": "measured bf16 dense burst (MEASURED_PEAKS.json) x 1.1/2.25 (nominal tf32/bf16)"}
+        else:
+            dom = {"kernel": "k_m2l_cc", "bound": "alu", "achieved": m2l_tf, "ms": m2l_avg,
+                   "peak": fp32_peak_tflops,
+                   "peak_source": "FP32 spec formula SMs x 128 lanes x 2 x median SM clock under load"}
     else:
-        dom = {"kernel": "k_p2p", "bound": "alu", "achieved": p2p_tf, "ms": p2p_avg}
+        dom = {"kernel": "k_p2p", "bound": "alu", "achieved": p2p_tf, "ms": p2p_avg, "peak": fp32_peak_tflops,
+               "peak_source": "FP32 spec formula SMs x 128 lanes x 2 x median SM clock under load"}
     roofline = {"bound": dom["bound"], "kernel": dom["kernel"], "achieved": round(dom["achieved"], 3),
-                "peak": round(fp32_peak_tflops, 3), "unit": "TFLOP/s",
-                "frac": round(dom["achieved"] / fp32_peak_tflops, 4), "traffic": None,
-                "peak_source": "FP32 spec formula SMs x 128 lanes x 2 x median SM clock under load",
-                "avg_launch_ms": round(dom["ms"], 4)}
+                "peak": round(dom["peak"], 3), "unit": "TFLOP/s",
+                "frac": round(dom["achieved"] / dom["peak"], 4), "traffic": None,
+                "peak_source": dom["peak_source"], "avg_launch_ms": round(dom["ms"], 4),
+                "work": "algorithmic: 2 K^2 flops per M2L pair (K = p^2), 20 flops per P2P body pair"}
+    slots = stats["n_m2l_slots"]
+    Kp = (K + 15) // 16 * 16
+    m2l_exec_flops = 3 * 2.0 * slots * Kp * Kp if stats["m2l_engine"] == 1 else 2.0 * slots * Kp * Kp
 
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -245,10 +260,13 @@ def run_gpu(args):
         "e2e": e2e, "gpu_launches": int(launches), "roofline": roofline,
         "p2p_frac_fp32_peak": round(p2p_tf / fp32_peak_tflops, 4),
         "m2l_tflops": round(m2l_tf, 3), "p2p_tflops": round(p2p_tf, 3),
+        "m2l_issued_tflops": round(m2l_exec_flops / (m2l_avg * 1e-3) / 1e12, 3),
+        "eval_only_particles_per_s": N / (stats["ms"]["eval_total"] * 1e-3),
         "err_vs_direct": {"pot": err_pot, "force": err_force, "targets": 4096},
         "phase_ms": {k: round(v, 4) for k, v in stats["ms"].items()},
         "tree": {k: stats[k] for k in ("n_cells", "n_leaves", "n_levels", "n_m2l", "n_p2p_body_pairs",
-                                       "n_m2l_classes", "m2l_engine")},
+                                       "n_m2l_classes", "n_m2l_tiles", "n_m2l_slots", "m2l_engine",
+                                       "workspace_bytes", "device_errors")},
         "clocks": clk,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -96,6 +96,8 @@ typedef struct {
   int32_t m2l_engine;        /* 0 CUDA cores, 1 tensor cores (tcgen05, 3xTF32) */
   int64_t workspace_bytes;   /* device bytes held by the tree */
   int32_t evaluations;       /* fmm_evaluate calls on this tree */
+  int32_t device_errors;     /* nonzero if a kernel's bounded wait gave up (the
+                                results of that pass are not valid) */
   float ms[FMM_PH_COUNT];    /* last evaluate/build phase times (FMM_FLAG_TIMING) */
 } fmm_stats;
 
@@ -190,6 +192,10 @@ int fmm_get_stats(const fmm_tree* t, fmm_stats* out);
 /* Releases the tree and its workspace (stream-ordered on the build stream).
  * NULL is accepted. */
 int fmm_destroy(fmm_tree* t);
+
+/* host: description of the last failure in the calling thread (the failing
+ * step and, for CUDA failures, the runtime's error name); empty if none. */
+const char* fmm_last_error(void);
 
 /* host: static string naming a return code. */
 const char* fmm_strerror(int code);

@@ -1,7 +1,9 @@
 // api.cu -- the C ABI (gbfmm.h): argument checks, the tree handle, and the
 // order of the passes of one evaluation (Sec. II.A / II.C: upward pass
 // P2M -> M2M, then M2L, downward pass L2L -> L2P; P2P alongside).
+#include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 
@@ -35,7 +37,7 @@ void create_tree(fmm_tree* t, const R* xyzq) {
   t->precision = f64 ? 64 : 32;
   t->K = t->p * t->p;
   t->Kp = (t->K + 15) / 16 * 16;
-  t->m2l_engine = 0;
+  t->m2l_engine = (!f64 && !(t->flags & FMM_FLAG_M2L_CUDA_CORE)) ? 1 : 0;
   GB_CK(cudaStreamCreateWithFlags(&t->side, cudaStreamNonBlocking));
   GB_CK(cudaEventCreateWithFlags(&t->fork, cudaEventDisableTiming));
   GB_CK(cudaEventCreateWithFlags(&t->join, cudaEventDisableTiming));
@@ -55,6 +57,14 @@ void create_tree(fmm_tree* t, const R* xyzq) {
   t->near = a.alloc(rs * 4 * (size_t)t->N);
   t->grad_q = a.alloc(rs * 4 * (size_t)t->N);
   t->q_last = a.alloc(rs * (size_t)t->N);
+  if (t->m2l_engine == 1) {
+    t->M_lo = alloc_n<float>(a, 2 * (size_t)t->ncell * t->Kp);
+    int per = kM2LChunk;
+    if (const char* env = getenv("GBFMM_M2L_CHUNK")) per = std::max(1, atoi(env));  // tuning knob
+    build_m2l_chunks(t, per);
+  }
+  t->dev_err = alloc_n<int>(a, 1);
+  GB_CK(cudaMemsetAsync(t->dev_err, 0, sizeof(int), s));
   t->check_rec = alloc_n<unsigned long long>(a, 4);
   GB_CK(cudaMemsetAsync(t->check_rec, 0, 4 * sizeof(unsigned long long), s));
   t->lim = Lim{t->N, t->ncell, t->nleaf, t->Kp, t->ntile, t->nentry, t->nclass, t->n_p2p_ranges, t->check_rec};
@@ -116,15 +126,20 @@ template <class R>
 void run_pass(fmm_tree* t, cudaStream_t s, int mode, R* a, R* b) {
   const bool timing = (t->flags & FMM_FLAG_TIMING) != 0;
   PhaseTimer T{t, s, timing};
-  PhaseTimer Ts{t, t->side, timing};
   T.begin(FMM_PH_EVAL_TOTAL);
-  // near field on the side stream, concurrently with the far field
-  GB_CK(cudaEventRecord(t->fork, s));
-  GB_CK(cudaStreamWaitEvent(t->side, t->fork, 0));
-  Ts.begin(FMM_PH_P2P);
-  launch_p2p<R>(t, t->side);
-  Ts.end(FMM_PH_P2P);
-  GB_CK(cudaEventRecord(t->join, t->side));
+  // Near field on the side stream, concurrently with the far field.  With
+  // per-phase timing everything runs on the caller's stream, one kernel at a
+  // time, so that each phase's events time that phase alone.
+  cudaStream_t ps = timing ? s : t->side;
+  if (!timing) {
+    GB_CK(cudaEventRecord(t->fork, s));
+    GB_CK(cudaStreamWaitEvent(t->side, t->fork, 0));
+  }
+  PhaseTimer Tp{t, ps, timing};
+  Tp.begin(FMM_PH_P2P);
+  launch_p2p<R>(t, ps);
+  Tp.end(FMM_PH_P2P);
+  if (!timing) GB_CK(cudaEventRecord(t->join, t->side));
   // far field
   GB_CK(cudaMemsetAsync(t->L, 0, sizeof(R) * (size_t)t->ncell * t->Kp, s));
   T.begin(FMM_PH_P2M);
@@ -134,12 +149,17 @@ void run_pass(fmm_tree* t, cudaStream_t s, int mode, R* a, R* b) {
   for (int l = t->nlevel - 2; l >= 0; --l) launch_m2m<R>(t, l, s);
   T.end(FMM_PH_M2M);
   T.begin(FMM_PH_M2L);
-  launch_m2l_cuda_core<R>(t, s);
+  if (t->m2l_engine == 1) {
+    launch_split_tf32(t, s);
+    launch_m2l_tcgen05(t, s);
+  } else {
+    launch_m2l_cuda_core<R>(t, s);
+  }
   T.end(FMM_PH_M2L);
   T.begin(FMM_PH_L2L);
   for (int l = 1; l < t->nlevel; ++l) launch_l2l<R>(t, l, s);
   T.end(FMM_PH_L2L);
-  GB_CK(cudaStreamWaitEvent(s, t->join, 0));
+  if (!timing) GB_CK(cudaStreamWaitEvent(s, t->join, 0));
   T.begin(FMM_PH_L2P);
   launch_l2p_finalize<R>(t, mode, a, b, s);
   T.end(FMM_PH_L2P);
@@ -281,12 +301,20 @@ int fmm_get_stats(const fmm_tree* tc, fmm_stats* o) {
   o->m2l_engine = t->m2l_engine;
   o->workspace_bytes = (int64_t)t->arena.bytes;
   o->evaluations = t->evaluations;
+  if (t->dev_err) {
+    int h = 0;
+    if (cudaMemcpy(&h, t->dev_err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) {
+      cudaGetLastError();
+      return FMM_ERR_CUDA;
+    }
+    o->device_errors = h;
+  }
   if ((t->flags & FMM_FLAG_TIMING) && t->evaluations > 0) {
     if (cudaEventSynchronize(t->ev[2 * FMM_PH_EVAL_TOTAL + 1]) != cudaSuccess) {
       cudaGetLastError();
       return FMM_ERR_CUDA;
     }
-    cudaEventSynchronize(t->ev[2 * FMM_PH_P2P + 1]);
+
     for (int ph = 0; ph < FMM_PH_COUNT; ++ph) {
       if (ph == FMM_PH_BUILD_TOTAL) continue;
       float ms = 0.0f;
@@ -357,20 +385,24 @@ int fmm_get_cells(const fmm_tree* t, int32_t* cells, fmm_stream stream) {
   return FMM_OK;
 }
 
-int fmm_get_lists(const fmm_tree* t, int32_t* p2p_tgt, int32_t* p2p_src, int32_t* m2l_tgt, int32_t* m2l_src,
+int fmm_get_lists(const fmm_tree* tc, int32_t* p2p_tgt, int32_t* p2p_src, int32_t* m2l_tgt, int32_t* m2l_src,
                   fmm_stream stream) {
-  if (!t || !p2p_tgt || !p2p_src || (t->n_m2l && (!m2l_tgt || !m2l_src))) return FMM_ERR_ARG;
+  if (!tc || !p2p_tgt || !p2p_src || (tc->n_m2l && (!m2l_tgt || !m2l_src))) return FMM_ERR_ARG;
+  fmm_tree* t = const_cast<fmm_tree*>(tc);
   cudaStream_t s = (cudaStream_t)stream;
-  bool ok = cudaMemcpyAsync(p2p_tgt, t->p2p_tgt, sizeof(int32_t) * t->n_p2p, cudaMemcpyDeviceToDevice, s) == cudaSuccess &&
-            cudaMemcpyAsync(p2p_src, t->p2p_src, sizeof(int32_t) * t->n_p2p, cudaMemcpyDeviceToDevice, s) == cudaSuccess;
-  if (ok && t->n_m2l)
-    ok = cudaMemcpyAsync(m2l_tgt, t->m2l_tgt, sizeof(int32_t) * t->n_m2l, cudaMemcpyDeviceToDevice, s) == cudaSuccess &&
-         cudaMemcpyAsync(m2l_src, t->m2l_src, sizeof(int32_t) * t->n_m2l, cudaMemcpyDeviceToDevice, s) == cudaSuccess;
-  if (!ok) {
-    cudaGetLastError();
-    return FMM_ERR_CUDA;
+  // the tree keeps traversal order; sort copies by (target, source) on the
+  // caller's stream (workspace from the tree's allocator)
+  cudaStream_t keep = t->arena.stream;
+  t->arena.stream = s;
+  int rc = FMM_OK;
+  try {
+    sort_pairs_copy(t->arena, t->p2p_tgt, t->p2p_src, t->n_p2p, t->ncell, p2p_tgt, p2p_src, s);
+    sort_pairs_copy(t->arena, t->m2l_tgt, t->m2l_src, t->n_m2l, t->ncell, m2l_tgt, m2l_src, s);
+  } catch (const Error& e) {
+    rc = e.code;
   }
-  return FMM_OK;
+  t->arena.stream = keep;
+  return rc;
 }
 
 int fmm_get_expansions(const fmm_tree* t, void* M, void* L, fmm_stream stream) {

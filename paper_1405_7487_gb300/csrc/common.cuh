@@ -14,6 +14,7 @@ namespace gbfmm {
 constexpr int kMaxLevel = 21;   // 63-bit Morton keys, 3 bits per level (Sec. II.B)
 constexpr int kMaxP = 16;       // expansion terms supported (K = p*p <= 256)
 constexpr int kTile = 128;      // targets per M2L tile (rows of one MMA / one CTA)
+constexpr int kM2LChunk = 8;    // entries accumulated per TMEM partial (tensor-core M2L)
 
 struct Error {
   int code;
@@ -123,13 +124,18 @@ struct fmm_tree {
 
   void* M = nullptr;  // ncell x Kp
   void* L = nullptr;  // ncell x Kp
-  float* M_lo = nullptr;  // split copy of M for the 3xTF32 engine
+  float* M_lo = nullptr;  // split copy of M for the 3xTF32 engine (lo | hi)
+  int nchunk = 0;                  // M2L work units of the tensor-core engine
+  int4* m2l_chunks = nullptr;      // (tile, first entry, end entry, 0)
+  int32_t* tile_cptr = nullptr;    // chunks of tile t: [cptr[t], cptr[t+1])
+  float* m2l_part = nullptr;       // nchunk x kTile x Kp partial local expansions
   void* near = nullptr;   // N x 4 (phi, grad) sorted, P2P part
   void* grad_q = nullptr; // N x 4 (phi, grad) sorted, of the last evaluate
   void* q_last = nullptr; // N sorted charges of the last evaluate
   int evaluations = 0;
 
   unsigned long long* check_rec = nullptr;  // self-check record (checked build)
+  int* dev_err = nullptr;  // set by a kernel whose bounded wait gave up
   gbfmm::Lim lim{};
   cudaStream_t side = nullptr;  // P2P runs here, concurrently with the far field
   cudaEvent_t fork = nullptr, join = nullptr;
@@ -143,6 +149,9 @@ namespace gbfmm {
 void build_tree(fmm_tree* t, const void* xyzq, bool f64);
 // Traversal and lists (traverse.cu)
 void build_lists(fmm_tree* t);
+int bits_for(int64_t v);
+void sort_pairs_copy(Arena& a, const int32_t* tgt, const int32_t* src, int64_t n, int ncell, int32_t* out_tgt,
+                     int32_t* out_src, cudaStream_t s);
 // M2L tiles and operator tables (ops.cu)
 void build_m2l_plan(fmm_tree* t);
 void build_operators(fmm_tree* t);

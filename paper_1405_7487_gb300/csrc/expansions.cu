@@ -59,17 +59,25 @@ __global__ void k_p2m(const R4* __restrict__ work, const int32_t* __restrict__ l
   double c[3], Rc;
   cell_geom(root, level[cell], ix[cell], iy[cell], iz[cell], c, Rc);
   const int s = bbeg[cell], e = bend[cell];
+  const double inv_r = 1.0 / Rc;
   const int h = lane >> 4, m = lane & 15;
-  R ar[kMaxP], ai[kMaxP];
+  R ar[kMaxP], ai[kMaxP], rf[kMaxP];
+  // per-lane constants of column m: 1 / ((n+1+m)(n+1-m)) for n = m + k, and
+  // the diagonal factor 1 / (2^m m!)
 #pragma unroll
-  for (int k = 0; k < kMaxP; ++k) ar[k] = ai[k] = (R)0;
+  for (int k = 0; k < kMaxP; ++k) {
+    ar[k] = ai[k] = (R)0;
+    rf[k] = (R)1 / ((R)(2 * m + k + 1) * (R)(k + 1));
+  }
+  R dfac = 1;
+  for (int k = 1; k <= m; ++k) dfac /= (R)(2 * k);
   for (int j0 = s; j0 < e; j0 += 32) {
     R bx = 0, by = 0, bz = 0, bq = 0;
     if (j0 + lane < e) {
       R4 b = GB_LD(work, j0 + lane, lim.N, 312);
-      bx = (R)(((double)b.x - c[0]) / Rc);
-      by = (R)(((double)b.y - c[1]) / Rc);
-      bz = (R)(((double)b.z - c[2]) / Rc);
+      bx = (R)(((double)b.x - c[0]) * inv_r);
+      by = (R)(((double)b.y - c[1]) * inv_r);
+      bz = (R)(((double)b.z - c[2]) * inv_r);
       bq = b.w;
     }
     const int cnt = min(32, e - j0);
@@ -82,11 +90,10 @@ __global__ void k_p2m(const R4* __restrict__ work, const int32_t* __restrict__ l
       const R z = __shfl_sync(0xffffffffu, bz, sl), q = __shfl_sync(0xffffffffu, bq, sl);
       if (!ok || m >= p) continue;
       // diagonal Ups_m^m = (-(x + i y))^m / (2^m m!)
-      R ur = 1, ui = 0;
+      R ur = dfac, ui = 0;
       for (int k = 1; k <= m; ++k) {
-        const R f = (R)1 / (R)(2 * k);
-        const R nr = (-x * ur + y * ui) * f;
-        const R ni = (-x * ui - y * ur) * f;
+        const R nr = -x * ur + y * ui;
+        const R ni = -x * ui - y * ur;
         ur = nr;
         ui = ni;
       }
@@ -100,7 +107,7 @@ __global__ void k_p2m(const R4* __restrict__ work, const int32_t* __restrict__ l
           ar[k] += q * ur;
           ai[k] -= q * ui;
           // advance to n + 1
-          const R f = (R)1 / ((R)(n + 1 + m) * (R)(n + 1 - m));
+          const R f = rf[k];
           const R a = (R)(2 * n + 1) * z;
           const R nr = (a * ur - r2 * pr) * f;
           const R ni = (a * ui - r2 * pi) * f;
@@ -203,7 +210,16 @@ __global__ void k_l2p_finalize(const R4* __restrict__ work, const int32_t* __res
                                R* __restrict__ q_last, Lim lim) {
   extern __shared__ unsigned char smem_raw[];
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  R* Ls = reinterpret_cast<R*>(smem_raw) + w * Kp;
+  // reciprocal tables: rtab[m * kMaxP + n] = 1 / ((n+1+m)(n+1-m)), dtab[m] = 1 / (2m)
+  R* rtab = reinterpret_cast<R*>(smem_raw);
+  R* dtab = rtab + kMaxP * kMaxP;
+  R* Ls = dtab + kMaxP + w * Kp;
+  for (int i = threadIdx.x; i < kMaxP * kMaxP; i += blockDim.x) {
+    const int mm = i / kMaxP, nn = i % kMaxP;
+    rtab[i] = nn >= mm ? (R)1 / ((R)(nn + 1 + mm) * (R)(nn + 1 - mm)) : (R)0;
+  }
+  for (int i = threadIdx.x; i < kMaxP; i += blockDim.x) dtab[i] = i ? (R)1 / (R)(2 * i) : (R)0;
+  __syncthreads();
   const int li = blockIdx.x * kWarps + w;
   if (li >= nleaf) return;
   const int cell = leaves[li];
@@ -214,19 +230,20 @@ __global__ void k_l2p_finalize(const R4* __restrict__ work, const int32_t* __res
   __syncwarp();
   double c[3], Rc;
   cell_geom(root, level[cell], ix[cell], iy[cell], iz[cell], c, Rc);
-  const R inv_r = (R)(1.0 / Rc);
+  const double inv_rd = 1.0 / Rc;
+  const R inv_r = (R)inv_rd;
   const int s = bbeg[cell], e = bend[cell];
   for (int i = s + lane; i < e; i += 32) {
     const R4 b = GB_LD(work, i, lim.N, 343);
-    const R x = (R)(((double)b.x - c[0]) / Rc);
-    const R y = (R)(((double)b.y - c[1]) / Rc);
-    const R z = (R)(((double)b.z - c[2]) / Rc);
+    const R x = (R)(((double)b.x - c[0]) * inv_rd);
+    const R y = (R)(((double)b.y - c[1]) * inv_rd);
+    const R z = (R)(((double)b.z - c[2]) * inv_rd);
     const R r2 = x * x + y * y + z * z;
     R ph = 0, gx = 0, gy = 0, gz = 0;
     R dr = 1, di = 0;  // Ups_m^m
     for (int m = 0; m < p; ++m) {
       if (m > 0) {
-        const R f = (R)1 / (R)(2 * m);
+        const R f = dtab[m];
         const R nr = (-x * dr + y * di) * f;
         const R ni = (-x * di - y * dr) * f;
         dr = nr;
@@ -256,7 +273,7 @@ __global__ void k_l2p_finalize(const R4* __restrict__ work, const int32_t* __res
             gy -= lim * ur - lr * ui;
           }
         }
-        const R f = (R)1 / ((R)(n + 1 + m) * (R)(n + 1 - m));
+        const R f = rtab[m * kMaxP + n];
         const R a = (R)(2 * n + 1) * z;
         const R nr = (a * ur - r2 * pr) * f;
         const R ni = (a * ui - r2 * pi) * f;
@@ -339,7 +356,8 @@ void launch_l2l(fmm_tree* t, int level, cudaStream_t s) {
 template <class R>
 void launch_l2p_finalize(fmm_tree* t, int mode, R* a, R* b, cudaStream_t s) {
   using R4 = typename Vec4<R>::type;
-  k_l2p_finalize<R, R4><<<blocks(t->nleaf, kWarps), 32 * kWarps, sizeof(R) * kWarps * t->Kp, s>>>(
+  k_l2p_finalize<R, R4><<<blocks(t->nleaf, kWarps), 32 * kWarps,
+                          sizeof(R) * (kMaxP * kMaxP + kMaxP + kWarps * t->Kp), s>>>(
       (const R4*)t->work, t->leaves, t->nleaf, t->c.level, t->c.ix, t->c.iy, t->c.iz, t->c.bbeg, t->c.bend,
       t->d_root, t->p, t->Kp, (const R*)t->L, (const R4*)t->near, t->perm, mode, a, b, (R4*)t->grad_q,
       (R*)t->q_last, t->lim);

@@ -60,5 +60,6 @@ template <class R> void launch_p2p(fmm_tree* t, cudaStream_t s);
 template <class R> void launch_l2p_finalize(fmm_tree* t, int mode, R* a, R* b, cudaStream_t s);
 void launch_m2l_tcgen05(fmm_tree* t, cudaStream_t s);
 void launch_split_tf32(fmm_tree* t, cudaStream_t s);
+void build_m2l_chunks(fmm_tree* t, int per);
 
 }  // namespace gbfmm

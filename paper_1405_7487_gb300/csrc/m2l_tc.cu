@@ -1,0 +1,381 @@
+// m2l_tc.cu -- M2L on the 5th-generation tensor cores (tcgen05), single
+// precision through three TF32 products.
+//
+// M2L converts the multipole of each well-separated source into the local
+// expansion of the target (Sec. II.A; with P2P it takes most of the run
+// time).  Targets are tiled 128 at a time; for one tile and one translation
+// operator T_c (an entry of the plan) the 128 rows hold the source of each
+// target at that relative position, so the entry is the product
+//     L~[128 x Kp] += M~_src[128 x Kp] . T_c^T[Kp x Kp]
+// (M = 128 rows, N = Kp outputs, K = Kp inputs).  All entries of a tile
+// accumulate into one TMEM tile (fp32), read back once at the end.
+//
+// Precision: every operand x is split into hi = tf32(x) and lo = x - hi, and
+// each entry issues hi*hi + lo*hi + hi*lo (the lo*lo term is below the fp32
+// rounding of the result).  The operator tables are split at set-up (double
+// precision -> hi/lo), the multipoles after the upward pass.
+//
+// Pipeline (one CTA per tile, 160 threads):
+//   warps 0-3  producers: cp.async 16-byte copies of the 128 source rows
+//              (hi and lo) and of the Kp operator rows (hi and lo) of one
+//              32-element k-block into a stage, in the 128-byte-swizzled
+//              K-major layout the MMA descriptors describe; after their
+//              copies land they fence the async proxy and arrive on the
+//              stage's "full" barrier.  Then the epilogue (TMEM -> L).
+//   warp 4     TMEM allocation; one elected lane issues the MMAs of a stage
+//              and commits them to the stage's "empty" barrier.
+// Every wait is bounded; a wait that gives up sets the error flag, the
+// roles drain and the TMEM is released.
+#include <algorithm>
+#include <vector>
+
+#include "kernels.cuh"
+
+namespace gbfmm {
+namespace {
+
+constexpr int kProducers = 128;
+constexpr int kThreadsTC = 160;
+constexpr int kKB = 32;               // fp32 elements per k-block (128 bytes per row)
+constexpr int kStageA = 128 * 128;    // bytes of one 128-row operand block
+constexpr long long kSpinLimit = 1ll << 20;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// Byte offset of 16-byte chunk c of row r in a [rows][128 B] block with the
+// 128-byte swizzle (8-row groups of 1024 bytes, chunk index XOR row % 8).
+__device__ __forceinline__ uint32_t swz(int r, int c) {
+  return (uint32_t)(((r >> 3) << 10) + ((r & 7) << 7) + (((c ^ (r & 7)) & 7) << 4));
+}
+
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, int bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(dst), "l"(src), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+// cp.async.wait_group needs an immediate: dispatch the pipeline depths used
+__device__ __forceinline__ void cp_async_wait_dyn(int n) {
+  switch (n) {
+    case 0: cp_async_wait<0>(); break;
+    case 1: cp_async_wait<1>(); break;
+    case 2: cp_async_wait<2>(); break;
+    case 3: cp_async_wait<3>(); break;
+    case 4: cp_async_wait<4>(); break;
+    default: cp_async_wait<5>(); break;
+  }
+}
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, int count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.shared::cta.b64 st, [%0];\n}\n" ::"r"(bar) : "memory");
+}
+// Bounded wait for the phase with the given parity; false if it gave up (or
+// another role aborted).
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag) {
+  for (long long it = 0; it < kSpinLimit; ++it) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if ((it & 1023) == 1023 && *abort_flag) return false;
+  }
+  *abort_flag = 1;
+  return false;
+}
+
+// UMMA shared-memory descriptor: K-major, 128-byte swizzle, 8-row groups
+// 1024 bytes apart (SBO), sm_100 descriptor version 1.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((addr >> 4) & 0x3FFF);
+  d |= (uint64_t)1 << 16;              // LBO (unused for swizzled K-major)
+  d |= (uint64_t)(1024 >> 4) << 32;    // SBO
+  d |= (uint64_t)1 << 46;              // version
+  d |= (uint64_t)2 << 61;              // SWIZZLE_128B
+  return d;
+}
+
+// Instruction descriptor, kind::tf32: D fp32, A and B tf32, both K-major,
+// N = n, M = 128.
+__device__ __forceinline__ uint32_t idesc_tf32(int n) {
+  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_tf32(uint32_t tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc)
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(bar)
+               : "memory");
+}
+
+__global__ void __launch_bounds__(kThreadsTC, 1)
+    k_m2l_tc(const int4* __restrict__ chunks, const int32_t* __restrict__ entry_class,
+             const int32_t* __restrict__ entry_src, const float* __restrict__ ops_hi,
+             const float* __restrict__ ops_lo, const float* __restrict__ Mhi, const float* __restrict__ Mlo, int Kp,
+             int nstage, int tmem_cols, float* __restrict__ part, int* __restrict__ err) {
+  extern __shared__ unsigned char smem_raw[];
+  __shared__ uint64_t bar_full[8], bar_empty[8], bar_done;
+  __shared__ uint32_t tmem_base;
+  __shared__ volatile int abort_flag;
+
+  // 1024-byte aligned stage buffers
+  const uint32_t raw = smem_u32(smem_raw);
+  const uint32_t base = (raw + 1023u) & ~1023u;
+  const int stageB = Kp * 128;
+  const int stage_bytes = 2 * kStageA + 2 * stageB;
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  // chunk = (tile, first entry, end entry): a bounded run of the tile's
+  // entries, accumulated in TMEM and written as one partial sum
+  const int4 ch = chunks[blockIdx.x];
+  const int e0 = ch.y, e1 = ch.z;
+  const int nkb = (Kp + kKB - 1) / kKB;
+  const int nit = (e1 - e0) * nkb;
+
+  if (tid == 0) {
+    abort_flag = 0;
+    for (int s = 0; s < nstage; ++s) {
+      mbar_init(smem_u32(&bar_full[s]), kProducers);
+      mbar_init(smem_u32(&bar_empty[s]), 1);
+    }
+    mbar_init(smem_u32(&bar_done), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  if (warp == 4) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(&tmem_base)),
+                 "r"(tmem_cols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+  const uint32_t tmem = tmem_base;
+
+  if (warp < 4) {
+    // ---------------------------------------------------------- producers
+    const int r = tid;
+    int cur_e = -1, src = -1, cls = 0;
+    // copies of the last nstage - 1 iterations stay in flight; iteration
+    // it - (nstage - 1) is published once its copies have landed
+    const int lag = nstage - 1;
+    for (int it = 0; it < nit; ++it) {
+      const int e = e0 + it / nkb, kb = it % nkb;
+      const int s = it % nstage, round = it / nstage;
+      if (round > 0 && !mbar_wait(smem_u32(&bar_empty[s]), (round - 1) & 1, &abort_flag)) break;
+      if (e != cur_e) {
+        cur_e = e;
+        src = entry_src[(int64_t)e * kTile + r];
+        cls = entry_class[e];
+      }
+      const uint32_t sb = base + s * stage_bytes;
+      const int k0 = kb * kKB;
+      const int nch = min(kKB, Kp - k0) / 4;  // 16-byte chunks in this k-block
+      // A rows: the source multipole of tile row r (zeros for an empty row)
+      const float* ah = Mhi + (int64_t)(src >= 0 ? src : 0) * Kp + k0;
+      const float* al = Mlo + (int64_t)(src >= 0 ? src : 0) * Kp + k0;
+      const int bytes = src >= 0 ? 16 : 0;
+      for (int c = 0; c < nch; ++c) {
+        cp_async16(sb + swz(r, c), ah + 4 * c, bytes);
+        cp_async16(sb + kStageA + swz(r, c), al + 4 * c, bytes);
+      }
+      // B rows: output coefficient rows of the operator
+      const float* oh = ops_hi + (int64_t)cls * Kp * Kp + k0;
+      const float* ol = ops_lo + (int64_t)cls * Kp * Kp + k0;
+      for (int w = r; w < Kp * nch; w += kProducers) {
+        const int row = w / nch, c = w % nch;
+        cp_async16(sb + 2 * kStageA + swz(row, c), oh + (int64_t)row * Kp + 4 * c, 16);
+        cp_async16(sb + 2 * kStageA + stageB + swz(row, c), ol + (int64_t)row * Kp + 4 * c, 16);
+      }
+      cp_async_commit();
+      if (it >= lag) {
+        // all but the newest `lag` groups have landed
+        cp_async_wait_dyn(lag);
+        fence_async_smem();
+        mbar_arrive(smem_u32(&bar_full[(it - lag) % nstage]));
+      }
+    }
+    cp_async_wait<0>();
+    fence_async_smem();
+    for (int it = max(0, nit - lag); it < nit; ++it) mbar_arrive(smem_u32(&bar_full[it % nstage]));
+    // ------------------------------------------------------------ epilogue
+    const bool ok = nit > 0 && mbar_wait(smem_u32(&bar_done), 0, &abort_flag);
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    if (ok || nit == 0) {
+      float* lrow = part + ((int64_t)blockIdx.x * kTile + r) * Kp;
+      for (int c0 = 0; c0 < Kp; c0 += 16) {
+        uint32_t v[16];
+        if (nit > 0) {
+          const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
+          asm volatile(
+              "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
+              "[%16];\n"
+              : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+                "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+              : "r"(taddr)
+              : "memory");
+          asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+        } else {
+          for (int k = 0; k < 16; ++k) v[k] = 0u;
+        }
+        float4* dst = reinterpret_cast<float4*>(lrow + c0);
+        for (int k = 0; k < 4; ++k)
+          dst[k] = make_float4(__uint_as_float(v[4 * k]), __uint_as_float(v[4 * k + 1]), __uint_as_float(v[4 * k + 2]),
+                               __uint_as_float(v[4 * k + 3]));
+      }
+    }
+  } else if (lane == 0) {
+    // ---------------------------------------------------------------- MMA
+    const uint32_t idesc = idesc_tf32(Kp);
+    bool ok = true;
+    for (int it = 0; it < nit; ++it) {
+      const int kb = it % nkb;
+      const int s = it % nstage, round = it / nstage;
+      if (!mbar_wait(smem_u32(&bar_full[s]), round & 1, &abort_flag)) {
+        ok = false;
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+      const uint32_t sb = base + s * stage_bytes;
+      const int nks = min(kKB, Kp - kb * kKB) / 8;  // tf32 k-steps of 8 elements
+      for (int ks = 0; ks < nks; ++ks) {
+        const uint32_t off = ks * 32;
+        const uint64_t ah = smem_desc(sb + off), al = smem_desc(sb + kStageA + off);
+        const uint64_t bh = smem_desc(sb + 2 * kStageA + off), bl = smem_desc(sb + 2 * kStageA + stageB + off);
+        const uint32_t first = (it == 0 && ks == 0) ? 0u : 1u;
+        mma_tf32(tmem, ah, bh, idesc, first);
+        mma_tf32(tmem, al, bh, idesc, 1u);
+        mma_tf32(tmem, ah, bl, idesc, 1u);
+      }
+      mma_commit(smem_u32(&bar_empty[s]));
+    }
+    if (ok && nit > 0) mma_commit(smem_u32(&bar_done));
+    if (!ok) abort_flag = 1;
+  }
+  // drain: the last commits must land before the TMEM is released
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  if (abort_flag && tid == 0) atomicExch(err, 1);
+  if (warp == 4) {
+    if (abort_flag && nit > 0) {
+      // wait (bounded) for the MMAs that were issued, then release
+      volatile int dummy = 0;
+      mbar_wait(smem_u32(&bar_done), 0, &dummy);
+    }
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(tmem_cols) : "memory");
+  }
+}
+
+// hi = tf32(x) and lo = tf32(x - hi) (both rounded to nearest), for the
+// multipoles.
+__global__ void k_split_tf32(const float* __restrict__ x, int64_t n, float* __restrict__ hi, float* __restrict__ lo) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float v = x[i];
+  uint32_t hb;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(hb) : "f"(v));
+  const float h = __uint_as_float(hb);
+  hi[i] = h;
+  uint32_t lb;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(lb) : "f"(v - h));
+  lo[i] = __uint_as_float(lb);
+}
+
+// L rows of one tile = compensated (Kahan) sum of its chunks' partials, in
+// chunk order.  Thread per (row, coefficient).
+__global__ void k_m2l_reduce(const int32_t* __restrict__ tile_tgt, const int32_t* __restrict__ tile_cptr,
+                             const float* __restrict__ part, int K, int Kp, float* __restrict__ L) {
+  const int tile = blockIdx.x;
+  const int c0 = tile_cptr[tile], c1 = tile_cptr[tile + 1];
+  for (int w = threadIdx.x; w < kTile * Kp; w += blockDim.x) {
+    const int r = w / Kp, c = w % Kp;
+    const int tgt = tile_tgt[(int64_t)tile * kTile + r];
+    if (tgt < 0 || c >= K) continue;
+    float sum = 0.f, comp = 0.f;
+    for (int ch = c0; ch < c1; ++ch) {
+      const float y = part[((int64_t)ch * kTile + r) * Kp + c] - comp;
+      const float tt = sum + y;
+      comp = (tt - sum) - y;
+      sum = tt;
+    }
+    L[(int64_t)tgt * Kp + c] = sum;
+  }
+}
+
+}  // namespace
+
+int m2l_tc_stages(int Kp) {
+  const int stage_bytes = 2 * kStageA + 2 * Kp * 128;
+  int s = (200 * 1024) / stage_bytes;
+  return s < 2 ? 2 : (s > 6 ? 6 : s);
+}
+
+void launch_split_tf32(fmm_tree* t, cudaStream_t s) {
+  const int64_t n = (int64_t)t->ncell * t->Kp;
+  k_split_tf32<<<(unsigned)((n + 255) / 256), 256, 0, s>>>((const float*)t->M, n, t->M_lo + n, t->M_lo);
+  GB_LAUNCH("k_split_tf32");
+}
+
+void launch_m2l_tcgen05(fmm_tree* t, cudaStream_t s) {
+  if (t->ntile == 0) return;
+  const int Kp = t->Kp;
+  const int nstage = m2l_tc_stages(Kp);
+  const size_t smem = (size_t)nstage * (2 * kStageA + 2 * Kp * 128) + 1024;
+  // the dynamic size this launch needs (static + dynamic must stay within the
+  // 227 KB per-block limit)
+  GB_CK(cudaFuncSetAttribute(k_m2l_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int cols = 32;
+  while (cols < Kp) cols <<= 1;
+  const int64_t n = (int64_t)t->ncell * Kp;
+  k_m2l_tc<<<t->nchunk, kThreadsTC, smem, s>>>(t->m2l_chunks, t->entry_class, t->entry_src,
+                                               (const float*)t->m2l_ops, t->m2l_ops_lo, t->M_lo + n, t->M_lo, Kp,
+                                               nstage, cols, t->m2l_part, t->dev_err);
+  GB_LAUNCH("k_m2l_tc");
+  k_m2l_reduce<<<t->ntile, 256, 0, s>>>(t->tile_tgt, t->tile_cptr, t->m2l_part, t->K, Kp, (float*)t->L);
+  GB_LAUNCH("k_m2l_reduce");
+}
+
+// Chunks of at most `per` consecutive entries of every tile (host: the entry
+// ranges of the tiles are read back once at build time).
+void build_m2l_chunks(fmm_tree* t, int per) {
+  Arena& a = t->arena;
+  cudaStream_t s = t->stream;
+  std::vector<int32_t> eptr(t->ntile + 1);
+  GB_CK(cudaMemcpyAsync(eptr.data(), t->tile_eptr, sizeof(int32_t) * (t->ntile + 1), cudaMemcpyDeviceToHost, s));
+  GB_CK(cudaStreamSynchronize(s));
+  std::vector<int4> ch;
+  std::vector<int32_t> cptr(t->ntile + 1, 0);
+  for (int tile = 0; tile < t->ntile; ++tile) {
+    cptr[tile] = (int32_t)ch.size();
+    for (int e = eptr[tile]; e < eptr[tile + 1]; e += per)
+      ch.push_back(make_int4(tile, e, std::min(e + per, eptr[tile + 1]), 0));
+  }
+  cptr[t->ntile] = (int32_t)ch.size();
+  t->nchunk = (int)ch.size();
+  t->m2l_chunks = alloc_n<int4>(a, ch.size());
+  t->tile_cptr = alloc_n<int32_t>(a, cptr.size());
+  GB_CK(cudaMemcpyAsync(t->m2l_chunks, ch.data(), sizeof(int4) * ch.size(), cudaMemcpyHostToDevice, s));
+  GB_CK(cudaMemcpyAsync(t->tile_cptr, cptr.data(), sizeof(int32_t) * cptr.size(), cudaMemcpyHostToDevice, s));
+  t->m2l_part = alloc_n<float>(a, (size_t)t->nchunk * kTile * t->Kp);
+  GB_CK(cudaStreamSynchronize(s));
+}
+
+}  // namespace gbfmm

@@ -89,13 +89,13 @@ enum Kind { kM2M = 0, kL2L = 1, kM2L = 2 };
 // Complex coefficient C(out (a, b), in (c, d)) for -c <= d <= c.
 struct Coef {
   int kind;
-  double sA, sB;  // M2L: R_A / r and R_B / r
+  int eA, eB;  // M2L: R_A / r = 2^eA and R_B / r = 2^eB
   const cd* X;
   __device__ cd operator()(int a, int b, int c, int d) const {
     if (kind == kM2L) {
       // out (k = a, l = b), in (n = c, m = d)
       cd t = hget(X, a + c, d + b);
-      double f = ((a & 1) ? -1.0 : 1.0) * pow(sB, a + 1) * pow(sA, c);
+      double f = ldexp((a & 1) ? -1.0 : 1.0, eB * (a + 1) + eA * c);
       return cscale(t, f);
     }
     if (kind == kM2M) {
@@ -121,7 +121,7 @@ __device__ __forceinline__ void put(R* op, int Kp, bool out_major, int ro, int r
 }
 
 // Real Kp x Kp matrices of one operator per block.  geom: per operator
-// (x, y, z, sA, sB) in double; X built in shared memory.
+// (x, y, z, log2(R_A / r), log2(R_B / r)) in double; X built in shared memory.
 template <class R>
 __global__ void k_build_ops(int kind, int p, int Kp, const double* __restrict__ geom, int nops,
                             R* __restrict__ ops, float* __restrict__ ops_lo, bool out_major,
@@ -136,7 +136,7 @@ __global__ void k_build_ops(int kind, int p, int Kp, const double* __restrict__ 
     else regular_tri(g[0], g[1], g[2], P, X);
   }
   __syncthreads();
-  Coef C{kind, g[3], g[4], X};
+  Coef C{kind, (int)g[3], (int)g[4], X};
   R* o = ops + (int64_t)op * Kp * Kp;
   float* olo = ops_lo ? ops_lo + (int64_t)op * Kp * Kp : nullptr;
   // zero (padding rows/columns stay zero)
@@ -182,7 +182,14 @@ __global__ void k_build_ops(int kind, int p, int Kp, const double* __restrict__ 
           uint32_t hb;
           asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(hb) : "f"(hf));
           float hi = __uint_as_float(hb);
-          float lo = (float)(v - (double)hi);
+          // the low part rounded to TF32 as well, so the tensor core sees it
+          // exactly (its own conversion would truncate)
+          float lo;
+          {
+            uint32_t lb;
+            asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(lb) : "f"((float)(v - (double)hi)));
+            lo = __uint_as_float(lb);
+          }
           int64_t at = out_major ? (int64_t)ro * Kp + ri : (int64_t)ri * Kp + ro;
           o[at] = (R)hi;
           olo[at] = lo;
@@ -205,25 +212,25 @@ __global__ void k_target_flags(const int32_t* __restrict__ tgt, int64_t n, int32
 // Targets ordered by (octant within the parent, cell): cells sharing an
 // octant see the same relative source pattern, so a tile of them needs few
 // distinct operators.
-__global__ void k_target_keys(const int32_t* __restrict__ has, CellView c, int ncell,
+__global__ void k_target_keys(const int32_t* __restrict__ has, CellView c, int ncell, int cbits,
                               uint64_t* __restrict__ key, unsigned long long* __restrict__ count) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= ncell) return;
   if (has[i]) {
     const uint64_t oct = ((c.ix[i] & 1) << 2) | ((c.iy[i] & 1) << 1) | (c.iz[i] & 1);
-    key[i] = (oct << 32) | (uint32_t)i;
+    key[i] = (oct << cbits) | (uint32_t)i;
     atomicAdd(count, 1ull);
   } else {
     key[i] = ~0ull;
   }
 }
 
-__global__ void k_target_rank(const uint64_t* __restrict__ key, int64_t ntgt, int64_t padded,
+__global__ void k_target_rank(const uint64_t* __restrict__ key, int64_t ntgt, int64_t padded, int cbits,
                               int32_t* __restrict__ tile_tgt, int32_t* __restrict__ rank_of) {
   const int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (r >= padded) return;
   if (r < ntgt) {
-    const int cell = (int)(key[r] & 0xffffffffu);
+    const int cell = (int)(key[r] & ((1ull << cbits) - 1));
     tile_tgt[r] = cell;
     rank_of[cell] = (int32_t)r;
   } else {
@@ -231,23 +238,52 @@ __global__ void k_target_rank(const uint64_t* __restrict__ key, int64_t ntgt, in
   }
 }
 
-__global__ void k_class_keys(const int32_t* __restrict__ tgt, const int32_t* __restrict__ src,
-                             int64_t n, CellView c, uint64_t* __restrict__ key, int32_t* __restrict__ val) {
-  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  const int A = src[i], B = tgt[i];
+__device__ __forceinline__ void pair_offset(const CellView& c, int A, int B, int64_t d[3], int& dl) {
   const int la = c.level[A], lb = c.level[B];
   const int lmax = la > lb ? la : lb;
   const int sh = kMaxLevel - lmax;
-  int64_t d[3];
   d[0] = (((2ll * c.ix[A] + 1) << (kMaxLevel - la)) - ((2ll * c.ix[B] + 1) << (kMaxLevel - lb))) >> sh;
   d[1] = (((2ll * c.iy[A] + 1) << (kMaxLevel - la)) - ((2ll * c.iy[B] + 1) << (kMaxLevel - lb))) >> sh;
   d[2] = (((2ll * c.iz[A] + 1) << (kMaxLevel - la)) - ((2ll * c.iz[B] + 1) << (kMaxLevel - lb))) >> sh;
-  const int64_t lim = 1ll << 18;
-  const bool regular = d[0] > -lim && d[0] < lim && d[1] > -lim && d[1] < lim && d[2] > -lim && d[2] < lim;
-  if (regular) {
-    key[i] = ((uint64_t)(la - lb + 32) << 57) | ((uint64_t)(d[0] + lim) << 38) |
-             ((uint64_t)(d[1] + lim) << 19) | (uint64_t)(d[2] + lim);
+  dl = la - lb;
+}
+
+// Largest |offset| component over all M2L pairs (sizes the class keys).
+__global__ void k_class_maxd(const int32_t* __restrict__ tgt, const int32_t* __restrict__ src, int64_t n,
+                             CellView c, unsigned long long* __restrict__ maxd) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  unsigned long long m = 0;
+  if (i < n) {
+    int64_t d[3];
+    int dl;
+    pair_offset(c, src[i], tgt[i], d, dl);
+    for (int k = 0; k < 3; ++k) m = max(m, (unsigned long long)(d[k] < 0 ? -d[k] : d[k]));
+  }
+  for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_down_sync(0xffffffffu, m, o));
+  __shared__ unsigned long long wm[kThreads / 32];
+  if ((threadIdx.x & 31) == 0) wm[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < kThreads / 32; ++w) m = max(m, wm[w]);
+    if (m) atomicMax(maxd, m);
+  }
+}
+
+// Class key of a pair: (level difference, offset in units of the smaller
+// cell's half side), packed into 6 + 3 b bits with every offset component
+// biased by maxd.  Offsets too large for 63 bits (b > 19) get a key of their
+// own (top bit set, then the pair index).
+__global__ void k_class_keys(const int32_t* __restrict__ tgt, const int32_t* __restrict__ src,
+                             int64_t n, CellView c, int b, int64_t maxd, uint64_t* __restrict__ key,
+                             int32_t* __restrict__ val) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int64_t d[3];
+  int dl;
+  pair_offset(c, src[i], tgt[i], d, dl);
+  if (b <= 19) {
+    key[i] = ((uint64_t)(dl + kMaxLevel) << (3 * b)) | ((uint64_t)(d[0] + maxd) << (2 * b)) |
+             ((uint64_t)(d[1] + maxd) << b) | (uint64_t)(d[2] + maxd);
   } else {
     key[i] = (1ull << 63) | (uint64_t)i;
   }
@@ -283,19 +319,20 @@ __global__ void k_class_assign(const uint64_t* __restrict__ key, const int32_t* 
   desc[4 * cid + 3] = (int32_t)((((2ll * c.iz[A] + 1) << (kMaxLevel - la)) - ((2ll * c.iz[B] + 1) << (kMaxLevel - lb))) >> sh);
 }
 
+// Entry key of a pair: (target tile, class, tile row) in tb + cb + 7 bits.
 __global__ void k_entry_keys(const int32_t* __restrict__ tgt, const int32_t* __restrict__ src,
                              const int32_t* __restrict__ class_of, const int32_t* __restrict__ rank_of,
-                             int64_t n, uint64_t* __restrict__ key, int32_t* __restrict__ val) {
+                             int64_t n, int cb, uint64_t* __restrict__ key, int32_t* __restrict__ val) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= n) return;
   const uint64_t r = (uint64_t)rank_of[tgt[i]];
   const uint64_t tile = r / kTile, slot = r % kTile;
-  key[i] = (tile << 39) | ((uint64_t)(uint32_t)class_of[i] << 7) | slot;
+  key[i] = (tile << (cb + 7)) | ((uint64_t)(uint32_t)class_of[i] << 7) | slot;
   val[i] = src[i];
 }
 
 __global__ void k_entry_fill(const uint64_t* __restrict__ key, const int32_t* __restrict__ val,
-                             const int64_t* __restrict__ excl, int64_t n, int32_t* __restrict__ entry_class,
+                             const int64_t* __restrict__ excl, int64_t n, int cb, int32_t* __restrict__ entry_class,
                              int32_t* __restrict__ entry_src, uint64_t* __restrict__ entry_key) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= n) return;
@@ -303,8 +340,8 @@ __global__ void k_entry_fill(const uint64_t* __restrict__ key, const int32_t* __
   const int64_t e = excl[i] + (first ? 0 : -1);
   entry_src[e * kTile + (key[i] & (kTile - 1))] = val[i];
   if (first) {
-    entry_class[e] = (int32_t)((key[i] >> 7) & 0xffffffffu);
-    entry_key[e] = key[i] >> 39;  // tile
+    entry_class[e] = (int32_t)((key[i] >> 7) & ((1ull << cb) - 1));
+    entry_key[e] = key[i] >> (cb + 7);  // tile
   }
 }
 
@@ -329,8 +366,8 @@ __global__ void k_m2l_geom(const int32_t* __restrict__ desc, int n, double* __re
   geom[5 * i + 0] = -(double)desc[4 * i + 1];
   geom[5 * i + 1] = -(double)desc[4 * i + 2];
   geom[5 * i + 2] = -(double)desc[4 * i + 3];
-  geom[5 * i + 3] = ldexp(1.0, dl < 0 ? -dl : 0);
-  geom[5 * i + 4] = ldexp(1.0, dl > 0 ? dl : 0);
+  geom[5 * i + 3] = dl < 0 ? -dl : 0;  // log2(R_A / r)
+  geom[5 * i + 4] = dl > 0 ? dl : 0;   // log2(R_B / r)
 }
 
 }  // namespace
@@ -356,9 +393,12 @@ void build_m2l_plan(fmm_tree* t) {
   uint64_t* tkey = alloc_n<uint64_t>(a, t->ncell);
   unsigned long long* d_cnt = alloc_n<unsigned long long>(a, 1);
   GB_CK(cudaMemsetAsync(d_cnt, 0, sizeof(unsigned long long), s));
-  k_target_keys<<<blocks(t->ncell), kThreads, 0, s>>>(has, cv, t->ncell, tkey, d_cnt);
+  // 2^cbits > ncell, so a real key never equals the all-ones key of a non-target
+  int cbits = 1;
+  while ((1ll << cbits) <= (int64_t)t->ncell) ++cbits;
+  k_target_keys<<<blocks(t->ncell), kThreads, 0, s>>>(has, cv, t->ncell, cbits, tkey, d_cnt);
   GB_LAUNCH("k_target_keys");
-  radix_sort_keys(a, tkey, t->ncell, 64, s);
+  radix_sort_keys(a, tkey, t->ncell, cbits + 3, s);
   unsigned long long ntgt = 0;
   GB_CK(cudaMemcpyAsync(&ntgt, d_cnt, sizeof(ntgt), cudaMemcpyDeviceToHost, s));
   GB_CK(cudaStreamSynchronize(s));
@@ -366,7 +406,7 @@ void build_m2l_plan(fmm_tree* t) {
   const int64_t padded = (int64_t)t->ntile * kTile;
   t->tile_tgt = alloc_n<int32_t>(a, padded);
   int32_t* rank_of = alloc_n<int32_t>(a, t->ncell);
-  k_target_rank<<<blocks(padded), kThreads, 0, s>>>(tkey, (int64_t)ntgt, padded, t->tile_tgt, rank_of);
+  k_target_rank<<<blocks(padded), kThreads, 0, s>>>(tkey, (int64_t)ntgt, padded, cbits, t->tile_tgt, rank_of);
   GB_LAUNCH("k_target_rank");
   a.release(tkey);
   a.release(has);
@@ -375,9 +415,19 @@ void build_m2l_plan(fmm_tree* t) {
   // --- translation classes
   uint64_t* ckey = alloc_n<uint64_t>(a, nm);
   int32_t* cval = alloc_n<int32_t>(a, nm);
-  k_class_keys<<<blocks(nm), kThreads, 0, s>>>(t->m2l_tgt, t->m2l_src, nm, cv, ckey, cval);
+  unsigned long long* d_maxd = alloc_n<unsigned long long>(a, 1);
+  GB_CK(cudaMemsetAsync(d_maxd, 0, sizeof(unsigned long long), s));
+  k_class_maxd<<<blocks(nm), kThreads, 0, s>>>(t->m2l_tgt, t->m2l_src, nm, cv, d_maxd);
+  GB_LAUNCH("k_class_maxd");
+  unsigned long long maxd = 0;
+  GB_CK(cudaMemcpyAsync(&maxd, d_maxd, sizeof(maxd), cudaMemcpyDeviceToHost, s));
+  GB_CK(cudaStreamSynchronize(s));
+  a.release(d_maxd);
+  int b = 1;
+  while ((1ull << b) <= 2 * maxd) ++b;
+  k_class_keys<<<blocks(nm), kThreads, 0, s>>>(t->m2l_tgt, t->m2l_src, nm, cv, b, (int64_t)maxd, ckey, cval);
   GB_LAUNCH("k_class_keys");
-  radix_sort_pairs(a, ckey, cval, nm, 64, s);
+  radix_sort_pairs(a, ckey, cval, nm, b <= 19 ? 6 + 3 * b : 64, s);
   int64_t* flag = alloc_n<int64_t>(a, nm);
   k_unique_flags<<<blocks(nm), kThreads, 0, s>>>(ckey, nm, 0, flag);
   GB_LAUNCH("k_unique_flags");
@@ -396,11 +446,15 @@ void build_m2l_plan(fmm_tree* t) {
   // --- entries: (tile, class) with the source of every tile row
   uint64_t* ekey = alloc_n<uint64_t>(a, nm);
   int32_t* eval = alloc_n<int32_t>(a, nm);
-  k_entry_keys<<<blocks(nm), kThreads, 0, s>>>(t->m2l_tgt, t->m2l_src, class_of, rank_of, nm, ekey, eval);
+  int cb = 1, tb = 1;
+  while ((1ll << cb) < (int64_t)t->nclass) ++cb;
+  while ((1ll << tb) < (int64_t)t->ntile) ++tb;
+  if (tb + cb + 7 > 64) fail(FMM_ERR_ARG, "M2L plan key too wide");
+  k_entry_keys<<<blocks(nm), kThreads, 0, s>>>(t->m2l_tgt, t->m2l_src, class_of, rank_of, nm, cb, ekey, eval);
   GB_LAUNCH("k_entry_keys");
   a.release(class_of);
   a.release(rank_of);
-  radix_sort_pairs(a, ekey, eval, nm, 63, s);
+  radix_sort_pairs(a, ekey, eval, nm, tb + cb + 7, s);
   int64_t* eflag = alloc_n<int64_t>(a, nm);
   k_unique_flags<<<blocks(nm), kThreads, 0, s>>>(ekey, nm, 7, eflag);
   GB_LAUNCH("k_unique_flags");
@@ -410,7 +464,7 @@ void build_m2l_plan(fmm_tree* t) {
   t->entry_src = alloc_n<int32_t>(a, ne * kTile);
   GB_CK(cudaMemsetAsync(t->entry_src, 0xff, sizeof(int32_t) * ne * kTile, s));
   uint64_t* etile = alloc_n<uint64_t>(a, ne);
-  k_entry_fill<<<blocks(nm), kThreads, 0, s>>>(ekey, eval, eflag, nm, t->entry_class, t->entry_src, etile);
+  k_entry_fill<<<blocks(nm), kThreads, 0, s>>>(ekey, eval, eflag, nm, cb, t->entry_class, t->entry_src, etile);
   GB_LAUNCH("k_entry_fill");
   t->tile_eptr = alloc_n<int32_t>(a, t->ntile + 1);
   k_tile_ptr<<<blocks(t->ntile + 1), kThreads, 0, s>>>(etile, ne, t->ntile, t->tile_eptr);
@@ -435,8 +489,8 @@ void build_operators(fmm_tree* t) {
     hgeom[5 * o + 0] = ((o >> 2) & 1) - 0.5;
     hgeom[5 * o + 1] = ((o >> 1) & 1) - 0.5;
     hgeom[5 * o + 2] = (o & 1) - 0.5;
-    hgeom[5 * o + 3] = 1.0;
-    hgeom[5 * o + 4] = 1.0;
+    hgeom[5 * o + 3] = 0.0;
+    hgeom[5 * o + 4] = 0.0;
   }
   double* g8 = alloc_n<double>(a, 40);
   GB_CK(cudaMemcpyAsync(g8, hgeom, sizeof(hgeom), cudaMemcpyHostToDevice, s));

@@ -2,23 +2,26 @@
 // the source leaves of its P2P list (Sec. II.A; Sec. II.C: P2P only needs
 // the neighbours).
 //
-// One block of 128 threads per target leaf.  A leaf of n <= 128 bodies is
-// covered G = floor(128 / n) times: thread (g, i) accumulates target i over
-// the sources j = g, g + G, ... of every staged tile, and the G partial sums
-// are added in a fixed order at the end (so results are reproducible).
-// Sources are staged through shared memory in tiles of 256 bodies (16 B
-// float4 each, coalesced loads).  Within a tile each thread sums naively; the
-// tile sums are combined with compensated (Kahan) addition.  The leaf's own
-// bodies are a separate, masked pass (self and coincident pairs contribute
-// zero); bodies of two different leaves always differ in position, so the
-// other ranges need no mask.
+// One block of 128 threads per target leaf (targets in chunks of 256).  Each
+// thread owns two targets (i and i + T2, T2 = ceil(n/2)), so one shared-memory
+// load of a source serves two pairs.  The T2 threads of a target chunk form a
+// group; G = floor(128 / T2) groups split every staged source tile into G
+// contiguous pieces, and the G partial sums are added in a fixed order at the
+// end (results are reproducible).  Sources are streamed through shared
+// memory in tiles of 512 bodies (float4, 16-byte cp.async copies, double
+// buffered): first the leaf's own bodies (masked: self and coincident pairs
+// contribute zero), then the merged neighbour ranges back to back.  Bodies of
+// two different leaves never coincide, so those tiles need no mask.
+// Within a tile each thread sums naively; tile sums are combined with
+// compensated (Kahan) addition.
 #include "kernels.cuh"
 
 namespace gbfmm {
 namespace {
 
 constexpr int kThreads = 128;
-constexpr int kSrcTile = 256;
+constexpr int kTgtChunk = 2 * kThreads;
+constexpr int kSrcTile = 512;
 
 __device__ __forceinline__ float rsqrt_fast(float x) {
   float y;
@@ -42,22 +45,76 @@ __device__ __forceinline__ void kahan_add(Acc<R>& s, Acc<R>& c, const Acc<R>& v)
 }
 
 template <class R, class R4, bool MASK>
-__device__ __forceinline__ void tile_sum(const R4* __restrict__ src, int cnt, int g, int G, R xi, R yi, R zi,
-                                         Acc<R>& part) {
+__device__ __forceinline__ void pair(const R4& b, R xi, R yi, R zi, Acc<R>& a) {
+  const R dx = b.x - xi, dy = b.y - yi, dz = b.z - zi;
+  const R r2 = dx * dx + dy * dy + dz * dz;
+  R inv = rsqrt_fast(r2);
+  if (MASK) inv = r2 > (R)0 ? inv : (R)0;
+  const R qi = b.w * inv;
+  a.p += qi;
+  const R f = qi * inv * inv;
+  a.x += f * dx;
+  a.y += f * dy;
+  a.z += f * dz;
+}
+
+template <class R, class R4, bool MASK>
+__device__ __forceinline__ void tile_sum(const R4* __restrict__ src, int k0, int k1, R xa, R ya, R za, R xb,
+                                         R yb, R zb, Acc<R>& pa, Acc<R>& pb) {
 #pragma unroll 4
-  for (int k = g; k < cnt; k += G) {
+  for (int k = k0; k < k1; ++k) {
     const R4 b = src[k];
-    const R dx = b.x - xi, dy = b.y - yi, dz = b.z - zi;
-    const R r2 = dx * dx + dy * dy + dz * dz;
-    R inv = rsqrt_fast(r2);
-    if (MASK) inv = r2 > (R)0 ? inv : (R)0;
-    const R qi = b.w * inv;
-    part.p += qi;
-    const R f = qi * inv * inv;
-    part.x += f * dx;
-    part.y += f * dy;
-    part.z += f * dz;
+    pair<R, R4, MASK>(b, xa, ya, za, pa);
+    pair<R, R4, MASK>(b, xb, yb, zb, pb);
   }
+}
+
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
+               "l"(src)
+               : "memory");
+}
+template <class R4>
+__device__ __forceinline__ void copy_body(R4* dst, const R4* src) {
+  if (sizeof(R4) == 16) {
+    cp_async16(dst, src);
+  } else {
+    cp_async16(dst, src);
+    cp_async16(reinterpret_cast<char*>(dst) + 16, reinterpret_cast<const char*>(src) + 16);
+  }
+}
+
+// Source stream of one leaf: the neighbour ranges [r0, r1) back to back.
+struct Cursor {
+  int r, off;
+};
+
+// Fill one tile from the stream; returns the number of bodies (uniform over
+// the block: every thread walks the same ranges).
+template <class R4>
+__device__ __forceinline__ int fill_tile(R4* tile, const R4* __restrict__ bodies, const int2* __restrict__ ranges,
+                                         Cursor& cur, int r1, const Lim& lim) {
+  int filled = 0;
+  while (filled < kSrcTile && cur.r < r1) {
+    const int2 rg = GB_LD(ranges, cur.r, lim.nranges, 107);
+    const int b = rg.x + cur.off;
+    const int take = min(rg.y - b, kSrcTile - filled);
+    for (int k = threadIdx.x; k < take; k += kThreads) {
+#ifdef GBFMM_CHECKED
+      if (!in_range(b + k, lim.N, 108, lim.rec)) continue;
+#endif
+      copy_body(tile + filled + k, bodies + b + k);
+    }
+    filled += take;
+    if (b + take == rg.y) {
+      ++cur.r;
+      cur.off = 0;
+    } else {
+      cur.off += take;
+    }
+  }
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+  return filled;
 }
 
 template <class R, class R4>
@@ -65,69 +122,88 @@ __global__ void __launch_bounds__(kThreads) k_p2p(const R4* __restrict__ bodies,
                                                   const int32_t* __restrict__ bbeg, const int32_t* __restrict__ bend,
                                                   const int32_t* __restrict__ rptr, const int2* __restrict__ ranges,
                                                   R4* __restrict__ near, Lim lim) {
-  __shared__ R4 src[kSrcTile];
-  __shared__ Acc<R> red[kThreads];
+  __shared__ R4 tiles[2][kSrcTile];
+  __shared__ Acc<R> red[2][kThreads];
   const int li = blockIdx.x;
   const int cell = GB_LD(leaves, li, lim.nleaf, 101);
   const int s = GB_LD(bbeg, cell, lim.ncell, 102), e = GB_LD(bend, cell, lim.ncell, 103);
   const int r0 = GB_LD(rptr, li, lim.nleaf + 1, 104), r1 = GB_LD(rptr, li + 1, lim.nleaf + 1, 105);
   const int tid = threadIdx.x;
-  for (int t0 = s; t0 < e; t0 += kThreads) {
-    const int nt = min(kThreads, e - t0);
-    const int G = kThreads / nt;
-    const int ti = tid % nt, g = tid / nt;
+  for (int t0 = s; t0 < e; t0 += kTgtChunk) {
+    const int nt = min(kTgtChunk, e - t0);
+    const int T2 = (nt + 1) >> 1;
+    const int G = kThreads / T2;
+    const int i = tid % T2, g = tid / T2;
     const bool active = g < G;
-    R xi = 0, yi = 0, zi = 0;
+    const bool has_b = i + T2 < nt;
+    R xa = 0, ya = 0, za = 0, xb = 0, yb = 0, zb = 0;
     if (active) {
-      const R4 b = GB_LD(bodies, t0 + ti, lim.N, 106);
-      xi = b.x;
-      yi = b.y;
-      zi = b.z;
+      const R4 a = GB_LD(bodies, t0 + i, lim.N, 106);
+      xa = a.x;
+      ya = a.y;
+      za = a.z;
+      const R4 b = has_b ? GB_LD(bodies, t0 + i + T2, lim.N, 106) : a;
+      xb = b.x;
+      yb = b.y;
+      zb = b.z;
     }
-    Acc<R> sum{0, 0, 0, 0}, cmp{0, 0, 0, 0};
-    // own leaf (masked), then the merged neighbour ranges
-    for (int r = r0 - 1; r < r1; ++r) {
-      int b0, b1;
-      if (r < r0) {
-        b0 = s;
-        b1 = e;
-      } else {
-        const int2 rg = GB_LD(ranges, r, lim.nranges, 107);
-        b0 = rg.x;
-        b1 = rg.y;
-      }
-      for (int c0 = b0; c0 < b1; c0 += kSrcTile) {
-        const int cnt = min(kSrcTile, b1 - c0);
-        __syncthreads();
-        for (int k = tid; k < cnt; k += kThreads) src[k] = GB_LD(bodies, c0 + k, lim.N, 108);
-        __syncthreads();
-        if (active) {
-          Acc<R> part{0, 0, 0, 0};
-          if (r < r0) tile_sum<R, R4, true>(src, cnt, g, G, xi, yi, zi, part);
-          else tile_sum<R, R4, false>(src, cnt, g, G, xi, yi, zi, part);
-          kahan_add(sum, cmp, part);
-        }
+    Acc<R> sa{0, 0, 0, 0}, ca{0, 0, 0, 0}, sb{0, 0, 0, 0}, cb{0, 0, 0, 0};
+    // own leaf, masked (tiles of the leaf's bodies)
+    for (int c0 = s; c0 < e; c0 += kSrcTile) {
+      const int cnt = min(kSrcTile, e - c0);
+      __syncthreads();
+      for (int k = tid; k < cnt; k += kThreads) copy_body(&tiles[0][k], bodies + c0 + k);
+      asm volatile("cp.async.commit_group;\n" ::: "memory");
+      asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+      __syncthreads();
+      if (active) {
+        const int k0 = (g * cnt) / G, k1 = ((g + 1) * cnt) / G;
+        Acc<R> pa{0, 0, 0, 0}, pb{0, 0, 0, 0};
+        tile_sum<R, R4, true>(tiles[0], k0, k1, xa, ya, za, xb, yb, zb, pa, pb);
+        kahan_add(sa, ca, pa);
+        kahan_add(sb, cb, pb);
       }
     }
+    // neighbour stream, double buffered
+    Cursor cur{r0, 0};
     __syncthreads();
-    red[tid] = sum;
+    int cnt = fill_tile(tiles[0], bodies, ranges, cur, r1, lim);
+    int buf = 0;
+    while (cnt > 0) {
+      const int nxt = fill_tile(tiles[buf ^ 1], bodies, ranges, cur, r1, lim);
+      asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+      __syncthreads();
+      if (active) {
+        const int k0 = (g * cnt) / G, k1 = ((g + 1) * cnt) / G;
+        Acc<R> pa{0, 0, 0, 0}, pb{0, 0, 0, 0};
+        tile_sum<R, R4, false>(tiles[buf], k0, k1, xa, ya, za, xb, yb, zb, pa, pb);
+        kahan_add(sa, ca, pa);
+        kahan_add(sb, cb, pb);
+      }
+      __syncthreads();  // tiles[buf] is refilled two steps later
+      buf ^= 1;
+      cnt = nxt;
+    }
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+    red[0][tid] = sa;
+    red[1][tid] = sb;
     __syncthreads();
     if (active && g == 0) {
-      Acc<R> tot = red[ti];
+      Acc<R> ta = red[0][i], tb = red[1][i];
       for (int gg = 1; gg < G; ++gg) {
-        const Acc<R> v = red[gg * nt + ti];
-        tot.p += v.p;
-        tot.x += v.x;
-        tot.y += v.y;
-        tot.z += v.z;
+        const Acc<R> va = red[0][gg * T2 + i], vb = red[1][gg * T2 + i];
+        ta.p += va.p; ta.x += va.x; ta.y += va.y; ta.z += va.z;
+        tb.p += vb.p; tb.x += vb.x; tb.y += vb.y; tb.z += vb.z;
       }
       R4 o;
-      o.x = tot.p;
-      o.y = tot.x;
-      o.z = tot.y;
-      o.w = tot.z;
-      GB_ST(near, t0 + ti, lim.N, 109, o);
+      o.x = ta.p; o.y = ta.x; o.z = ta.y; o.w = ta.z;
+      GB_ST(near, t0 + i, lim.N, 109, o);
+      if (has_b) {
+        o.x = tb.p; o.y = tb.x; o.z = tb.y; o.w = tb.z;
+        GB_ST(near, t0 + i + T2, lim.N, 109, o);
+      }
     }
+    __syncthreads();
   }
 }
 

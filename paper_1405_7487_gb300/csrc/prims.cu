@@ -7,7 +7,12 @@
 
 namespace gbfmm {
 
-void fail(int code, const char* what) { throw Error{code, what ? what : ""}; }
+thread_local std::string g_last_error;
+
+void fail(int code, const char* what) {
+  g_last_error = what ? what : "";
+  throw Error{code, g_last_error};
+}
 
 std::atomic<long long> g_launches{0};
 
@@ -16,8 +21,8 @@ void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 void check_cuda(cudaError_t e, const char* what) {
   if (e == cudaSuccess) return;
   cudaGetLastError();  // clear a sticky launch error of this thread
-  if (e == cudaErrorMemoryAllocation) fail(FMM_ERR_OOM, what);
-  fail(FMM_ERR_CUDA, what);
+  std::string msg = std::string(what ? what : "") + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
+  fail(e == cudaErrorMemoryAllocation ? FMM_ERR_OOM : FMM_ERR_CUDA, msg.c_str());
 }
 
 void* Arena::alloc(size_t n) {
@@ -273,3 +278,5 @@ void radix_sort_keys(Arena& a, uint64_t*& keys, int64_t n, int bits, cudaStream_
 }  // namespace gbfmm
 
 extern "C" int64_t fmm_launch_count(void) { return (int64_t)gbfmm::g_launches.load(); }
+
+extern "C" const char* fmm_last_error(void) { return gbfmm::g_last_error.c_str(); }

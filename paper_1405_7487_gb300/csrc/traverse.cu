@@ -127,6 +127,12 @@ __global__ void k_trav_write(const int2* __restrict__ fr, int64_t n, CellView c,
   }
 }
 
+__global__ void k_pack_pairs(const int32_t* __restrict__ tgt, const int32_t* __restrict__ src, int64_t n,
+                             uint64_t* __restrict__ k) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) k[i] = ((uint64_t)(uint32_t)tgt[i] << 32) | (uint32_t)src[i];
+}
+
 __global__ void k_unpack_pairs(const uint64_t* __restrict__ k, int64_t n, int32_t* __restrict__ tgt,
                                int32_t* __restrict__ src) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -139,33 +145,38 @@ __global__ void k_unpack_pairs(const uint64_t* __restrict__ k, int64_t n, int32_
 // self pairs dropped (the kernel treats a leaf's own bodies separately).
 __global__ void k_p2p_range_keys(const int32_t* __restrict__ tgt, const int32_t* __restrict__ src,
                                  int64_t n, const int32_t* __restrict__ leaf_of,
-                                 const int32_t* __restrict__ bbeg, uint64_t* __restrict__ key,
+                                 const int32_t* __restrict__ bbeg, int nb, uint64_t* __restrict__ key,
                                  int32_t* __restrict__ val, unsigned long long* __restrict__ pairs,
                                  const int32_t* __restrict__ bend) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  // body-pair count: warp sums, one atomic per warp
+  unsigned long long np = 0;
+  if (i < n) np = (unsigned long long)(bend[tgt[i]] - bbeg[tgt[i]]) * (unsigned long long)(bend[src[i]] - bbeg[src[i]]);
+  for (int o = 16; o > 0; o >>= 1) np += __shfl_down_sync(0xffffffffu, np, o);
+  if ((threadIdx.x & 31) == 0 && np) atomicAdd(pairs, np);
   if (i >= n) return;
   const int t = tgt[i], s = src[i];
-  const int64_t nt = bend[t] - bbeg[t], ns = bend[s] - bbeg[s];
-  atomicAdd(pairs, (unsigned long long)(nt * ns));
   if (t == s) {
     key[i] = ~0ull;  // sorts last, ignored
     val[i] = -1;
     return;
   }
-  key[i] = ((uint64_t)(uint32_t)leaf_of[t] << 32) | (uint32_t)bbeg[s];
+  key[i] = ((uint64_t)(uint32_t)leaf_of[t] << nb) | (uint32_t)bbeg[s];
   val[i] = s;
 }
 
-// Position of the first key >= (leaf << 32) for every leaf (and the end).
-__global__ void k_leaf_entry_ptr(const uint64_t* __restrict__ key, int64_t n, int nleaf,
+// Position of the first key >= (leaf << nb) for every leaf (and the end);
+// keys are compared on their low `bits` bits (the sorted ones).
+__global__ void k_leaf_entry_ptr(const uint64_t* __restrict__ key, int64_t n, int nleaf, int nb, int bits,
                                  int64_t* __restrict__ ptr) {
   const int l = blockIdx.x * blockDim.x + threadIdx.x;
   if (l > nleaf) return;
-  const uint64_t want = (uint64_t)(uint32_t)l << 32;
+  const uint64_t mask = bits >= 64 ? ~0ull : ((1ull << bits) - 1);
+  const uint64_t want = (uint64_t)(uint32_t)l << nb;
   int64_t lo = 0, hi = n;
   while (lo < hi) {
     int64_t mid = (lo + hi) >> 1;
-    if (key[mid] < want) lo = mid + 1;
+    if ((key[mid] & mask) < want) lo = mid + 1;
     else hi = mid;
   }
   ptr[l] = lo;
@@ -209,13 +220,27 @@ __global__ void k_i64_to_i32(const int64_t* __restrict__ a, int64_t n, int32_t* 
   if (i < n) b[i] = (int32_t)a[i];
 }
 
+}  // namespace
+
+// Smallest b with 2^b > v.
 int bits_for(int64_t v) {
   int b = 0;
   while (b < 63 && (1ll << b) <= v) ++b;
   return b;
 }
 
-}  // namespace
+// (target, source) order of a directed pair list, for the inspection call.
+void sort_pairs_copy(Arena& a, const int32_t* tgt, const int32_t* src, int64_t n, int ncell, int32_t* out_tgt,
+                     int32_t* out_src, cudaStream_t s) {
+  if (n == 0) return;
+  uint64_t* k = alloc_n<uint64_t>(a, n);
+  k_pack_pairs<<<blocks(n), kThreads, 0, s>>>(tgt, src, n, k);
+  GB_LAUNCH("k_pack_pairs");
+  radix_sort_keys(a, k, n, 32 + bits_for(ncell), s);
+  k_unpack_pairs<<<blocks(n), kThreads, 0, s>>>(k, n, out_tgt, out_src);
+  GB_LAUNCH("k_unpack_pairs");
+  a.release(k);
+}
 
 void build_lists(fmm_tree* t) {
   Arena& a = t->arena;
@@ -272,10 +297,9 @@ void build_lists(fmm_tree* t) {
   }
   a.release(fr);
 
-  // --- sort the directed pairs by (target, source)
-  const int cbits = bits_for(t->ncell);
-  radix_sort_keys(a, m2l, nm, 32 + cbits, s);
-  radix_sort_keys(a, p2p, np, 32 + cbits, s);
+  // The pairs stay in traversal order (deterministic: every offset comes from
+  // an exclusive scan); only the inspection call sorts a copy by (target,
+  // source).  Nothing on the evaluation path depends on that order.
   t->n_m2l = nm;
   t->n_p2p = np;
   t->m2l_tgt = alloc_n<int32_t>(a, nm);
@@ -296,12 +320,15 @@ void build_lists(fmm_tree* t) {
   int32_t* rval = alloc_n<int32_t>(a, np);
   unsigned long long* d_pairs = alloc_n<unsigned long long>(a, 1);
   GB_CK(cudaMemsetAsync(d_pairs, 0, sizeof(unsigned long long), s));
+  // key = (leaf, body_begin) in lb + nb bits; 2^lb > nleaf and 2^nb > N, so a
+  // real key is never the all-ones key of a self pair
+  const int nb = bits_for(t->N), lb = bits_for(t->nleaf);
   k_p2p_range_keys<<<blocks(np), kThreads, 0, s>>>(t->p2p_tgt, t->p2p_src, np, t->leaf_of_cell,
-                                                   t->c.bbeg, rkey, rval, d_pairs, t->c.bend);
+                                                   t->c.bbeg, nb, rkey, rval, d_pairs, t->c.bend);
   GB_LAUNCH("k_p2p_range_keys");
-  radix_sort_pairs(a, rkey, rval, np, 64, s);
+  radix_sort_pairs(a, rkey, rval, np, lb + nb, s);
   int64_t* eptr = alloc_n<int64_t>(a, t->nleaf + 1);
-  k_leaf_entry_ptr<<<blocks(t->nleaf + 1), kThreads, 0, s>>>(rkey, np, t->nleaf, eptr);
+  k_leaf_entry_ptr<<<blocks(t->nleaf + 1), kThreads, 0, s>>>(rkey, np, t->nleaf, nb, lb + nb, eptr);
   GB_LAUNCH("k_leaf_entry_ptr");
   // the self entries (key ~0) sort last; cap the last leaf at the non-self count
   int64_t* rcount = alloc_n<int64_t>(a, t->nleaf + 1);

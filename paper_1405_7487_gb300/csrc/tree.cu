@@ -80,15 +80,25 @@ __global__ void k_bbox_partial(const R* __restrict__ xyzq, int64_t n, double* __
 // double operations: no fused multiply-add may change the keys.
 __global__ void k_bbox_final(const double* __restrict__ part, int nb, double* __restrict__ root,
                              int* __restrict__ nonfinite) {
-  if (threadIdx.x != 0) return;
-  double r[7];
-  for (int k = 0; k < 7; ++k) r[k] = part[k];
-  for (int b = 1; b < nb; ++b) {
+  // min/max are exact, so the reduction order does not matter
+  __shared__ double sh[kThreads][7];
+  double r[7] = {INFINITY, INFINITY, INFINITY, -INFINITY, -INFINITY, -INFINITY, 0.0};
+  for (int b = threadIdx.x; b < nb; b += blockDim.x) {
     for (int a = 0; a < 3; ++a) {
       r[a] = fmin(r[a], part[7 * b + a]);
       r[3 + a] = fmax(r[3 + a], part[7 * b + 3 + a]);
     }
     r[6] = fmax(r[6], part[7 * b + 6]);
+  }
+  for (int k = 0; k < 7; ++k) sh[threadIdx.x][k] = r[k];
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  for (int t = 1; t < (int)blockDim.x; ++t) {
+    for (int a = 0; a < 3; ++a) {
+      r[a] = fmin(r[a], sh[t][a]);
+      r[3 + a] = fmax(r[3 + a], sh[t][3 + a]);
+    }
+    r[6] = fmax(r[6], sh[t][6]);
   }
   *nonfinite = r[6] != 0.0;
   double h = 0.0;
@@ -259,7 +269,7 @@ void build_tree_impl(fmm_tree* t, const R* xyzq) {
   int* d_bad = alloc_n<int>(a, 1);
   k_bbox_partial<R><<<nb, kThreads, 0, s>>>(xyzq, N, part);
   GB_LAUNCH("k_bbox_partial");
-  k_bbox_final<<<1, 32, 0, s>>>(part, nb, t->d_root, d_bad);
+  k_bbox_final<<<1, kThreads, 0, s>>>(part, nb, t->d_root, d_bad);
   GB_LAUNCH("k_bbox_final");
   double hroot[13];
   int hbad = 0;

@@ -34,7 +34,8 @@ class FMMError(RuntimeError):
     def __init__(self, code: int, where: str):
         self.code = code
         self.name = _ERRORS.get(code, str(code))
-        super().__init__(f"{where}: {self.name} ({lib().fmm_strerror(code).decode()})")
+        detail = lib().fmm_last_error().decode(errors="replace")
+        super().__init__(f"{where}: {self.name} ({lib().fmm_strerror(code).decode()}) {detail}")
 
 
 class Stats(ctypes.Structure):
@@ -46,6 +47,7 @@ class Stats(ctypes.Structure):
                 ("ncrit", ctypes.c_int32), ("precision_bits", ctypes.c_int32), ("theta", ctypes.c_double),
                 ("flags", ctypes.c_uint32), ("m2l_engine", ctypes.c_int32),
                 ("workspace_bytes", ctypes.c_int64), ("evaluations", ctypes.c_int32),
+                ("device_errors", ctypes.c_int32),
                 ("ms", ctypes.c_float * 8)]
 
 
@@ -89,6 +91,8 @@ def lib():
             f.restype = ctypes.c_int
         L.fmm_launch_count.argtypes = []
         L.fmm_launch_count.restype = ctypes.c_int64
+        L.fmm_last_error.argtypes = []
+        L.fmm_last_error.restype = ctypes.c_char_p
         L.fmm_strerror.argtypes = [ctypes.c_int]
         L.fmm_strerror.restype = ctypes.c_char_p
         _lib = L

@@ -348,3 +348,24 @@ def test_plan_in_bounds_and_covers_lists(fmm, name, f64):
         for a, b in want[int(cell)]:
             ref[a:b] += 1
         assert np.array_equal(cover, ref)
+
+
+@pytest.mark.parametrize("name", ["cube4k_p4", "cube65k_p10", "cube20k_p16", "cube3k_p1", "sphere40k_p6"])
+def test_m2l_engines_agree(fmm, name):
+    """The tensor-core M2L (3xTF32, tcgen05) and the CUDA-core M2L give the same
+    local expansions to single-precision accuracy."""
+    gen, p, theta, ncrit = CASES[name]
+    x = gen()
+    A = gpu_tree(fmm, x, p, theta, ncrit)
+    B = gpu_tree(fmm, x, p, theta, ncrit, fmm.FMM_FLAG_M2L_CUDA_CORE)
+    assert A.stats()["m2l_engine"] == 1 and B.stats()["m2l_engine"] == 0
+    pa, fa = evaluate(A)
+    pb, fb = evaluate(B)
+    La = A.expansions()[1].astype(np.float64)
+    Lb = B.expansions()[1].astype(np.float64)
+    # 3xTF32 products with TF32-rounded halves and chunked fp32 accumulation
+    # differ from plain fp32 by a few 1e-6 (both are checked against the
+    # oracle by the other tests)
+    assert rel(La, Lb) < 3e-5
+    assert rel(pa, pb) < 1e-5 and rel(fa, fb) < 5e-5
+    assert A.stats()["device_errors"] == 0
