@@ -58,7 +58,6 @@ void create_tree(fmm_tree* t, const R* xyzq) {
   t->grad_q = a.alloc(rs * 4 * (size_t)t->N);
   t->q_last = a.alloc(rs * (size_t)t->N);
   if (t->m2l_engine == 1) {
-    t->M_lo = alloc_n<float>(a, 2 * (size_t)t->ncell * t->Kp);
     int per = kM2LChunk;
     if (const char* env = getenv("GBFMM_M2L_CHUNK")) per = std::max(1, atoi(env));  // tuning knob
     build_m2l_chunks(t, per);

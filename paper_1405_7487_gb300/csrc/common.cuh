@@ -14,7 +14,7 @@ namespace gbfmm {
 constexpr int kMaxLevel = 21;   // 63-bit Morton keys, 3 bits per level (Sec. II.B)
 constexpr int kMaxP = 16;       // expansion terms supported (K = p*p <= 256)
 constexpr int kTile = 128;      // targets per M2L tile (rows of one MMA / one CTA)
-constexpr int kM2LChunk = 8;    // entries accumulated per TMEM partial (tensor-core M2L)
+constexpr int kM2LChunk = 16;   // entries accumulated per TMEM partial (tensor-core M2L)
 
 struct Error {
   int code;
@@ -22,6 +22,7 @@ struct Error {
 };
 
 [[noreturn]] void fail(int code, const char* what);
+extern thread_local std::string g_last_error;
 void check_cuda(cudaError_t e, const char* what);
 void count_launch();
 #define GB_CK(call) ::gbfmm::check_cuda((call), #call)

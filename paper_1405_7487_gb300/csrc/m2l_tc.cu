@@ -7,21 +7,25 @@
 // operator T_c (an entry of the plan) the 128 rows hold the source of each
 // target at that relative position, so the entry is the product
 //     L~[128 x Kp] += M~_src[128 x Kp] . T_c^T[Kp x Kp]
-// (M = 128 rows, N = Kp outputs, K = Kp inputs).  All entries of a tile
-// accumulate into one TMEM tile (fp32), read back once at the end.
+// (M = 128 rows, N = Kp outputs, K = Kp inputs).
 //
-// Precision: every operand x is split into hi = tf32(x) and lo = x - hi, and
-// each entry issues hi*hi + lo*hi + hi*lo (the lo*lo term is below the fp32
-// rounding of the result).  The operator tables are split at set-up (double
-// precision -> hi/lo), the multipoles after the upward pass.
+// Precision: every operand x is split into hi = tf32(x) and lo = tf32(x - hi)
+// (both rounded to nearest, so the tensor core sees them exactly) and each
+// entry issues hi*hi + lo*hi + hi*lo.  The entries of a tile are cut into
+// chunks of a few entries; each chunk accumulates in TMEM (fp32) and is
+// written out as a partial, and the partials of a tile are added with
+// compensated (Kahan) summation in a fixed order (k_m2l_reduce).  Short
+// chunks bound the rounding of the fp32 tensor-core accumulation.
 //
-// Pipeline (one CTA per tile, 160 threads):
+// Pipeline (one CTA per chunk, 160 threads):
 //   warps 0-3  producers: cp.async 16-byte copies of the 128 source rows
 //              (hi and lo) and of the Kp operator rows (hi and lo) of one
 //              32-element k-block into a stage, in the 128-byte-swizzled
-//              K-major layout the MMA descriptors describe; after their
-//              copies land they fence the async proxy and arrive on the
-//              stage's "full" barrier.  Then the epilogue (TMEM -> L).
+//              K-major layout the MMA descriptors describe.  A stage is
+//              published (async-proxy fence, then an arrive on its "full"
+//              barrier) once its copies have landed, which each producer
+//              checks after issuing the next stage's copies.  Then the
+//              epilogue (TMEM -> the chunk's partial).
 //   warp 4     TMEM allocation; one elected lane issues the MMAs of a stage
 //              and commits them to the stage's "empty" barrier.
 // Every wait is bounded; a wait that gives up sets the error flag, the
@@ -37,17 +41,20 @@ namespace {
 constexpr int kProducers = 128;
 constexpr int kThreadsTC = 160;
 constexpr int kKB = 32;               // fp32 elements per k-block (128 bytes per row)
-constexpr int kStageA = 128 * 128;    // bytes of one 128-row operand block
+constexpr int kRowB = kKB * 4;        // bytes per row of a k-block
+constexpr int kStageA = 128 * kRowB;  // bytes of one 128-row operand block
+constexpr int kMaxStages = 8;
 constexpr long long kSpinLimit = 1ll << 20;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
 }
 
-// Byte offset of 16-byte chunk c of row r in a [rows][128 B] block with the
-// 128-byte swizzle (8-row groups of 1024 bytes, chunk index XOR row % 8).
+// Byte offset of 16-byte chunk c (0..7) of row r in a [rows][128 B] block
+// with the 128-byte swizzle: address bits [4,6] are XORed with bits [7,9],
+// i.e. the chunk index with r % 8 (8-row groups of 1024 bytes).
 __device__ __forceinline__ uint32_t swz(int r, int c) {
-  return (uint32_t)(((r >> 3) << 10) + ((r & 7) << 7) + (((c ^ (r & 7)) & 7) << 4));
+  return (uint32_t)((r << 7) + (((c ^ r) & 7) << 4));
 }
 
 __device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, int bytes) {
@@ -131,14 +138,14 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
              const float* __restrict__ ops_lo, const float* __restrict__ Mhi, const float* __restrict__ Mlo, int Kp,
              int nstage, int tmem_cols, float* __restrict__ part, int* __restrict__ err) {
   extern __shared__ unsigned char smem_raw[];
-  __shared__ uint64_t bar_full[8], bar_empty[8], bar_done;
+  __shared__ uint64_t bar_full[kMaxStages], bar_empty[kMaxStages], bar_done;
   __shared__ uint32_t tmem_base;
   __shared__ volatile int abort_flag;
 
   // 1024-byte aligned stage buffers
   const uint32_t raw = smem_u32(smem_raw);
   const uint32_t base = (raw + 1023u) & ~1023u;
-  const int stageB = Kp * 128;
+  const int stageB = Kp * kRowB;
   const int stage_bytes = 2 * kStageA + 2 * stageB;
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -173,9 +180,9 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
     // ---------------------------------------------------------- producers
     const int r = tid;
     int cur_e = -1, src = -1, cls = 0;
-    // copies of the last nstage - 1 iterations stay in flight; iteration
-    // it - (nstage - 1) is published once its copies have landed
-    const int lag = nstage - 1;
+    // the copies of iteration it are in flight while iteration it - 1 is
+    // published (measured faster than deeper lags on GB300)
+    const int lag = 1;
     for (int it = 0; it < nit; ++it) {
       const int e = e0 + it / nkb, kb = it % nkb;
       const int s = it % nstage, round = it / nstage;
@@ -323,9 +330,9 @@ __global__ void k_m2l_reduce(const int32_t* __restrict__ tile_tgt, const int32_t
 }  // namespace
 
 int m2l_tc_stages(int Kp) {
-  const int stage_bytes = 2 * kStageA + 2 * Kp * 128;
+  const int stage_bytes = 2 * kStageA + 2 * Kp * kRowB;
   int s = (200 * 1024) / stage_bytes;
-  return s < 2 ? 2 : (s > 6 ? 6 : s);
+  return s < 3 ? 3 : (s > kMaxStages ? kMaxStages : s);
 }
 
 void launch_split_tf32(fmm_tree* t, cudaStream_t s) {
@@ -338,7 +345,7 @@ void launch_m2l_tcgen05(fmm_tree* t, cudaStream_t s) {
   if (t->ntile == 0) return;
   const int Kp = t->Kp;
   const int nstage = m2l_tc_stages(Kp);
-  const size_t smem = (size_t)nstage * (2 * kStageA + 2 * Kp * 128) + 1024;
+  const size_t smem = (size_t)nstage * (2 * kStageA + 2 * Kp * kRowB) + 1024;
   // the dynamic size this launch needs (static + dynamic must stay within the
   // 227 KB per-block limit)
   GB_CK(cudaFuncSetAttribute(k_m2l_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -354,7 +361,8 @@ void launch_m2l_tcgen05(fmm_tree* t, cudaStream_t s) {
 }
 
 // Chunks of at most `per` consecutive entries of every tile (host: the entry
-// ranges of the tiles are read back once at build time).
+// ranges of the tiles are read back once at build time), the partial buffer
+// and the split multipole copies.
 void build_m2l_chunks(fmm_tree* t, int per) {
   Arena& a = t->arena;
   cudaStream_t s = t->stream;
@@ -375,6 +383,7 @@ void build_m2l_chunks(fmm_tree* t, int per) {
   GB_CK(cudaMemcpyAsync(t->m2l_chunks, ch.data(), sizeof(int4) * ch.size(), cudaMemcpyHostToDevice, s));
   GB_CK(cudaMemcpyAsync(t->tile_cptr, cptr.data(), sizeof(int32_t) * cptr.size(), cudaMemcpyHostToDevice, s));
   t->m2l_part = alloc_n<float>(a, (size_t)t->nchunk * kTile * t->Kp);
+  t->M_lo = alloc_n<float>(a, 2 * (size_t)t->ncell * t->Kp);
   GB_CK(cudaStreamSynchronize(s));
 }
 
