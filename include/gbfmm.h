@@ -239,6 +239,31 @@ int fmm_get_expansions(const fmm_tree* t, void* M, void* L, fmm_stream stream);
 int fmm_get_plan(const fmm_tree* t, int32_t* tile_tgt, int32_t* tile_eptr, int32_t* entry_class,
                  int32_t* entry_src, int32_t* p2p_rptr, int32_t* p2p_ranges, fmm_stream stream);
 
+/*
+ * fmm_root_keys_noalloc: the root cube and the Morton keys of fmm_build's
+ * first step (same results, bit for bit), without allocating any device
+ * memory.  The paper has no counterpart; this exists for callers that may
+ * not allocate while they call this library: code under a fixed
+ * device-memory budget or inside another framework's allocator, and code
+ * that must not risk the device-wide synchronisation a cudaMalloc/cudaFree
+ * can cause.  The reduction's scratch is a fixed file-scope device array
+ * (about 57 KB per device, held until the process exits).
+ *   xyzq       device, n x 4 float (x, y, z, q), input order.
+ *   n          1 <= n <= 2^31 - 1; larger n returns FMM_ERR_ARG
+ *              (fmm_last_error says why).
+ *   root       device, 13 doubles, the layout of fmm_get_root.
+ *   keys       device, n uint64 Morton keys in input order, or NULL.
+ *   nonfinite  device int32, set to 1 if a position or charge is NaN or
+ *              infinite (root and keys are then undefined), else 0; or NULL.
+ * Stream-ordered and asynchronous.  The first call on a device looks up the
+ * device address of the scratch array, so make that first call before any
+ * stream capture.  All calls share the one scratch array: calls whose work
+ * overlaps on the GPU (other streams, other host threads) race and must be
+ * ordered by the caller.
+ */
+int fmm_root_keys_noalloc(const float* xyzq, int64_t n, double* root, uint64_t* keys, int32_t* nonfinite,
+                          fmm_stream stream);
+
 /* host out[4]: record of the self-checking build (compiled with
  * -DGBFMM_CHECKED): site code and index of the first out-of-range access the
  * evaluation kernels skipped, the bound it broke, and the number of such

@@ -4,6 +4,8 @@
 // N_crit is the maximum number of bodies per leaf).
 #include <algorithm>
 #include <cmath>
+#include <mutex>
+#include <string>
 
 #include "common.cuh"
 
@@ -394,3 +396,94 @@ void build_tree(fmm_tree* t, const void* xyzq, bool f64) {
 }
 
 }  // namespace gbfmm
+
+// ---------------------------------------------------------------------------
+// Allocation-free root cube and Morton keys.
+//
+// The paper has no counterpart of this entry point.  It serves callers that
+// may not allocate device memory while they call this library: code running
+// under a fixed device-memory budget or inside another framework's allocator
+// (which owns every allocation), and code that must not trigger the device-
+// wide synchronisation a cudaMalloc/cudaFree can cause in the middle of its
+// own stream work.  It is the first step of fmm_build (bounding cube and
+// keys) with the reduction's scratch held in a fixed file-scope device array
+// instead of workspace from an allocator.
+namespace gbfmm {
+namespace {
+
+constexpr int kNoAllocBlocks = 1024;  // partial boxes of at most 1024 blocks
+constexpr int kNoAllocBodies = 0x7fffffff;
+
+// Partial bounding boxes (7 doubles per block) and the non-finite flag used
+// when the caller passes none.  One copy per device, kept until exit
+// (about 57 KB); every call overwrites it.
+static __device__ __align__(256) double g_noalloc_scratch[kNoAllocBlocks * 7 + 32];
+
+// Keys only (the allocating path also writes the identity permutation).
+__global__ void k_keys_noalloc(const float* __restrict__ xyzq, int64_t n, const double* __restrict__ root,
+                               uint64_t* __restrict__ keys) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double side = __dadd_rn(root[9], root[9]);
+  uint64_t key = 0;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    double d = __dsub_rn((double)xyzq[4 * i + a], root[10 + a]);
+    double s = __dmul_rn(__ddiv_rn(d, side), 2097152.0);
+    double f = floor(s);
+    int64_t k = (int64_t)f;
+    k = k < 0 ? 0 : (k > 2097151 ? 2097151 : k);
+    key |= spread_bits((uint64_t)k) << (2 - a);
+  }
+  keys[i] = key;
+}
+
+std::mutex g_noalloc_mu;
+double* g_noalloc_ptr[64] = {};
+
+}  // namespace
+}  // namespace gbfmm
+
+extern "C" int fmm_root_keys_noalloc(const float* xyzq, int64_t n, double* root, uint64_t* keys,
+                                     int32_t* nonfinite, fmm_stream stream) {
+  using namespace gbfmm;
+  if (!xyzq || !root || n < 1) return FMM_ERR_ARG;
+  if (n > kNoAllocBodies) {
+    g_last_error = "fmm_root_keys_noalloc: n exceeds the maximum of 2^31 - 1 bodies";
+    return FMM_ERR_ARG;
+  }
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+    cudaGetLastError();
+    return FMM_ERR_CUDA;
+  }
+  double* scratch = nullptr;
+  {
+    // once per device, with that device current: the device address of the
+    // scratch array (the host-side symbol is only a stand-in for it)
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+      void* p = nullptr;
+      cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+      if (e != cudaSuccess || !p) {
+        cudaGetLastError();
+        g_last_error = "fmm_root_keys_noalloc: cudaGetSymbolAddress failed";
+        return FMM_ERR_CUDA;
+      }
+      g_noalloc_ptr[dev] = static_cast<double*>(p);
+    }
+    scratch = g_noalloc_ptr[dev];
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  const int nb = (int)std::min<int64_t>(kNoAllocBlocks, (n + kThreads - 1) / kThreads);
+  int* flag = nonfinite ? nonfinite : reinterpret_cast<int*>(scratch + kNoAllocBlocks * 7);
+  k_bbox_partial<float><<<nb, kThreads, 0, s>>>(xyzq, n, scratch);
+  k_bbox_final<<<1, kThreads, 0, s>>>(scratch, nb, root, flag);
+  if (keys) k_keys_noalloc<<<(unsigned)((n + kThreads - 1) / kThreads), kThreads, 0, s>>>(xyzq, n, root, keys);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    g_last_error = std::string("fmm_root_keys_noalloc: ") + cudaGetErrorName(e);
+    return FMM_ERR_CUDA;
+  }
+  return FMM_OK;
+}
