@@ -127,9 +127,9 @@ struct fmm_tree {
   void* L = nullptr;  // ncell x Kp
   float* M_lo = nullptr;  // split copy of M for the 3xTF32 engine (lo | hi)
   int nchunk = 0;                  // M2L work units of the tensor-core engine
-  int4* m2l_chunks = nullptr;      // (tile, first entry, end entry, 0)
-  int32_t* tile_cptr = nullptr;    // chunks of tile t: [cptr[t], cptr[t+1])
-  float* m2l_part = nullptr;       // nchunk x kTile x Kp partial local expansions
+  int4* m2l_chunks = nullptr;      // (tile, first entry, end entry, partial slot)
+  int32_t* tile_cptr = nullptr;    // partial slots of tile t: [cptr[t], cptr[t+1])
+  float* m2l_part = nullptr;       // nchunk x Kp x kTile partial local expansions
   void* near = nullptr;   // N x 4 (phi, grad) sorted, P2P part
   void* grad_q = nullptr; // N x 4 (phi, grad) sorted, of the last evaluate
   void* q_last = nullptr; // N sorted charges of the last evaluate

@@ -179,7 +179,12 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
   if (warp < 4) {
     // ---------------------------------------------------------- producers
     const int r = tid;
-    int cur_e = -1, src = -1, cls = 0;
+    // A copies: thread r moves 16-byte chunk (r % 8) of tile rows
+    // r / 8 + 16 i (i = 0..7), so eight neighbouring threads read one
+    // 128-byte row segment and write one swizzled 128-byte line
+    const int cA = r & 7, rA = r >> 3;
+    int src[8];
+    int cur_e = -1, cls = 0;
     // the copies of iteration it are in flight while iteration it - 1 is
     // published (measured faster than deeper lags on GB300)
     const int lag = 1;
@@ -189,19 +194,23 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
       if (round > 0 && !mbar_wait(smem_u32(&bar_empty[s]), (round - 1) & 1, &abort_flag)) break;
       if (e != cur_e) {
         cur_e = e;
-        src = entry_src[(int64_t)e * kTile + r];
-        cls = entry_class[e];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) src[i] = __ldg(entry_src + (int64_t)e * kTile + rA + 16 * i);
+        cls = __ldg(entry_class + e);
       }
       const uint32_t sb = base + s * stage_bytes;
       const int k0 = kb * kKB;
       const int nch = min(kKB, Kp - k0) / 4;  // 16-byte chunks in this k-block
-      // A rows: the source multipole of tile row r (zeros for an empty row)
-      const float* ah = Mhi + (int64_t)(src >= 0 ? src : 0) * Kp + k0;
-      const float* al = Mlo + (int64_t)(src >= 0 ? src : 0) * Kp + k0;
-      const int bytes = src >= 0 ? 16 : 0;
-      for (int c = 0; c < nch; ++c) {
-        cp_async16(sb + swz(r, c), ah + 4 * c, bytes);
-        cp_async16(sb + kStageA + swz(r, c), al + 4 * c, bytes);
+      // A rows: the source multipole of each tile row (zeros for an empty row)
+      if (cA < nch) {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          const int row = rA + 16 * i;
+          const int64_t off = (int64_t)(src[i] >= 0 ? src[i] : 0) * Kp + k0 + 4 * cA;
+          const int bytes = src[i] >= 0 ? 16 : 0;
+          cp_async16(sb + swz(row, cA), Mhi + off, bytes);
+          cp_async16(sb + kStageA + swz(row, cA), Mlo + off, bytes);
+        }
       }
       // B rows: output coefficient rows of the operator
       const float* oh = ops_hi + (int64_t)cls * Kp * Kp + k0;
@@ -226,7 +235,9 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
     const bool ok = nit > 0 && mbar_wait(smem_u32(&bar_done), 0, &abort_flag);
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
     if (ok || nit == 0) {
-      float* lrow = part + ((int64_t)blockIdx.x * kTile + r) * Kp;
+      // partial slot ch.w, column-major ([Kp][128]): a warp's store of one
+      // column is 128 contiguous bytes
+      float* pcol = part + (int64_t)ch.w * kTile * Kp + r;
       for (int c0 = 0; c0 < Kp; c0 += 16) {
         uint32_t v[16];
         if (nit > 0) {
@@ -242,10 +253,8 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
         } else {
           for (int k = 0; k < 16; ++k) v[k] = 0u;
         }
-        float4* dst = reinterpret_cast<float4*>(lrow + c0);
-        for (int k = 0; k < 4; ++k)
-          dst[k] = make_float4(__uint_as_float(v[4 * k]), __uint_as_float(v[4 * k + 1]), __uint_as_float(v[4 * k + 2]),
-                               __uint_as_float(v[4 * k + 3]));
+#pragma unroll
+        for (int k = 0; k < 16; ++k) __stcs(pcol + (int64_t)(c0 + k) * kTile, __uint_as_float(v[k]));
       }
     }
   } else if (lane == 0) {
@@ -307,18 +316,19 @@ __global__ void k_split_tf32(const float* __restrict__ x, int64_t n, float* __re
 }
 
 // L rows of one tile = compensated (Kahan) sum of its chunks' partials, in
-// chunk order.  Thread per (row, coefficient).
+// chunk order.  Thread per (coefficient, row), rows fastest (the partials
+// are column-major).
 __global__ void k_m2l_reduce(const int32_t* __restrict__ tile_tgt, const int32_t* __restrict__ tile_cptr,
                              const float* __restrict__ part, int K, int Kp, float* __restrict__ L) {
   const int tile = blockIdx.x;
   const int c0 = tile_cptr[tile], c1 = tile_cptr[tile + 1];
-  for (int w = threadIdx.x; w < kTile * Kp; w += blockDim.x) {
-    const int r = w / Kp, c = w % Kp;
+  for (int w = threadIdx.x; w < kTile * K; w += blockDim.x) {
+    const int c = w / kTile, r = w % kTile;
     const int tgt = tile_tgt[(int64_t)tile * kTile + r];
-    if (tgt < 0 || c >= K) continue;
+    if (tgt < 0) continue;
     float sum = 0.f, comp = 0.f;
     for (int ch = c0; ch < c1; ++ch) {
-      const float y = part[((int64_t)ch * kTile + r) * Kp + c] - comp;
+      const float y = __ldcs(part + ((int64_t)ch * Kp + c) * kTile + r) - comp;
       const float tt = sum + y;
       comp = (tt - sum) - y;
       sum = tt;
@@ -331,8 +341,8 @@ __global__ void k_m2l_reduce(const int32_t* __restrict__ tile_tgt, const int32_t
 
 int m2l_tc_stages(int Kp) {
   const int stage_bytes = 2 * kStageA + 2 * Kp * kRowB;
-  int s = (200 * 1024) / stage_bytes;
-  return s < 3 ? 3 : (s > kMaxStages ? kMaxStages : s);
+  int s = (200 * 1024) / stage_bytes;  // two stages still fit at Kp = 256
+  return s < 2 ? 2 : (s > kMaxStages ? kMaxStages : s);
 }
 
 void launch_split_tf32(fmm_tree* t, cudaStream_t s) {
@@ -362,21 +372,30 @@ void launch_m2l_tcgen05(fmm_tree* t, cudaStream_t s) {
 
 // Chunks of at most `per` consecutive entries of every tile (host: the entry
 // ranges of the tiles are read back once at build time), the partial buffer
-// and the split multipole copies.
+// and the split multipole copies.  Partial slots are numbered tile by tile
+// (chunk .w); the launch order is chunk-within-tile major, so the CTAs that
+// run at the same time work on the same stretch of every tile's class list
+// and share the translation operators in L2.
 void build_m2l_chunks(fmm_tree* t, int per) {
   Arena& a = t->arena;
   cudaStream_t s = t->stream;
   std::vector<int32_t> eptr(t->ntile + 1);
   GB_CK(cudaMemcpyAsync(eptr.data(), t->tile_eptr, sizeof(int32_t) * (t->ntile + 1), cudaMemcpyDeviceToHost, s));
   GB_CK(cudaStreamSynchronize(s));
-  std::vector<int4> ch;
   std::vector<int32_t> cptr(t->ntile + 1, 0);
+  int maxc = 0;
   for (int tile = 0; tile < t->ntile; ++tile) {
-    cptr[tile] = (int32_t)ch.size();
-    for (int e = eptr[tile]; e < eptr[tile + 1]; e += per)
-      ch.push_back(make_int4(tile, e, std::min(e + per, eptr[tile + 1]), 0));
+    const int nc = (eptr[tile + 1] - eptr[tile] + per - 1) / per;
+    cptr[tile + 1] = cptr[tile] + nc;
+    maxc = std::max(maxc, nc);
   }
-  cptr[t->ntile] = (int32_t)ch.size();
+  std::vector<int4> ch;
+  ch.reserve(cptr[t->ntile]);
+  for (int j = 0; j < maxc; ++j)
+    for (int tile = 0; tile < t->ntile; ++tile) {
+      const int e = eptr[tile] + j * per;
+      if (e < eptr[tile + 1]) ch.push_back(make_int4(tile, e, std::min(e + per, eptr[tile + 1]), cptr[tile] + j));
+    }
   t->nchunk = (int)ch.size();
   t->m2l_chunks = alloc_n<int4>(a, ch.size());
   t->tile_cptr = alloc_n<int32_t>(a, cptr.size());

@@ -1,0 +1,68 @@
+"""Host logic of bench.py's multi-rank mode (replicas only), on CPU with gloo.
+
+Every rank runs an independent replica, and the only cross-rank steps are a
+barrier and the max-reduction of the timed seconds.  These tests run two
+gloo ranks on the host and check that reduction and the whole-job
+throughput formula.
+"""
+
+import os
+import socket
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import bench  # noqa: E402
+
+
+def _free_port() -> int:
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank_main(rank, world, port, out_dir):
+    import torch.distributed as dist
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        # rank r "took" 1 + r seconds: the job time is the slowest rank's
+        mx = bench.reduce_max(1.0 + rank, "cpu")
+        v = bench.aggregate(1000, 5, world, mx)
+        dist.barrier()
+        with open(os.path.join(out_dir, f"r{rank}.txt"), "w") as f:
+            f.write(f"{mx} {v}\n")
+    finally:
+        dist.destroy_process_group()
+
+
+def test_reduce_max_and_aggregate_two_gloo_ranks(tmp_path):
+    import torch.multiprocessing as mp
+    world = 2
+    mp.start_processes(_rank_main, args=(world, _free_port(), str(tmp_path)), nprocs=world, join=True,
+                       start_method="spawn")
+    for r in range(world):
+        mx, v = map(float, (tmp_path / f"r{r}.txt").read_text().split())
+        assert mx == 2.0  # every rank sees the maximum
+        assert v == pytest.approx(1000 * 5 * world / 2.0)
+
+
+def test_single_process_reduce_is_identity():
+    assert bench.reduce_max(3.25, "cpu") == 3.25
+    assert bench.aggregate(10, 2, 1, 4.0) == 5.0
+
+
+def test_reference_arm_other_ranks_exit_without_work(monkeypatch, capsys):
+    # ranks other than 0 print nothing and touch neither the oracle nor a GPU
+    monkeypatch.setenv("RANK", "1")
+    monkeypatch.setenv("WORLD_SIZE", "2")
+
+    class A:
+        workload, steps, warmup = "cube4k_p4", 1, 0
+
+    bench.run_reference(A())
+    assert capsys.readouterr().out == ""
