@@ -61,8 +61,11 @@ enum {
 enum {
   FMM_FLAG_CIRCUMSCRIBED = 1u << 0, /* MAC radius = half diagonal instead of half side */
   FMM_FLAG_TIMING = 1u << 1,        /* record per-phase CUDA-event times (fmm_get_stats) */
-  FMM_FLAG_M2L_CUDA_CORE = 1u << 2  /* single precision: M2L on CUDA cores instead of
+  FMM_FLAG_M2L_CUDA_CORE = 1u << 2, /* single precision: M2L on CUDA cores instead of
                                        the tensor-core (3xTF32) engine */
+  FMM_FLAG_SORTED_PLAN = 1u << 3    /* number the M2L classes and (tile, class) entries by
+                                       sorting the pairs, also where the dense key tables
+                                       would be used; the plan is identical either way */
 };
 
 /* Optional stream-ordered allocator; NULL selects cudaMallocAsync/cudaFreeAsync. */
@@ -75,7 +78,12 @@ typedef struct {
 /* Phases timed with FMM_FLAG_TIMING (index into fmm_stats.ms). */
 enum {
   FMM_PH_P2M = 0, FMM_PH_M2M, FMM_PH_M2L, FMM_PH_L2L, FMM_PH_P2P, FMM_PH_L2P,
-  FMM_PH_EVAL_TOTAL, FMM_PH_BUILD_TOTAL, FMM_PH_COUNT
+  FMM_PH_EVAL_TOTAL, FMM_PH_BUILD_TOTAL,
+  /* parts of fmm_build: cube, keys, sort and cells; dual traversal and
+     P2P ranges; M2L tiles, classes and entries; operators, work chunks and
+     expansion buffers */
+  FMM_PH_BUILD_TREE, FMM_PH_BUILD_LISTS, FMM_PH_BUILD_PLAN, FMM_PH_BUILD_OPS,
+  FMM_PH_COUNT
 };
 
 typedef struct {

@@ -45,10 +45,21 @@ void create_tree(fmm_tree* t, const R* xyzq) {
     for (auto& e : t->ev) GB_CK(cudaEventCreate(&e));
   Arena& a = t->arena;
   cudaStream_t s = t->stream;
-  if (t->flags & FMM_FLAG_TIMING) GB_CK(cudaEventRecord(t->ev[2 * FMM_PH_BUILD_TOTAL], s));
+  const bool timing = (t->flags & FMM_FLAG_TIMING) != 0;
+  auto mark = [&](int ph, int end) {
+    if (timing) GB_CK(cudaEventRecord(t->ev[2 * ph + end], s));
+  };
+  mark(FMM_PH_BUILD_TOTAL, 0);
+  mark(FMM_PH_BUILD_TREE, 0);
   build_tree(t, xyzq, f64);
+  mark(FMM_PH_BUILD_TREE, 1);
+  mark(FMM_PH_BUILD_LISTS, 0);
   build_lists(t);
+  mark(FMM_PH_BUILD_LISTS, 1);
+  mark(FMM_PH_BUILD_PLAN, 0);
   build_m2l_plan(t);
+  mark(FMM_PH_BUILD_PLAN, 1);
+  mark(FMM_PH_BUILD_OPS, 0);
   build_operators(t);
   const size_t rs = sizeof(R);
   t->M = a.alloc(rs * (size_t)t->ncell * t->Kp);
@@ -67,11 +78,12 @@ void create_tree(fmm_tree* t, const R* xyzq) {
   t->check_rec = alloc_n<unsigned long long>(a, 4);
   GB_CK(cudaMemsetAsync(t->check_rec, 0, 4 * sizeof(unsigned long long), s));
   t->lim = Lim{t->N, t->ncell, t->nleaf, t->Kp, t->ntile, t->nentry, t->nclass, t->n_p2p_ranges, t->check_rec};
-  if (t->flags & FMM_FLAG_TIMING) GB_CK(cudaEventRecord(t->ev[2 * FMM_PH_BUILD_TOTAL + 1], s));
+  mark(FMM_PH_BUILD_OPS, 1);
+  mark(FMM_PH_BUILD_TOTAL, 1);
   GB_CK(cudaStreamSynchronize(s));
-  if (t->flags & FMM_FLAG_TIMING)
-    cudaEventElapsedTime(&t->ms[FMM_PH_BUILD_TOTAL], t->ev[2 * FMM_PH_BUILD_TOTAL],
-                         t->ev[2 * FMM_PH_BUILD_TOTAL + 1]);
+  if (timing)
+    for (int ph : {FMM_PH_BUILD_TOTAL, FMM_PH_BUILD_TREE, FMM_PH_BUILD_LISTS, FMM_PH_BUILD_PLAN, FMM_PH_BUILD_OPS})
+      cudaEventElapsedTime(&t->ms[ph], t->ev[2 * ph], t->ev[2 * ph + 1]);
 }
 
 template <class R>
@@ -314,8 +326,7 @@ int fmm_get_stats(const fmm_tree* tc, fmm_stats* o) {
       return FMM_ERR_CUDA;
     }
 
-    for (int ph = 0; ph < FMM_PH_COUNT; ++ph) {
-      if (ph == FMM_PH_BUILD_TOTAL) continue;
+    for (int ph = 0; ph < FMM_PH_BUILD_TOTAL; ++ph) {  // evaluate phases; build times are set by fmm_build
       float ms = 0.0f;
       if (cudaEventElapsedTime(&ms, t->ev[2 * ph], t->ev[2 * ph + 1]) == cudaSuccess) t->ms[ph] = ms;
       else cudaGetLastError();

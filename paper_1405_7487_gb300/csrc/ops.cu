@@ -29,6 +29,9 @@ namespace gbfmm {
 namespace {
 
 constexpr int kThreads = 256;
+// Largest dense key table (log2 entries) of the M2L plan; beyond it the plan
+// sorts the pairs instead.
+constexpr int kDenseBits = 22;
 inline unsigned blocks(int64_t n) { return (unsigned)((n + kThreads - 1) / kThreads); }
 
 struct cd {
@@ -358,6 +361,85 @@ __global__ void k_tile_ptr(const uint64_t* __restrict__ etile, int64_t ne, int n
   ptr[t] = (int32_t)lo;
 }
 
+// Dense form of the class and entry numbering, used when the key space is
+// small: a table over all possible keys marks the keys present, and the
+// exclusive scan of the marks numbers them in ascending key order, which is
+// the numbering the sort-and-unique form produces.
+__device__ __forceinline__ uint64_t class_key(const CellView& c, int A, int B, int b, int64_t maxd) {
+  int64_t d[3];
+  int dl;
+  pair_offset(c, A, B, d, dl);
+  return ((uint64_t)(dl + kMaxLevel) << (3 * b)) | ((uint64_t)(d[0] + maxd) << (2 * b)) |
+         ((uint64_t)(d[1] + maxd) << b) | (uint64_t)(d[2] + maxd);
+}
+
+__global__ void k_class_mark(const int32_t* __restrict__ tgt, const int32_t* __restrict__ src, int64_t n,
+                             CellView c, int b, int64_t maxd, int64_t* __restrict__ mark) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const uint64_t k = class_key(c, src[i], tgt[i], b, maxd);
+  if (mark[k] == 0) mark[k] = 1;
+}
+
+// After the scan: class id of every pair.
+__global__ void k_class_lookup(const int32_t* __restrict__ tgt, const int32_t* __restrict__ src, int64_t n,
+                               CellView c, int b, int64_t maxd, const int64_t* __restrict__ excl,
+                               int32_t* __restrict__ class_of) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  class_of[i] = (int32_t)excl[class_key(c, src[i], tgt[i], b, maxd)];
+}
+
+// Descriptor (dl, dx, dy, dz) of every class, decoded from its key.
+__global__ void k_class_desc_dense(const int64_t* __restrict__ excl, int64_t nkey, int64_t total, int b,
+                                   int64_t maxd, int32_t* __restrict__ desc) {
+  const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (k >= nkey) return;
+  const int64_t next = k + 1 < nkey ? excl[k + 1] : total;
+  if (next == excl[k]) return;  // key absent
+  const int64_t cid = excl[k];
+  const uint64_t m = (1ull << b) - 1;
+  desc[4 * cid + 0] = (int32_t)((int64_t)((uint64_t)k >> (3 * b)) - kMaxLevel);
+  desc[4 * cid + 1] = (int32_t)((int64_t)(((uint64_t)k >> (2 * b)) & m) - maxd);
+  desc[4 * cid + 2] = (int32_t)((int64_t)(((uint64_t)k >> b) & m) - maxd);
+  desc[4 * cid + 3] = (int32_t)((int64_t)((uint64_t)k & m) - maxd);
+}
+
+__global__ void k_entry_mark(const int32_t* __restrict__ tgt, const int32_t* __restrict__ class_of,
+                             const int32_t* __restrict__ rank_of, int64_t n, int nclass,
+                             int64_t* __restrict__ mark) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int64_t e = (int64_t)(rank_of[tgt[i]] / kTile) * nclass + class_of[i];
+  if (mark[e] == 0) mark[e] = 1;
+}
+
+__global__ void k_entry_fill_dense(const int32_t* __restrict__ tgt, const int32_t* __restrict__ src,
+                                   const int32_t* __restrict__ class_of, const int32_t* __restrict__ rank_of,
+                                   int64_t n, int nclass, const int64_t* __restrict__ excl,
+                                   int32_t* __restrict__ entry_src) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int r = rank_of[tgt[i]];
+  const int64_t e = excl[(int64_t)(r / kTile) * nclass + class_of[i]];
+  entry_src[e * kTile + (r % kTile)] = src[i];
+}
+
+// Entry classes and tile pointers from the scanned (tile, class) table.
+__global__ void k_entry_table(const int64_t* __restrict__ excl, int ntile, int nclass, int64_t total,
+                              int32_t* __restrict__ entry_class, int32_t* __restrict__ tile_eptr) {
+  const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t nk = (int64_t)ntile * nclass;
+  if (k > nk) return;
+  if (k == nk) {
+    tile_eptr[ntile] = (int32_t)total;
+    return;
+  }
+  if (k % nclass == 0) tile_eptr[k / nclass] = (int32_t)excl[k];
+  const int64_t next = k + 1 < nk ? excl[k + 1] : total;
+  if (next != excl[k]) entry_class[excl[k]] = (int32_t)(k % nclass);
+}
+
 __global__ void k_m2l_geom(const int32_t* __restrict__ desc, int n, double* __restrict__ geom) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
@@ -413,8 +495,6 @@ void build_m2l_plan(fmm_tree* t) {
   a.release(d_cnt);
 
   // --- translation classes
-  uint64_t* ckey = alloc_n<uint64_t>(a, nm);
-  int32_t* cval = alloc_n<int32_t>(a, nm);
   unsigned long long* d_maxd = alloc_n<unsigned long long>(a, 1);
   GB_CK(cudaMemsetAsync(d_maxd, 0, sizeof(unsigned long long), s));
   k_class_maxd<<<blocks(nm), kThreads, 0, s>>>(t->m2l_tgt, t->m2l_src, nm, cv, d_maxd);
@@ -425,25 +505,73 @@ void build_m2l_plan(fmm_tree* t) {
   a.release(d_maxd);
   int b = 1;
   while ((1ull << b) <= 2 * maxd) ++b;
-  k_class_keys<<<blocks(nm), kThreads, 0, s>>>(t->m2l_tgt, t->m2l_src, nm, cv, b, (int64_t)maxd, ckey, cval);
-  GB_LAUNCH("k_class_keys");
-  radix_sort_pairs(a, ckey, cval, nm, b <= 19 ? 6 + 3 * b : 64, s);
-  int64_t* flag = alloc_n<int64_t>(a, nm);
-  k_unique_flags<<<blocks(nm), kThreads, 0, s>>>(ckey, nm, 0, flag);
-  GB_LAUNCH("k_unique_flags");
-  const int64_t ncls = scan_exclusive_i64_total(a, flag, nm, s);
-  if (ncls > 0x7fffffff) fail(FMM_ERR_ARG, "too many translation classes");
-  t->nclass = (int)ncls;
-  t->class_desc = alloc_n<int32_t>(a, 4 * ncls);
-  int32_t* class_of = alloc_n<int32_t>(a, nm);
-  k_class_assign<<<blocks(nm), kThreads, 0, s>>>(ckey, cval, flag, nm, t->m2l_tgt, t->m2l_src, cv,
-                                                 class_of, t->class_desc);
-  GB_LAUNCH("k_class_assign");
-  a.release(ckey);
-  a.release(cval);
-  a.release(flag);
+  // dense numbering while the key table stays small (2^22 keys), else sort
+  const int kbits = 6 + 3 * b;
+  const bool sorted_only = (t->flags & FMM_FLAG_SORTED_PLAN) != 0;
+  const bool dense_cls = !sorted_only && b <= 19 && kbits <= kDenseBits;
+  int32_t* class_of = nullptr;
+  if (dense_cls) {
+    const int64_t nkey = 1ll << kbits;
+    int64_t* mark = alloc_n<int64_t>(a, nkey);
+    GB_CK(cudaMemsetAsync(mark, 0, sizeof(int64_t) * nkey, s));
+    k_class_mark<<<blocks(nm), kThreads, 0, s>>>(t->m2l_tgt, t->m2l_src, nm, cv, b, (int64_t)maxd, mark);
+    GB_LAUNCH("k_class_mark");
+    const int64_t ncls = scan_exclusive_i64_total(a, mark, nkey, s);
+    t->nclass = (int)ncls;
+    t->class_desc = alloc_n<int32_t>(a, 4 * ncls);
+    class_of = alloc_n<int32_t>(a, nm);
+    k_class_lookup<<<blocks(nm), kThreads, 0, s>>>(t->m2l_tgt, t->m2l_src, nm, cv, b, (int64_t)maxd, mark,
+                                                   class_of);
+    GB_LAUNCH("k_class_lookup");
+    k_class_desc_dense<<<blocks(nkey), kThreads, 0, s>>>(mark, nkey, ncls, b, (int64_t)maxd, t->class_desc);
+    GB_LAUNCH("k_class_desc_dense");
+    a.release(mark);
+  } else {
+    uint64_t* ckey = alloc_n<uint64_t>(a, nm);
+    int32_t* cval = alloc_n<int32_t>(a, nm);
+    k_class_keys<<<blocks(nm), kThreads, 0, s>>>(t->m2l_tgt, t->m2l_src, nm, cv, b, (int64_t)maxd, ckey, cval);
+    GB_LAUNCH("k_class_keys");
+    radix_sort_pairs(a, ckey, cval, nm, b <= 19 ? 6 + 3 * b : 64, s);
+    int64_t* flag = alloc_n<int64_t>(a, nm);
+    k_unique_flags<<<blocks(nm), kThreads, 0, s>>>(ckey, nm, 0, flag);
+    GB_LAUNCH("k_unique_flags");
+    const int64_t ncls = scan_exclusive_i64_total(a, flag, nm, s);
+    if (ncls > 0x7fffffff) fail(FMM_ERR_ARG, "too many translation classes");
+    t->nclass = (int)ncls;
+    t->class_desc = alloc_n<int32_t>(a, 4 * ncls);
+    class_of = alloc_n<int32_t>(a, nm);
+    k_class_assign<<<blocks(nm), kThreads, 0, s>>>(ckey, cval, flag, nm, t->m2l_tgt, t->m2l_src, cv,
+                                                   class_of, t->class_desc);
+    GB_LAUNCH("k_class_assign");
+    a.release(ckey);
+    a.release(cval);
+    a.release(flag);
+  }
 
   // --- entries: (tile, class) with the source of every tile row
+  if (!sorted_only && (int64_t)t->ntile * t->nclass <= (1ll << kDenseBits)) {
+    const int64_t nk = (int64_t)t->ntile * t->nclass;
+    int64_t* mark = alloc_n<int64_t>(a, nk);
+    GB_CK(cudaMemsetAsync(mark, 0, sizeof(int64_t) * nk, s));
+    k_entry_mark<<<blocks(nm), kThreads, 0, s>>>(t->m2l_tgt, class_of, rank_of, nm, t->nclass, mark);
+    GB_LAUNCH("k_entry_mark");
+    const int64_t ne = scan_exclusive_i64_total(a, mark, nk, s);
+    t->nentry = ne;
+    t->entry_class = alloc_n<int32_t>(a, ne);
+    t->entry_src = alloc_n<int32_t>(a, ne * kTile);
+    GB_CK(cudaMemsetAsync(t->entry_src, 0xff, sizeof(int32_t) * ne * kTile, s));
+    k_entry_fill_dense<<<blocks(nm), kThreads, 0, s>>>(t->m2l_tgt, t->m2l_src, class_of, rank_of, nm, t->nclass,
+                                                       mark, t->entry_src);
+    GB_LAUNCH("k_entry_fill_dense");
+    t->tile_eptr = alloc_n<int32_t>(a, t->ntile + 1);
+    k_entry_table<<<blocks(nk + 1), kThreads, 0, s>>>(mark, t->ntile, t->nclass, ne, t->entry_class,
+                                                      t->tile_eptr);
+    GB_LAUNCH("k_entry_table");
+    a.release(mark);
+    a.release(class_of);
+    a.release(rank_of);
+    return;
+  }
   uint64_t* ekey = alloc_n<uint64_t>(a, nm);
   int32_t* eval = alloc_n<int32_t>(a, nm);
   int cb = 1, tb = 1;

@@ -23,8 +23,10 @@ _lib = None
 FMM_FLAG_CIRCUMSCRIBED = 1
 FMM_FLAG_TIMING = 2
 FMM_FLAG_M2L_CUDA_CORE = 4
+FMM_FLAG_SORTED_PLAN = 8
 
-PHASES = ("p2m", "m2m", "m2l", "l2l", "p2p", "l2p", "eval_total", "build_total")
+PHASES = ("p2m", "m2m", "m2l", "l2l", "p2p", "l2p", "eval_total", "build_total",
+          "build_tree", "build_lists", "build_plan", "build_ops")
 
 _ERRORS = {0: "ok", -1: "FMM_ERR_ARG", -2: "FMM_ERR_NONFINITE", -3: "FMM_ERR_OOM", -4: "FMM_ERR_CUDA",
            -5: "FMM_ERR_TIMEOUT", -6: "FMM_ERR_STATE", -7: "FMM_ERR_RANGE"}
@@ -48,7 +50,7 @@ class Stats(ctypes.Structure):
                 ("flags", ctypes.c_uint32), ("m2l_engine", ctypes.c_int32),
                 ("workspace_bytes", ctypes.c_int64), ("evaluations", ctypes.c_int32),
                 ("device_errors", ctypes.c_int32),
-                ("ms", ctypes.c_float * 8)]
+                ("ms", ctypes.c_float * len(PHASES))]
 
 
 _V = ctypes.c_void_p

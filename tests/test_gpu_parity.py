@@ -350,6 +350,24 @@ def test_plan_in_bounds_and_covers_lists(fmm, name, f64):
         assert np.array_equal(cover, ref)
 
 
+@pytest.mark.parametrize("name", ["cube65k_p10", "plummer60k_p8", "sphere40k_p6", "cube3k_p1"])
+def test_dense_and_sorted_plans_identical(fmm, name):
+    """The M2L plan numbered through dense key tables equals the plan numbered
+    by sorting the pairs, array for array, and so do the outputs."""
+    gen, p, theta, ncrit = CASES[name]
+    x = gen()
+    A = gpu_tree(fmm, x, p, theta, ncrit)
+    B = gpu_tree(fmm, x, p, theta, ncrit, fmm.FMM_FLAG_SORTED_PLAN)
+    assert A.stats()["n_m2l_classes"] == B.stats()["n_m2l_classes"]
+    PA, PB = A.plan(), B.plan()
+    assert PA.keys() == PB.keys()
+    for k in PA:
+        assert np.array_equal(PA[k], PB[k]), k
+    pa, fa = evaluate(A)
+    pb, fb = evaluate(B)
+    assert np.array_equal(pa, pb) and np.array_equal(fa, fb)
+
+
 @pytest.mark.parametrize("name", ["cube4k_p4", "cube65k_p10", "cube20k_p16", "cube3k_p1", "sphere40k_p6"])
 def test_m2l_engines_agree(fmm, name):
     """The tensor-core M2L (3xTF32, tcgen05) and the CUDA-core M2L give the same
