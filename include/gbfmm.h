@@ -60,15 +60,22 @@ enum {
 /* fmm_build flags */
 enum {
   FMM_FLAG_CIRCUMSCRIBED = 1u << 0, /* MAC radius = half diagonal instead of half side */
-  FMM_FLAG_TIMING = 1u << 1,        /* record per-phase CUDA-event times (fmm_get_stats) */
+  FMM_FLAG_TIMING = 1u << 1,        /* record per-phase CUDA-event times (fmm_get_stats); the
+                                       near field's events are on the stream it runs on */
   FMM_FLAG_M2L_CUDA_CORE = 1u << 2, /* single precision: M2L on CUDA cores instead of
                                        the tensor-core (3xTF32) engine */
-  FMM_FLAG_SORTED_PLAN = 1u << 3    /* number the M2L classes and (tile, class) entries by
+  FMM_FLAG_SORTED_PLAN = 1u << 3,   /* number the M2L classes and (tile, class) entries by
                                        sorting the pairs, also where the dense key tables
                                        would be used; the plan is identical either way */
+  FMM_FLAG_SERIAL_PHASES = 1u << 4  /* run the near field on the caller's stream after the
+                                       far field instead of concurrently on a second stream
+                                       (with FMM_FLAG_TIMING: each phase timed alone) */
 };
 
-/* Optional stream-ordered allocator; NULL selects cudaMallocAsync/cudaFreeAsync. */
+/* Optional stream-ordered allocator.  NULL selects the library's memory pool
+   on the current device (cudaMallocFromPoolAsync / cudaFreeAsync): it keeps up
+   to 16 GiB of freed memory mapped for reuse by later calls instead of
+   returning it to the driver at every synchronisation. */
 typedef struct {
   void* (*alloc)(size_t bytes, fmm_stream stream, void* ctx);
   void (*free)(void* ptr, fmm_stream stream, void* ctx);

@@ -38,7 +38,11 @@ void create_tree(fmm_tree* t, const R* xyzq) {
   t->K = t->p * t->p;
   t->Kp = (t->K + 15) / 16 * 16;
   t->m2l_engine = (!f64 && !(t->flags & FMM_FLAG_M2L_CUDA_CORE)) ? 1 : 0;
-  GB_CK(cudaStreamCreateWithFlags(&t->side, cudaStreamNonBlocking));
+  {
+    int lo = 0, hi = 0;  // numerically greatest = lowest priority
+    GB_CK(cudaDeviceGetStreamPriorityRange(&lo, &hi));
+    GB_CK(cudaStreamCreateWithPriority(&t->side, cudaStreamNonBlocking, lo));
+  }
   GB_CK(cudaEventCreateWithFlags(&t->fork, cudaEventDisableTiming));
   GB_CK(cudaEventCreateWithFlags(&t->join, cudaEventDisableTiming));
   if (t->flags & FMM_FLAG_TIMING)
@@ -136,13 +140,14 @@ struct PhaseTimer {
 template <class R>
 void run_pass(fmm_tree* t, cudaStream_t s, int mode, R* a, R* b) {
   const bool timing = (t->flags & FMM_FLAG_TIMING) != 0;
+  const bool serial = (t->flags & FMM_FLAG_SERIAL_PHASES) != 0;
   PhaseTimer T{t, s, timing};
   T.begin(FMM_PH_EVAL_TOTAL);
-  // Near field on the side stream, concurrently with the far field.  With
-  // per-phase timing everything runs on the caller's stream, one kernel at a
-  // time, so that each phase's events time that phase alone.
-  cudaStream_t ps = timing ? s : t->side;
-  if (!timing) {
+  // Near field on the side stream (lower priority), concurrently with the far
+  // field: P2P blocks fill the SMs the tensor-core M2L leaves free.  Serial
+  // mode runs it on the caller's stream first, one phase at a time.
+  cudaStream_t ps = serial ? s : t->side;
+  if (!serial) {
     GB_CK(cudaEventRecord(t->fork, s));
     GB_CK(cudaStreamWaitEvent(t->side, t->fork, 0));
   }
@@ -150,7 +155,7 @@ void run_pass(fmm_tree* t, cudaStream_t s, int mode, R* a, R* b) {
   Tp.begin(FMM_PH_P2P);
   launch_p2p<R>(t, ps);
   Tp.end(FMM_PH_P2P);
-  if (!timing) GB_CK(cudaEventRecord(t->join, t->side));
+  if (!serial) GB_CK(cudaEventRecord(t->join, t->side));
   // far field
   GB_CK(cudaMemsetAsync(t->L, 0, sizeof(R) * (size_t)t->ncell * t->Kp, s));
   T.begin(FMM_PH_P2M);
@@ -170,7 +175,7 @@ void run_pass(fmm_tree* t, cudaStream_t s, int mode, R* a, R* b) {
   T.begin(FMM_PH_L2L);
   for (int l = 1; l < t->nlevel; ++l) launch_l2l<R>(t, l, s);
   T.end(FMM_PH_L2L);
-  if (!timing) GB_CK(cudaStreamWaitEvent(s, t->join, 0));
+  if (!serial) GB_CK(cudaStreamWaitEvent(s, t->join, 0));
   T.begin(FMM_PH_L2P);
   launch_l2p_finalize<R>(t, mode, a, b, s);
   T.end(FMM_PH_L2P);
@@ -247,9 +252,15 @@ int fmm_solve_host(const float* xyzq_h, const float* w_h, int64_t n, int p, doub
   float *d_x = nullptr, *d_w = nullptr, *d_pot = nullptr, *d_force = nullptr, *d_dq = nullptr, *d_dx = nullptr;
   fmm_tree* t = nullptr;
   int rc = FMM_OK;
+  cudaMemPool_t pool = nullptr;
+  try {
+    pool = library_pool();
+  } catch (const Error& e) {
+    return to_code(e);
+  }
   auto mal = [&](float** p, size_t count) {
     if (rc != FMM_OK) return;
-    if (cudaMallocAsync((void**)p, sizeof(float) * count, s) != cudaSuccess) {
+    if (cudaMallocFromPoolAsync((void**)p, sizeof(float) * count, pool, s) != cudaSuccess) {
       cudaGetLastError();
       rc = FMM_ERR_OOM;
     }

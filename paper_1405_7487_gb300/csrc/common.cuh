@@ -29,8 +29,9 @@ void count_launch();
 // after every kernel launch: count it and surface a launch error
 #define GB_LAUNCH(what) (::gbfmm::count_launch(), ::gbfmm::check_cuda(cudaGetLastError(), what))
 
-// Stream-ordered device memory through the caller's allocator or
-// cudaMallocAsync.  Every allocation of a tree is recorded for release.
+// Stream-ordered device memory through the caller's allocator or the
+// library's memory pool.  Every allocation of a tree is recorded for release.
+cudaMemPool_t library_pool();
 struct Arena {
   fmm_allocator user{};
   bool has_user = false;

@@ -21,13 +21,15 @@
 //   warps 0-3  producers: cp.async 16-byte copies of the 128 source rows
 //              (hi and lo) and of the Kp operator rows (hi and lo) of one
 //              32-element k-block into a stage, in the 128-byte-swizzled
-//              K-major layout the MMA descriptors describe.  A stage is
-//              published (async-proxy fence, then an arrive on its "full"
-//              barrier) once its copies have landed, which each producer
-//              checks after issuing the next stage's copies.  Then the
-//              epilogue (TMEM -> the chunk's partial).
-//   warp 4     TMEM allocation; one elected lane issues the MMAs of a stage
-//              and commits them to the stage's "empty" barrier.
+//              K-major layout the MMA descriptors describe.  Each thread
+//              publishes its part of a stage with cp.async.mbarrier.arrive
+//              (the arrival on the stage's "full" barrier fires when its
+//              copies land), so up to nstage stages are in flight.  Then
+//              the epilogue (TMEM -> the chunk's partial).
+//   warp 4     TMEM allocation; one elected lane waits for a full stage,
+//              fences the generic-proxy writes against the tensor core's
+//              async-proxy reads, issues the stage's MMAs and commits them
+//              to the stage's "empty" barrier.
 // Every wait is bounded; a wait that gives up sets the error flag, the
 // roles drain and the TMEM is released.
 #include <algorithm>
@@ -60,21 +62,9 @@ __device__ __forceinline__ uint32_t swz(int r, int c) {
 __device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, int bytes) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(dst), "l"(src), "r"(bytes) : "memory");
 }
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 template <int N>
 __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
-}
-// cp.async.wait_group needs an immediate: dispatch the pipeline depths used
-__device__ __forceinline__ void cp_async_wait_dyn(int n) {
-  switch (n) {
-    case 0: cp_async_wait<0>(); break;
-    case 1: cp_async_wait<1>(); break;
-    case 2: cp_async_wait<2>(); break;
-    case 3: cp_async_wait<3>(); break;
-    case 4: cp_async_wait<4>(); break;
-    default: cp_async_wait<5>(); break;
-  }
 }
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
 
@@ -179,15 +169,16 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
   if (warp < 4) {
     // ---------------------------------------------------------- producers
     const int r = tid;
-    // A copies: thread r moves 16-byte chunk (r % 8) of tile rows
-    // r / 8 + 16 i (i = 0..7), so eight neighbouring threads read one
-    // 128-byte row segment and write one swizzled 128-byte line
-    const int cA = r & 7, rA = r >> 3;
+    // Thread r moves 16-byte chunk (r % 8) of rows r / 8 + 16 i of both
+    // operands, so eight neighbouring threads read one 128-byte row segment
+    // and write one swizzled 128-byte line.  A stage is published by
+    // cp.async.mbarrier.arrive: each thread's arrival on the stage's "full"
+    // barrier fires when its copies have landed, so the producers run ahead
+    // by up to nstage stages without waiting for their own copies.
+    const int c8 = r & 7, r8 = r >> 3;
+    const int nbrow = (Kp + 15) / 16;  // operator rows per thread
     int src[8];
     int cur_e = -1, cls = 0;
-    // the copies of iteration it are in flight while iteration it - 1 is
-    // published (measured faster than deeper lags on GB300)
-    const int lag = 1;
     for (int it = 0; it < nit; ++it) {
       const int e = e0 + it / nkb, kb = it % nkb;
       const int s = it % nstage, round = it / nstage;
@@ -195,42 +186,38 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
       if (e != cur_e) {
         cur_e = e;
 #pragma unroll
-        for (int i = 0; i < 8; ++i) src[i] = __ldg(entry_src + (int64_t)e * kTile + rA + 16 * i);
+        for (int i = 0; i < 8; ++i) src[i] = __ldg(entry_src + (int64_t)e * kTile + r8 + 16 * i);
         cls = __ldg(entry_class + e);
       }
       const uint32_t sb = base + s * stage_bytes;
       const int k0 = kb * kKB;
       const int nch = min(kKB, Kp - k0) / 4;  // 16-byte chunks in this k-block
-      // A rows: the source multipole of each tile row (zeros for an empty row)
-      if (cA < nch) {
+      if (c8 < nch) {
+        // A rows: the source multipole of each tile row (zeros for an empty row)
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
-          const int row = rA + 16 * i;
-          const int64_t off = (int64_t)(src[i] >= 0 ? src[i] : 0) * Kp + k0 + 4 * cA;
+          const int row = r8 + 16 * i;
+          const int64_t off = (int64_t)(src[i] >= 0 ? src[i] : 0) * Kp + k0 + 4 * c8;
           const int bytes = src[i] >= 0 ? 16 : 0;
-          cp_async16(sb + swz(row, cA), Mhi + off, bytes);
-          cp_async16(sb + kStageA + swz(row, cA), Mlo + off, bytes);
+          cp_async16(sb + swz(row, c8), Mhi + off, bytes);
+          cp_async16(sb + kStageA + swz(row, c8), Mlo + off, bytes);
+        }
+        // B rows: output coefficient rows of the operator
+        const float* oh = ops_hi + (int64_t)cls * Kp * Kp + k0 + 4 * c8;
+        const float* ol = ops_lo + (int64_t)cls * Kp * Kp + k0 + 4 * c8;
+        for (int i = 0; i < nbrow; ++i) {
+          const int row = r8 + 16 * i;
+          if (row < Kp) {
+            cp_async16(sb + 2 * kStageA + swz(row, c8), oh + (int64_t)row * Kp, 16);
+            cp_async16(sb + 2 * kStageA + stageB + swz(row, c8), ol + (int64_t)row * Kp, 16);
+          }
         }
       }
-      // B rows: output coefficient rows of the operator
-      const float* oh = ops_hi + (int64_t)cls * Kp * Kp + k0;
-      const float* ol = ops_lo + (int64_t)cls * Kp * Kp + k0;
-      for (int w = r; w < Kp * nch; w += kProducers) {
-        const int row = w / nch, c = w % nch;
-        cp_async16(sb + 2 * kStageA + swz(row, c), oh + (int64_t)row * Kp + 4 * c, 16);
-        cp_async16(sb + 2 * kStageA + stageB + swz(row, c), ol + (int64_t)row * Kp + 4 * c, 16);
-      }
-      cp_async_commit();
-      if (it >= lag) {
-        // all but the newest `lag` groups have landed
-        cp_async_wait_dyn(lag);
-        fence_async_smem();
-        mbar_arrive(smem_u32(&bar_full[(it - lag) % nstage]));
-      }
+      asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];\n" ::"r"(smem_u32(&bar_full[s]))
+                   : "memory");
     }
+    // no copy may still be in flight when the CTA ends
     cp_async_wait<0>();
-    fence_async_smem();
-    for (int it = max(0, nit - lag); it < nit; ++it) mbar_arrive(smem_u32(&bar_full[it % nstage]));
     // ------------------------------------------------------------ epilogue
     const bool ok = nit > 0 && mbar_wait(smem_u32(&bar_done), 0, &abort_flag);
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
@@ -268,6 +255,9 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
         ok = false;
         break;
       }
+      // the stage was written through the generic proxy (cp.async); make it
+      // visible to the tensor core's async-proxy reads
+      fence_async_smem();
       asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
       const uint32_t sb = base + s * stage_bytes;
       const int nks = min(kKB, Kp - kb * kKB) / 8;  // tf32 k-steps of 8 elements

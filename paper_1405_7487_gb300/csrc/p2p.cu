@@ -207,11 +207,272 @@ __global__ void __launch_bounds__(kThreads) k_p2p(const R4* __restrict__ bodies,
   }
 }
 
+// ---------------------------------------------------------------------------
+// Single precision with packed FP32 pairs (add/sub/mul/fma.rn.f32x2, sm_100
+// and later): one instruction evaluates one target against two sources.  The
+// staged tile holds the sources two by two, {x0,x1,y0,y1} {z0,z1,q0,q1}, so a
+// pair of sources is two 16-byte shared loads.  Each thread owns two targets
+// as in the generic kernel; its sums are kept per source parity (the low and
+// high halves) and added at the end.  A padding source (odd tile length) sits
+// at 1e30 with zero charge: r^2 overflows to +inf, rsqrt gives 0, and it adds
+// exactly zero.
+
+typedef unsigned long long f2;  // two packed floats (low half first in memory)
+
+__device__ __forceinline__ f2 f2_pack(float lo, float hi) {
+  f2 r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+  return r;
+}
+__device__ __forceinline__ void f2_unpack(f2 v, float& lo, float& hi) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ f2 f2_add(f2 a, f2 b) {
+  f2 r;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ f2 f2_sub(f2 a, f2 b) {
+  f2 r;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ f2 f2_mul(f2 a, f2 b) {
+  f2 r;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ f2 f2_fma(f2 a, f2 b, f2 c) {
+  f2 r;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+  return r;
+}
+
+struct Acc2 {
+  f2 p, x, y, z;
+};
+
+// One target (X, Y, Z duplicated in both halves) against the source pair.
+template <bool MASK>
+__device__ __forceinline__ void pair2(f2 XX, f2 YY, f2 ZZ, f2 QQ, f2 X, f2 Y, f2 Z, Acc2& a) {
+  const f2 dx = f2_sub(XX, X), dy = f2_sub(YY, Y), dz = f2_sub(ZZ, Z);
+  f2 r2 = f2_mul(dx, dx);
+  r2 = f2_fma(dy, dy, r2);
+  r2 = f2_fma(dz, dz, r2);
+  float rl, rh;
+  f2_unpack(r2, rl, rh);
+  float il = rsqrt_fast(rl), ih = rsqrt_fast(rh);
+  if (MASK) {
+    il = rl > 0.f ? il : 0.f;
+    ih = rh > 0.f ? ih : 0.f;
+  }
+  const f2 inv = f2_pack(il, ih);
+  const f2 qi = f2_mul(QQ, inv);
+  a.p = f2_add(a.p, qi);
+  const f2 f = f2_mul(f2_mul(qi, inv), inv);
+  a.x = f2_fma(f, dx, a.x);
+  a.y = f2_fma(f, dy, a.y);
+  a.z = f2_fma(f, dz, a.z);
+}
+
+constexpr int kPairTile = kSrcTile / 2;
+constexpr int kSlots = kSrcTile / kThreads;  // bodies staged per thread per tile
+constexpr float kFar = 1e30f;
+
+struct __align__(16) SrcPair {
+  float w[8];  // x0 x1 y0 y1 z0 z1 q0 q1
+};
+
+__device__ __forceinline__ void put_body(SrcPair* tile, int slot, float4 b) {
+  float* w = tile[slot >> 1].w + (slot & 1);
+  w[0] = b.x;
+  w[2] = b.y;
+  w[4] = b.z;
+  w[6] = b.w;
+}
+
+// Global indices of this thread's slots of the next tile of the neighbour
+// stream (-1: none); returns the tile length (uniform over the block).
+__device__ __forceinline__ int plan_tile(const int2* __restrict__ ranges, Cursor& cur, int r1, int (&gidx)[kSlots],
+                                         const Lim& lim) {
+  int filled = 0;
+#pragma unroll
+  for (int m = 0; m < kSlots; ++m) gidx[m] = -1;
+  while (filled < kSrcTile && cur.r < r1) {
+    const int2 rg = GB_LD(ranges, cur.r, lim.nranges, 107);
+    const int b = rg.x + cur.off;
+    const int take = min(rg.y - b, kSrcTile - filled);
+#pragma unroll
+    for (int m = 0; m < kSlots; ++m) {
+      const int sl = threadIdx.x + m * kThreads - filled;
+      if (sl >= 0 && sl < take) gidx[m] = b + sl;
+    }
+    filled += take;
+    if (b + take == rg.y) {
+      ++cur.r;
+      cur.off = 0;
+    } else {
+      cur.off += take;
+    }
+  }
+  return filled;
+}
+
+__device__ __forceinline__ void load_slots(const float4* __restrict__ bodies, const int (&gidx)[kSlots],
+                                           float4 (&v)[kSlots], const Lim& lim) {
+#pragma unroll
+  for (int m = 0; m < kSlots; ++m)
+    v[m] = gidx[m] >= 0 ? GB_LD(bodies, gidx[m], lim.N, 108) : make_float4(kFar, kFar, kFar, 0.f);
+}
+
+__device__ __forceinline__ void store_slots(SrcPair* tile, int cnt, const float4 (&v)[kSlots]) {
+  const int lim2 = (cnt + 1) & ~1;  // slots up to the even length (the pad)
+#pragma unroll
+  for (int m = 0; m < kSlots; ++m) {
+    const int sl = threadIdx.x + m * kThreads;
+    if (sl < lim2) put_body(tile, sl, v[m]);
+  }
+}
+
+template <bool MASK>
+__device__ __forceinline__ void tile_sum2(const SrcPair* __restrict__ tile, int k0, int k1, f2 X0, f2 Y0, f2 Z0,
+                                          f2 X1, f2 Y1, f2 Z1, Acc2& a0, Acc2& a1) {
+#pragma unroll 2
+  for (int k = k0; k < k1; ++k) {
+    const ulonglong2 A = *reinterpret_cast<const ulonglong2*>(tile[k].w);
+    const ulonglong2 B = *reinterpret_cast<const ulonglong2*>(tile[k].w + 4);
+    pair2<MASK>(A.x, A.y, B.x, B.y, X0, Y0, Z0, a0);
+    pair2<MASK>(A.x, A.y, B.x, B.y, X1, Y1, Z1, a1);
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) k_p2p_f2(const float4* __restrict__ bodies,
+                                                     const int32_t* __restrict__ leaves,
+                                                     const int32_t* __restrict__ bbeg, const int32_t* __restrict__ bend,
+                                                     const int32_t* __restrict__ rptr, const int2* __restrict__ ranges,
+                                                     float4* __restrict__ near, Lim lim) {
+  __shared__ SrcPair tiles[2][kPairTile];
+  __shared__ Acc<float> red[2][kThreads];
+  const int li = blockIdx.x;
+  const int cell = GB_LD(leaves, li, lim.nleaf, 101);
+  const int s = GB_LD(bbeg, cell, lim.ncell, 102), e = GB_LD(bend, cell, lim.ncell, 103);
+  const int r0 = GB_LD(rptr, li, lim.nleaf + 1, 104), r1 = GB_LD(rptr, li + 1, lim.nleaf + 1, 105);
+  const int tid = threadIdx.x;
+  const f2 zero = 0ull;
+  for (int t0 = s; t0 < e; t0 += kTgtChunk) {
+    const int nt = min(kTgtChunk, e - t0);
+    const int T2 = (nt + 1) >> 1;
+    const int G = kThreads / T2;
+    const int i = tid % T2, g = tid / T2;
+    const bool active = g < G;
+    const bool has_b = i + T2 < nt;
+    f2 X0 = zero, Y0 = zero, Z0 = zero, X1 = zero, Y1 = zero, Z1 = zero;
+    if (active) {
+      const float4 a = GB_LD(bodies, t0 + i, lim.N, 106);
+      const float4 b = has_b ? GB_LD(bodies, t0 + i + T2, lim.N, 106) : a;
+      X0 = f2_pack(a.x, a.x);
+      Y0 = f2_pack(a.y, a.y);
+      Z0 = f2_pack(a.z, a.z);
+      X1 = f2_pack(b.x, b.x);
+      Y1 = f2_pack(b.y, b.y);
+      Z1 = f2_pack(b.z, b.z);
+    }
+    // tile sums: the two parities folded, then compensated (Kahan) addition
+    auto fold = [](const Acc2& a) {
+      Acc<float> r;
+      float l, h;
+      f2_unpack(a.p, l, h);
+      r.p = l + h;
+      f2_unpack(a.x, l, h);
+      r.x = l + h;
+      f2_unpack(a.y, l, h);
+      r.y = l + h;
+      f2_unpack(a.z, l, h);
+      r.z = l + h;
+      return r;
+    };
+    Acc<float> s0{0, 0, 0, 0}, c0{0, 0, 0, 0}, s1{0, 0, 0, 0}, c1{0, 0, 0, 0};
+    auto accumulate = [&](const Acc2& p, Acc<float>& sm, Acc<float>& cm) { kahan_add(sm, cm, fold(p)); };
+    // own leaf, masked
+    for (int c0b = s; c0b < e; c0b += kSrcTile) {
+      const int cnt = min(kSrcTile, e - c0b);
+      int gidx[kSlots];
+#pragma unroll
+      for (int m = 0; m < kSlots; ++m) {
+        const int sl = tid + m * kThreads;
+        gidx[m] = sl < cnt ? c0b + sl : -1;
+      }
+      float4 v[kSlots];
+      load_slots(bodies, gidx, v, lim);
+      __syncthreads();
+      store_slots(tiles[0], cnt, v);
+      __syncthreads();
+      if (active) {
+        const int np = (cnt + 1) >> 1;
+        const int k0 = (g * np) / G, k1 = ((g + 1) * np) / G;
+        Acc2 p0{zero, zero, zero, zero}, p1{zero, zero, zero, zero};
+        tile_sum2<true>(tiles[0], k0, k1, X0, Y0, Z0, X1, Y1, Z1, p0, p1);
+        accumulate(p0, s0, c0);
+        accumulate(p1, s1, c1);
+      }
+    }
+    // neighbour stream: the next tile is loaded into registers while the
+    // current one is summed
+    Cursor cur{r0, 0};
+    int gidx[kSlots];
+    float4 v[kSlots];
+    int cnt = plan_tile(ranges, cur, r1, gidx, lim);
+    load_slots(bodies, gidx, v, lim);
+    __syncthreads();
+    store_slots(tiles[0], cnt, v);
+    __syncthreads();
+    int buf = 0;
+    while (cnt > 0) {
+      const int nxt = plan_tile(ranges, cur, r1, gidx, lim);
+      if (nxt > 0) load_slots(bodies, gidx, v, lim);
+      if (active) {
+        const int np = (cnt + 1) >> 1;
+        const int k0 = (g * np) / G, k1 = ((g + 1) * np) / G;
+        Acc2 p0{zero, zero, zero, zero}, p1{zero, zero, zero, zero};
+        tile_sum2<false>(tiles[buf], k0, k1, X0, Y0, Z0, X1, Y1, Z1, p0, p1);
+        accumulate(p0, s0, c0);
+        accumulate(p1, s1, c1);
+      }
+      // tiles[buf ^ 1] was last read two iterations ago (before the barrier
+      // that ended the previous iteration)
+      if (nxt > 0) store_slots(tiles[buf ^ 1], nxt, v);
+      __syncthreads();
+      buf ^= 1;
+      cnt = nxt;
+    }
+    red[0][tid] = s0;
+    red[1][tid] = s1;
+    __syncthreads();
+    if (active && g == 0) {
+      Acc<float> ta = red[0][i], tb = red[1][i];
+      for (int gg = 1; gg < G; ++gg) {
+        const Acc<float> va = red[0][gg * T2 + i], vb = red[1][gg * T2 + i];
+        ta.p += va.p; ta.x += va.x; ta.y += va.y; ta.z += va.z;
+        tb.p += vb.p; tb.x += vb.x; tb.y += vb.y; tb.z += vb.z;
+      }
+      GB_ST(near, t0 + i, lim.N, 109, make_float4(ta.p, ta.x, ta.y, ta.z));
+      if (has_b) GB_ST(near, t0 + i + T2, lim.N, 109, make_float4(tb.p, tb.x, tb.y, tb.z));
+    }
+    __syncthreads();
+  }
+}
+
 }  // namespace
 
 template <class R>
 void launch_p2p(fmm_tree* t, cudaStream_t s) {
   using R4 = typename Vec4<R>::type;
+  if (std::is_same<R, float>::value) {
+    k_p2p_f2<<<t->nleaf, kThreads, 0, s>>>((const float4*)t->work, t->leaves, t->c.bbeg, t->c.bend, t->p2p_rptr,
+                                           t->p2p_ranges, (float4*)t->near, t->lim);
+    GB_LAUNCH("k_p2p_f2");
+    return;
+  }
   k_p2p<R, R4><<<t->nleaf, kThreads, 0, s>>>((const R4*)t->work, t->leaves, t->c.bbeg, t->c.bend, t->p2p_rptr,
                                              t->p2p_ranges, (R4*)t->near, t->lim);
   GB_LAUNCH("k_p2p");

@@ -2,6 +2,8 @@
 #include <cstdio>
 #include <cstring>
 #include <atomic>
+#include <map>
+#include <mutex>
 
 #include "common.cuh"
 
@@ -25,16 +27,45 @@ void check_cuda(cudaError_t e, const char* what) {
   fail(e == cudaErrorMemoryAllocation ? FMM_ERR_OOM : FMM_ERR_CUDA, msg.c_str());
 }
 
+// The library's stream-ordered memory pool on the current device.  Unlike
+// the device's default pool (release threshold 0), it keeps up to
+// kPoolKeepBytes of freed memory mapped for reuse across synchronisations,
+// so the many short-lived buffers of fmm_build and repeated builds do not
+// map and unmap physical memory every time.
+constexpr uint64_t kPoolKeepBytes = 16ull << 30;
+
+cudaMemPool_t library_pool() {
+  static std::mutex mu;
+  static std::map<int, cudaMemPool_t> pools;
+  int dev = 0;
+  GB_CK(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lock(mu);
+  auto it = pools.find(dev);
+  if (it != pools.end()) return it->second;
+  cudaMemPoolProps props;
+  memset(&props, 0, sizeof(props));
+  props.allocType = cudaMemAllocationTypePinned;
+  props.handleTypes = cudaMemHandleTypeNone;
+  props.location.type = cudaMemLocationTypeDevice;
+  props.location.id = dev;
+  cudaMemPool_t pool = nullptr;
+  GB_CK(cudaMemPoolCreate(&pool, &props));
+  uint64_t keep = kPoolKeepBytes;
+  GB_CK(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep));
+  pools[dev] = pool;
+  return pool;
+}
+
 void* Arena::alloc(size_t n) {
   void* p = nullptr;
   if (has_user) {
     p = user.alloc(n, (fmm_stream)stream, user.ctx);
     if (!p) fail(FMM_ERR_OOM, "user allocator");
   } else {
-    cudaError_t e = cudaMallocAsync(&p, n, stream);
+    cudaError_t e = cudaMallocFromPoolAsync(&p, n, library_pool(), stream);
     if (e != cudaSuccess) {
       cudaGetLastError();
-      fail(e == cudaErrorMemoryAllocation ? FMM_ERR_OOM : FMM_ERR_CUDA, "cudaMallocAsync");
+      fail(e == cudaErrorMemoryAllocation ? FMM_ERR_OOM : FMM_ERR_CUDA, "cudaMallocFromPoolAsync");
     }
   }
   live.push_back(p);
