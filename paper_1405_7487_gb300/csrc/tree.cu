@@ -83,7 +83,7 @@ __global__ void k_bbox_partial(const R* __restrict__ xyzq, int64_t n, double* __
 __global__ void k_bbox_final(const double* __restrict__ part, int nb, double* __restrict__ root,
                              int* __restrict__ nonfinite) {
   // min/max are exact, so the reduction order does not matter
-  __shared__ double sh[kThreads][7];
+  __shared__ double sh[kThreads / 32][7];
   double r[7] = {INFINITY, INFINITY, INFINITY, -INFINITY, -INFINITY, -INFINITY, 0.0};
   for (int b = threadIdx.x; b < nb; b += blockDim.x) {
     for (int a = 0; a < 3; ++a) {
@@ -92,15 +92,22 @@ __global__ void k_bbox_final(const double* __restrict__ part, int nb, double* __
     }
     r[6] = fmax(r[6], part[7 * b + 6]);
   }
-  for (int k = 0; k < 7; ++k) sh[threadIdx.x][k] = r[k];
+  for (int o = 16; o > 0; o >>= 1)
+    for (int k = 0; k < 7; ++k) {
+      const double v = __shfl_down_sync(0xffffffffu, r[k], o);
+      r[k] = k < 3 ? fmin(r[k], v) : fmax(r[k], v);
+    }
+  const int warp = threadIdx.x >> 5;
+  if ((threadIdx.x & 31) == 0)
+    for (int k = 0; k < 7; ++k) sh[warp][k] = r[k];
   __syncthreads();
   if (threadIdx.x != 0) return;
-  for (int t = 1; t < (int)blockDim.x; ++t) {
+  for (int w = 1; w < (int)(blockDim.x >> 5); ++w) {
     for (int a = 0; a < 3; ++a) {
-      r[a] = fmin(r[a], sh[t][a]);
-      r[3 + a] = fmax(r[3 + a], sh[t][3 + a]);
+      r[a] = fmin(r[a], sh[w][a]);
+      r[3 + a] = fmax(r[3 + a], sh[w][3 + a]);
     }
-    r[6] = fmax(r[6], sh[t][6]);
+    r[6] = fmax(r[6], sh[w][6]);
   }
   *nonfinite = r[6] != 0.0;
   double h = 0.0;
@@ -176,23 +183,39 @@ __device__ __forceinline__ int lower_digit(const uint64_t* __restrict__ keys, in
 
 // Children of the cells of one level: a cell with more than ncrit bodies
 // (and below level 21) splits into its nonempty octants, in Morton order.
+// Eight lanes per cell: lane d finds where octant d starts (one binary
+// search over the cell's sorted keys), its neighbour's start is its end, and
+// a ballot over the eight lanes numbers the nonempty octants.
+struct Octants {
+  int c, d, s, e, b, nb;
+  bool valid, split;
+  unsigned group;  // nonempty-octant bits of this cell's eight lanes
+};
+
+__device__ __forceinline__ Octants octants(const uint64_t* __restrict__ keys, const int32_t* __restrict__ bbeg,
+                                           const int32_t* __restrict__ bend, int ncell, int level, int ncrit) {
+  Octants o;
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  o.c = g >> 3;
+  o.d = g & 7;
+  o.valid = o.c < ncell;
+  o.s = o.valid ? bbeg[o.c] : 0;
+  o.e = o.valid ? bend[o.c] : 0;
+  o.split = o.valid && o.e - o.s > ncrit && level < kMaxLevel;
+  o.b = o.s;
+  if (o.split && o.d > 0) o.b = lower_digit(keys, o.s, o.e, 3 * (kMaxLevel - level - 1), o.d);
+  o.nb = __shfl_down_sync(0xffffffffu, o.b, 1, 8);
+  if (o.d == 7) o.nb = o.e;
+  const unsigned m = __ballot_sync(0xffffffffu, o.split && o.nb > o.b);
+  o.group = (m >> (threadIdx.x & 24)) & 0xffu;
+  return o;
+}
+
 __global__ void k_split_count(const uint64_t* __restrict__ keys, const int32_t* __restrict__ bbeg,
                               const int32_t* __restrict__ bend, int ncell, int level, int ncrit,
                               int64_t* __restrict__ nchild) {
-  const int c = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= ncell) return;
-  const int s = bbeg[c], e = bend[c];
-  int cnt = 0;
-  if (e - s > ncrit && level < kMaxLevel) {
-    const int shift = 3 * (kMaxLevel - level - 1);
-    int prev = s;
-    for (int d = 1; d <= 8; ++d) {
-      int b = d < 8 ? lower_digit(keys, s, e, shift, d) : e;
-      cnt += b > prev;
-      prev = b;
-    }
-  }
-  nchild[c] = cnt;
+  const Octants o = octants(keys, bbeg, bend, ncell, level, ncrit);
+  if (o.valid && o.d == 0) nchild[o.c] = __popc(o.group);
 }
 
 __global__ void k_split_write(const uint64_t* __restrict__ keys, const int32_t* __restrict__ bbeg,
@@ -204,30 +227,23 @@ __global__ void k_split_write(const uint64_t* __restrict__ keys, const int32_t* 
                               int32_t* __restrict__ o_bend, int32_t* __restrict__ o_ix,
                               int32_t* __restrict__ o_iy, int32_t* __restrict__ o_iz,
                               int32_t* __restrict__ o_parent) {
-  const int c = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= ncell) return;
-  const int s = bbeg[c], e = bend[c];
-  int k = (int)off[c];
-  const int k0 = k;
-  if (e - s > ncrit && level < kMaxLevel) {
-    const int shift = 3 * (kMaxLevel - level - 1);
-    int prev = s;
-    for (int d = 0; d < 8; ++d) {
-      int b = d < 7 ? lower_digit(keys, s, e, shift, d + 1) : e;
-      if (b > prev) {
-        o_bbeg[k] = prev;
-        o_bend[k] = b;
-        o_ix[k] = 2 * ix[c] + ((d >> 2) & 1);
-        o_iy[k] = 2 * iy[c] + ((d >> 1) & 1);
-        o_iz[k] = 2 * iz[c] + (d & 1);
-        o_parent[k] = first_cell + c;
-        ++k;
-      }
-      prev = b;
-    }
+  const Octants o = octants(keys, bbeg, bend, ncell, level, ncrit);
+  if (!o.valid) return;
+  const int k0 = (int)off[o.c];
+  const int n = __popc(o.group);
+  if ((o.group >> o.d) & 1u) {
+    const int k = k0 + __popc(o.group & ((1u << o.d) - 1u));
+    o_bbeg[k] = o.b;
+    o_bend[k] = o.nb;
+    o_ix[k] = 2 * ix[o.c] + ((o.d >> 2) & 1);
+    o_iy[k] = 2 * iy[o.c] + ((o.d >> 1) & 1);
+    o_iz[k] = 2 * iz[o.c] + (o.d & 1);
+    o_parent[k] = first_cell + o.c;
   }
-  cbeg[c] = k > k0 ? first_child + k0 : -1;
-  nch[c] = k - k0;
+  if (o.d == 0) {
+    cbeg[o.c] = n > 0 ? first_child + k0 : -1;
+    nch[o.c] = n;
+  }
 }
 
 __global__ void k_fill_i32(int32_t* __restrict__ p, int64_t n, int32_t v) {
@@ -329,8 +345,8 @@ void build_tree_impl(fmm_tree* t, const R* xyzq) {
     cur.cbeg = alloc_n<int32_t>(a, cur.n);
     cur.nch = alloc_n<int32_t>(a, cur.n);
     int64_t* off = alloc_n<int64_t>(a, cur.n);
-    k_split_count<<<blocks(cur.n), kThreads, 0, s>>>(t->keys, cur.bbeg, cur.bend, cur.n, l, t->ncrit,
-                                                     off);
+    k_split_count<<<blocks(8 * (int64_t)cur.n), kThreads, 0, s>>>(t->keys, cur.bbeg, cur.bend, cur.n, l,
+                                                                   t->ncrit, off);
     GB_LAUNCH("k_split_count");
     const int64_t nnext = scan_exclusive_i64_total(a, off, cur.n, s);
     if (nnext > 0x7fffffff - first - cur.n) fail(FMM_ERR_ARG, "too many cells");
@@ -344,7 +360,7 @@ void build_tree_impl(fmm_tree* t, const R* xyzq) {
       nx.iz = alloc_n<int32_t>(a, nnext);
       nx.parent = alloc_n<int32_t>(a, nnext);
     }
-    k_split_write<<<blocks(cur.n), kThreads, 0, s>>>(
+    k_split_write<<<blocks(8 * (int64_t)cur.n), kThreads, 0, s>>>(
         t->keys, cur.bbeg, cur.bend, cur.ix, cur.iy, cur.iz, cur.n, l, t->ncrit, first,
         first + cur.n, off, cur.cbeg, cur.nch, nx.bbeg, nx.bend, nx.ix, nx.iy, nx.iz, nx.parent);
     GB_LAUNCH("k_split_write");
