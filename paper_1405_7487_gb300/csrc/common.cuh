@@ -1,6 +1,7 @@
 // common.cuh -- internal declarations shared by the gbfmm CUDA sources.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -120,6 +121,7 @@ struct fmm_tree {
   int32_t* entry_src = nullptr;    // nentry x kTile
   void* m2l_ops = nullptr;         // nclass x Kp x Kp (out-major), working precision
   float* m2l_ops_lo = nullptr;     // low parts for the 3xTF32 engine
+  CUtensorMap m2l_ops_map[2] = {}; // TMA maps of the operator hi / lo parts (tensor-core engine)
   int m2l_engine = 0;
   void* m2m_ops = nullptr;  // 8 x Kp x Kp
   void* l2l_ops = nullptr;  // 8 x Kp x Kp

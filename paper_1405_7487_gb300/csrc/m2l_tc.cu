@@ -17,22 +17,25 @@
 // compensated (Kahan) summation in a fixed order (k_m2l_reduce).  Short
 // chunks bound the rounding of the fp32 tensor-core accumulation.
 //
-// Pipeline (one CTA per chunk, 160 threads):
-//   warps 0-3  producers: cp.async 16-byte copies of the 128 source rows
-//              (hi and lo) and of the Kp operator rows (hi and lo) of one
-//              32-element k-block into a stage, in the 128-byte-swizzled
-//              K-major layout the MMA descriptors describe.  Each thread
-//              publishes its part of a stage with cp.async.mbarrier.arrive
-//              (the arrival on the stage's "full" barrier fires when its
-//              copies land), so up to nstage stages are in flight.  Then
-//              the epilogue (TMEM -> the chunk's partial).
-//   warp 4     TMEM allocation; one elected lane waits for a full stage,
-//              fences the generic-proxy writes against the tensor core's
-//              async-proxy reads, issues the stage's MMAs and commits them
-//              to the stage's "empty" barrier.
+// Pipeline (one CTA per chunk, 160 threads), stages of one 32-element
+// k-block in the 128-byte-swizzled K-major layout the MMA descriptors
+// describe:
+//   warps 0-3  producers: cp.async 16-byte copies of the 128 gathered source
+//              rows (hi and lo); each thread publishes its part of a stage
+//              with cp.async.mbarrier.arrive (the arrival on the stage's
+//              "full" barrier fires when its copies land).  Thread 0 also
+//              loads the operator's k-block (Kp rows, hi and lo) with two
+//              tiled TMA copies that complete on the stage's operator
+//              barrier.  Up to nstage stages are in flight.  Then the
+//              epilogue (TMEM -> the chunk's partial).
+//   warp 4     TMEM allocation; one elected lane waits for both barriers of
+//              a stage, fences the generic-proxy writes against the tensor
+//              core's async-proxy reads, issues the stage's MMAs and commits
+//              them to the stage's "empty" barrier.
 // Every wait is bounded; a wait that gives up sets the error flag, the
 // roles drain and the TMEM is released.
 #include <algorithm>
+#include <cstdlib>
 #include <vector>
 
 #include "kernels.cuh"
@@ -42,11 +45,12 @@ namespace {
 
 constexpr int kProducers = 128;
 constexpr int kThreadsTC = 160;
+constexpr int kMaxStages = 8;
+constexpr long long kSpinLimit = 1ll << 20;
+
 constexpr int kKB = 32;               // fp32 elements per k-block (128 bytes per row)
 constexpr int kRowB = kKB * 4;        // bytes per row of a k-block
 constexpr int kStageA = 128 * kRowB;  // bytes of one 128-row operand block
-constexpr int kMaxStages = 8;
-constexpr long long kSpinLimit = 1ll << 20;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -54,9 +58,37 @@ __device__ __forceinline__ uint32_t smem_u32(const void* p) {
 
 // Byte offset of 16-byte chunk c (0..7) of row r in a [rows][128 B] block
 // with the 128-byte swizzle: address bits [4,6] are XORed with bits [7,9],
-// i.e. the chunk index with r % 8 (8-row groups of 1024 bytes).
+// i.e. the chunk index with r % 8 (8-row groups of 1024 bytes).  TMA writes
+// the same pattern for a 128-byte-wide box with CU_TENSOR_MAP_SWIZZLE_128B.
 __device__ __forceinline__ uint32_t swz(int r, int c) {
   return (uint32_t)((r << 7) + (((c ^ r) & 7) << 4));
+}
+
+// UMMA shared-memory descriptor: K-major, 128-byte swizzle, 8-row groups
+// 1024 bytes apart (SBO), sm_100 descriptor version 1.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((addr >> 4) & 0x3FFF);
+  d |= (uint64_t)1 << 16;              // LBO (unused for swizzled K-major)
+  d |= (uint64_t)(1024 >> 4) << 32;    // SBO
+  d |= (uint64_t)1 << 46;              // version
+  d |= (uint64_t)2 << 61;              // SWIZZLE_128B
+  return d;
+}
+
+// 2-D tiled TMA load of the box at (x, y) into dst; completes on bar.
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
+      "[%4];\n" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
+      : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n}\n" ::"r"(bar),
+               "r"(bytes)
+               : "memory");
 }
 
 __device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, int bytes) {
@@ -91,18 +123,6 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatil
   return false;
 }
 
-// UMMA shared-memory descriptor: K-major, 128-byte swizzle, 8-row groups
-// 1024 bytes apart (SBO), sm_100 descriptor version 1.
-__device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
-  uint64_t d = 0;
-  d |= (uint64_t)((addr >> 4) & 0x3FFF);
-  d |= (uint64_t)1 << 16;              // LBO (unused for swizzled K-major)
-  d |= (uint64_t)(1024 >> 4) << 32;    // SBO
-  d |= (uint64_t)1 << 46;              // version
-  d |= (uint64_t)2 << 61;              // SWIZZLE_128B
-  return d;
-}
-
 // Instruction descriptor, kind::tf32: D fp32, A and B tf32, both K-major,
 // N = n, M = 128.
 __device__ __forceinline__ uint32_t idesc_tf32(int n) {
@@ -123,12 +143,12 @@ __device__ __forceinline__ void mma_commit(uint32_t bar) {
 }
 
 __global__ void __launch_bounds__(kThreadsTC, 1)
-    k_m2l_tc(const int4* __restrict__ chunks, const int32_t* __restrict__ entry_class,
-             const int32_t* __restrict__ entry_src, const float* __restrict__ ops_hi,
-             const float* __restrict__ ops_lo, const float* __restrict__ Mhi, const float* __restrict__ Mlo, int Kp,
-             int nstage, int tmem_cols, float* __restrict__ part, int* __restrict__ err) {
+    k_m2l_tc(const __grid_constant__ CUtensorMap tm_ops_hi, const __grid_constant__ CUtensorMap tm_ops_lo,
+             const int4* __restrict__ chunks, const int32_t* __restrict__ entry_class,
+             const int32_t* __restrict__ entry_src, const float* __restrict__ Mhi, const float* __restrict__ Mlo,
+             int Kp, int nstage, int tmem_cols, float* __restrict__ part, int* __restrict__ err) {
   extern __shared__ unsigned char smem_raw[];
-  __shared__ uint64_t bar_full[kMaxStages], bar_empty[kMaxStages], bar_done;
+  __shared__ uint64_t bar_full[kMaxStages], bar_opfull[kMaxStages], bar_empty[kMaxStages], bar_done;
   __shared__ uint32_t tmem_base;
   __shared__ volatile int abort_flag;
 
@@ -139,8 +159,8 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
   const int stage_bytes = 2 * kStageA + 2 * stageB;
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  // chunk = (tile, first entry, end entry): a bounded run of the tile's
-  // entries, accumulated in TMEM and written as one partial sum
+  // chunk = (tile, first entry, end entry, partial slot): a bounded run of
+  // the tile's entries, accumulated in TMEM and written as one partial sum
   const int4 ch = chunks[blockIdx.x];
   const int e0 = ch.y, e1 = ch.z;
   const int nkb = (Kp + kKB - 1) / kKB;
@@ -149,7 +169,8 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
   if (tid == 0) {
     abort_flag = 0;
     for (int s = 0; s < nstage; ++s) {
-      mbar_init(smem_u32(&bar_full[s]), kProducers);
+      mbar_init(smem_u32(&bar_full[s]), kProducers);  // the producers' cp.async arrivals
+      mbar_init(smem_u32(&bar_opfull[s]), 1);         // the operator TMA (expect-tx)
       mbar_init(smem_u32(&bar_empty[s]), 1);
     }
     mbar_init(smem_u32(&bar_done), 1);
@@ -168,29 +189,48 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
 
   if (warp < 4) {
     // ---------------------------------------------------------- producers
+    // A (the gathered source rows): thread r moves 16-byte chunk (r % 8) of
+    // rows r / 8 + 16 i, so eight neighbouring threads read one 128-byte row
+    // segment and write one swizzled line; each thread's part of a stage is
+    // published by cp.async.mbarrier.arrive, which fires when its copies
+    // have landed.  B (the operator's k-block, Kp rows x 128 bytes, hi and
+    // lo): two tiled TMA loads issued by thread 0, completing on the stage's
+    // operator barrier through expect-tx.  The producers run ahead by up to
+    // nstage stages; the next entry's source rows are loaded while the
+    // current entry is copied.
     const int r = tid;
-    // Thread r moves 16-byte chunk (r % 8) of rows r / 8 + 16 i of both
-    // operands, so eight neighbouring threads read one 128-byte row segment
-    // and write one swizzled 128-byte line.  A stage is published by
-    // cp.async.mbarrier.arrive: each thread's arrival on the stage's "full"
-    // barrier fires when its copies have landed, so the producers run ahead
-    // by up to nstage stages without waiting for their own copies.
     const int c8 = r & 7, r8 = r >> 3;
-    const int nbrow = (Kp + 15) / 16;  // operator rows per thread
-    int src[8];
-    int cur_e = -1, cls = 0;
+    const uint32_t b_bytes = 2u * (uint32_t)stageB;
+    int src[8], nsrc[8];
+    int cls = 0, ncls = 0;
+    int tma_issued = 0;  // thread 0: operator loads issued
+    auto fetch = [&](int e, int (&to)[8], int& tc) {
+#pragma unroll
+      for (int i = 0; i < 8; ++i) to[i] = __ldg(entry_src + (int64_t)e * kTile + r8 + 16 * i);
+      tc = __ldg(entry_class + e);
+    };
+    if (nit > 0) fetch(e0, nsrc, ncls);
     for (int it = 0; it < nit; ++it) {
       const int e = e0 + it / nkb, kb = it % nkb;
       const int s = it % nstage, round = it / nstage;
-      if (round > 0 && !mbar_wait(smem_u32(&bar_empty[s]), (round - 1) & 1, &abort_flag)) break;
-      if (e != cur_e) {
-        cur_e = e;
+      if (kb == 0) {
 #pragma unroll
-        for (int i = 0; i < 8; ++i) src[i] = __ldg(entry_src + (int64_t)e * kTile + r8 + 16 * i);
-        cls = __ldg(entry_class + e);
+        for (int i = 0; i < 8; ++i) src[i] = nsrc[i];
+        cls = ncls;
+        if (e + 1 < e1) fetch(e + 1, nsrc, ncls);
       }
+      if (round > 0 && !mbar_wait(smem_u32(&bar_empty[s]), (round - 1) & 1, &abort_flag)) break;
       const uint32_t sb = base + s * stage_bytes;
       const int k0 = kb * kKB;
+      if (r == 0) {
+        // the box is 32 columns wide; columns past Kp (last k-block) read as
+        // zeros and are not used by the MMAs
+        const uint32_t ob = smem_u32(&bar_opfull[s]);
+        mbar_arrive_expect_tx(ob, b_bytes);
+        tma_load_2d(sb + 2 * kStageA, &tm_ops_hi, k0, cls * Kp, ob);
+        tma_load_2d(sb + 2 * kStageA + stageB, &tm_ops_lo, k0, cls * Kp, ob);
+        tma_issued = it + 1;
+      }
       const int nch = min(kKB, Kp - k0) / 4;  // 16-byte chunks in this k-block
       if (c8 < nch) {
         // A rows: the source multipole of each tile row (zeros for an empty row)
@@ -202,22 +242,18 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
           cp_async16(sb + swz(row, c8), Mhi + off, bytes);
           cp_async16(sb + kStageA + swz(row, c8), Mlo + off, bytes);
         }
-        // B rows: output coefficient rows of the operator
-        const float* oh = ops_hi + (int64_t)cls * Kp * Kp + k0 + 4 * c8;
-        const float* ol = ops_lo + (int64_t)cls * Kp * Kp + k0 + 4 * c8;
-        for (int i = 0; i < nbrow; ++i) {
-          const int row = r8 + 16 * i;
-          if (row < Kp) {
-            cp_async16(sb + 2 * kStageA + swz(row, c8), oh + (int64_t)row * Kp, 16);
-            cp_async16(sb + 2 * kStageA + stageB + swz(row, c8), ol + (int64_t)row * Kp, 16);
-          }
-        }
       }
       asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];\n" ::"r"(smem_u32(&bar_full[s]))
                    : "memory");
     }
-    // no copy may still be in flight when the CTA ends
+    // no copy may still be in flight when the CTA ends: the thread's own
+    // cp.async copies, and (thread 0, after an abort) the last operator load
     cp_async_wait<0>();
+    if (r == 0 && tma_issued > 0) {
+      volatile int dummy = 0;
+      const int last = tma_issued - 1;
+      mbar_wait(smem_u32(&bar_opfull[last % nstage]), (last / nstage) & 1, &dummy);
+    }
     // ------------------------------------------------------------ epilogue
     const bool ok = nit > 0 && mbar_wait(smem_u32(&bar_done), 0, &abort_flag);
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
@@ -251,12 +287,13 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
     for (int it = 0; it < nit; ++it) {
       const int kb = it % nkb;
       const int s = it % nstage, round = it / nstage;
-      if (!mbar_wait(smem_u32(&bar_full[s]), round & 1, &abort_flag)) {
+      if (!mbar_wait(smem_u32(&bar_full[s]), round & 1, &abort_flag) ||
+          !mbar_wait(smem_u32(&bar_opfull[s]), round & 1, &abort_flag)) {
         ok = false;
         break;
       }
-      // the stage was written through the generic proxy (cp.async); make it
-      // visible to the tensor core's async-proxy reads
+      // A was written through the generic proxy (cp.async); make it visible
+      // to the tensor core's async-proxy reads
       fence_async_smem();
       asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
       const uint32_t sb = base + s * stage_bytes;
@@ -272,7 +309,9 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
       }
       mma_commit(smem_u32(&bar_empty[s]));
     }
-    if (ok && nit > 0) mma_commit(smem_u32(&bar_done));
+    // tracks every MMA issued, also after an abort, so that the TMEM is
+    // released only when they are done
+    if (nit > 0) mma_commit(smem_u32(&bar_done));
     if (!ok) abort_flag = 1;
   }
   // drain: the last commits must land before the TMEM is released
@@ -352,13 +391,47 @@ void launch_m2l_tcgen05(fmm_tree* t, cudaStream_t s) {
   int cols = 32;
   while (cols < Kp) cols <<= 1;
   const int64_t n = (int64_t)t->ncell * Kp;
-  k_m2l_tc<<<t->nchunk, kThreadsTC, smem, s>>>(t->m2l_chunks, t->entry_class, t->entry_src,
-                                               (const float*)t->m2l_ops, t->m2l_ops_lo, t->M_lo + n, t->M_lo, Kp,
-                                               nstage, cols, t->m2l_part, t->dev_err);
+  k_m2l_tc<<<t->nchunk, kThreadsTC, smem, s>>>(t->m2l_ops_map[0], t->m2l_ops_map[1], t->m2l_chunks, t->entry_class,
+                                               t->entry_src, t->M_lo + n, t->M_lo, Kp, nstage, cols, t->m2l_part,
+                                               t->dev_err);
   GB_LAUNCH("k_m2l_tc");
   k_m2l_reduce<<<t->ntile, 256, 0, s>>>(t->tile_tgt, t->tile_cptr, t->m2l_part, t->K, Kp, (float*)t->L);
   GB_LAUNCH("k_m2l_reduce");
 }
+
+namespace {
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+// cuTensorMapEncodeTiled from the driver, found through the runtime (the
+// library does not link libcuda)
+EncodeTiledFn encode_tiled() {
+  static EncodeTiledFn fn = [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    GB_CK(cudaGetDriverEntryPoint("cuTensorMapEncodeTiled", &p, cudaEnableDefault, &q));
+    if (q != cudaDriverEntryPointSuccess || !p) fail(FMM_ERR_CUDA, "cuTensorMapEncodeTiled unavailable");
+    return reinterpret_cast<EncodeTiledFn>(p);
+  }();
+  return fn;
+}
+
+// The operators as one fp32 row-major [nclass * Kp][Kp] matrix; boxes of
+// 32 columns x Kp rows (one k-block of one operator), 128-byte swizzle.
+void make_ops_map(CUtensorMap* map, const float* ptr, int64_t rows, int Kp) {
+  const cuuint64_t dims[2] = {(cuuint64_t)Kp, (cuuint64_t)rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)Kp * sizeof(float)};
+  const cuuint32_t box[2] = {(cuuint32_t)kKB, (cuuint32_t)Kp};
+  const cuuint32_t estr[2] = {1, 1};
+  const CUresult r = encode_tiled()(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(ptr), dims, strides,
+                                    box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) fail(FMM_ERR_CUDA, "cuTensorMapEncodeTiled (M2L operators) failed");
+}
+
+}  // namespace
 
 // Chunks of at most `per` consecutive entries of every tile (host: the entry
 // ranges of the tiles are read back once at build time), the partial buffer
@@ -393,6 +466,11 @@ void build_m2l_chunks(fmm_tree* t, int per) {
   GB_CK(cudaMemcpyAsync(t->tile_cptr, cptr.data(), sizeof(int32_t) * cptr.size(), cudaMemcpyHostToDevice, s));
   t->m2l_part = alloc_n<float>(a, (size_t)t->nchunk * kTile * t->Kp);
   t->M_lo = alloc_n<float>(a, 2 * (size_t)t->ncell * t->Kp);
+  if (t->nclass > 0) {
+    const int64_t rows = (int64_t)t->nclass * t->Kp;
+    make_ops_map(&t->m2l_ops_map[0], (const float*)t->m2l_ops, rows, t->Kp);
+    make_ops_map(&t->m2l_ops_map[1], t->m2l_ops_lo, rows, t->Kp);
+  }
   GB_CK(cudaStreamSynchronize(s));
 }
 
