@@ -130,9 +130,14 @@ struct fmm_tree {
   void* L = nullptr;  // ncell x Kp
   float* M_lo = nullptr;  // split copy of M for the 3xTF32 engine (lo | hi)
   int nchunk = 0;                  // M2L work units of the tensor-core engine
-  int4* m2l_chunks = nullptr;      // (tile, first entry, end entry, partial slot)
-  int32_t* tile_cptr = nullptr;    // partial slots of tile t: [cptr[t], cptr[t+1])
-  float* m2l_part = nullptr;       // nchunk x Kp x kTile partial local expansions
+  int4* m2l_chunks = nullptr;      // single-tile engine: (tile, first entry, end entry, partial slot);
+                                   // quad engine: (quad, first quad entry, end quad entry, chunk)
+  int32_t* tile_cptr = nullptr;    // single-tile: partial slots of tile t [cptr[t], cptr[t+1]);
+                                   // quad: chunks of quad q [cptr[q], cptr[q+1])
+  float* m2l_part = nullptr;       // partial local expansions, Kp x kTile each
+  bool m2l_quad = false;           // four tiles per CTA sharing each operator k-block
+  int32_t* quad_class = nullptr;   // per quad entry: the class
+  int4* quad_entry = nullptr;      // per quad entry: the entry of each of the quad's tiles (-1: none)
   void* near = nullptr;   // N x 4 (phi, grad) sorted, P2P part
   void* grad_q = nullptr; // N x 4 (phi, grad) sorted, of the last evaluate
   void* q_last = nullptr; // N sorted charges of the last evaluate

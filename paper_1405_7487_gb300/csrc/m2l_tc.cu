@@ -103,9 +103,6 @@ __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.a
 __device__ __forceinline__ void mbar_init(uint32_t bar, int count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(bar), "r"(count) : "memory");
 }
-__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
-  asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.shared::cta.b64 st, [%0];\n}\n" ::"r"(bar) : "memory");
-}
 // Bounded wait for the phase with the given parity; false if it gave up (or
 // another role aborted).
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag) {
@@ -329,6 +326,278 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
   }
 }
 
+// ---------------------------------------------------------------------------
+// Quad engine (Kp <= 128): one CTA takes four tiles of the same octant
+// together.  The tiles' class lists are merged into quad entries (class, the
+// entry of each tile or -1); per quad entry and k-block the operator's
+// k-block is loaded once (TMA, two stages) and multiplied with the source
+// rows of every tile that has the class (cp.async, kAStages stages of
+// 128 rows), each tile accumulating in its own quarter of the TMEM (128
+// columns).  So the operator bytes per tile entry drop four-fold, and the
+// source-row stages can run deeper than the combined stages of the
+// single-tile engine.  Chunks of up to kM2LChunk quad entries per CTA; the
+// partial of (chunk, tile) is written column-major, zeros for a tile without
+// entries in the chunk.
+constexpr int kQuad = 4;
+constexpr int kMaxAStages = 6;
+constexpr int kQuadMaxKp = 128;  // four 128-column TMEM accumulators
+
+// GBFMM_M2L_SINGLE=1 selects the single-tile engine at every Kp (tuning and
+// cross-checking knob)
+bool m2l_single_tile_forced() {
+  static const bool on = [] {
+    const char* env = getenv("GBFMM_M2L_SINGLE");
+    return env && atoi(env) == 1;
+  }();
+  return on;
+}
+
+__global__ void __launch_bounds__(kThreadsTC, 1)
+    k_m2l_tc4(const __grid_constant__ CUtensorMap tm_ops_hi, const __grid_constant__ CUtensorMap tm_ops_lo,
+              const int4* __restrict__ chunks, const int32_t* __restrict__ quad_class,
+              const int4* __restrict__ quad_entry, const int32_t* __restrict__ entry_src,
+              const float* __restrict__ Mhi, const float* __restrict__ Mlo, int Kp, int nastage,
+              float* __restrict__ part, int* __restrict__ err) {
+  extern __shared__ unsigned char smem_raw[];
+  __shared__ uint64_t bar_bfull[2], bar_bempty[2], bar_afull[kMaxAStages], bar_aempty[kMaxAStages], bar_done;
+  __shared__ uint32_t tmem_base;
+  __shared__ volatile int abort_flag;
+
+  const uint32_t raw = smem_u32(smem_raw);
+  const uint32_t base = (raw + 1023u) & ~1023u;
+  const int stageB = Kp * kRowB;           // one of hi / lo
+  const uint32_t bbase = base;             // 2 operator stages of 2 * stageB
+  const uint32_t abase = base + 4 * stageB;  // nastage source stages of 2 * kStageA
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int4 ch = chunks[blockIdx.x];
+  const int j0 = ch.y, j1 = ch.z;
+  const int nkb = (Kp + kKB - 1) / kKB;
+
+  if (tid == 0) {
+    abort_flag = 0;
+    for (int s = 0; s < 2; ++s) {
+      mbar_init(smem_u32(&bar_bfull[s]), 1);
+      mbar_init(smem_u32(&bar_bempty[s]), 1);
+    }
+    for (int s = 0; s < nastage; ++s) {
+      mbar_init(smem_u32(&bar_afull[s]), kProducers);
+      mbar_init(smem_u32(&bar_aempty[s]), 1);
+    }
+    mbar_init(smem_u32(&bar_done), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  if (warp == 4) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(&tmem_base)),
+                 "r"(512)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+  const uint32_t tmem = tmem_base;
+
+  if (warp < 4) {
+    // ---------------------------------------------------------- producers
+    const int r = tid;
+    const int c8 = r & 7, r8 = r >> 3;
+    // the next quad entry's class, entries and source rows are loaded while
+    // the current one is copied
+    int src[kQuad][8], nsrc[kQuad][8];
+    int ncls = 0, used = 0;
+    int4 ne4 = make_int4(-1, -1, -1, -1);
+    auto fetch = [&](int j) {
+      ncls = __ldg(quad_class + j);
+      ne4 = __ldg(quad_entry + j);
+      const int ev[kQuad] = {ne4.x, ne4.y, ne4.z, ne4.w};
+#pragma unroll
+      for (int q = 0; q < kQuad; ++q)
+        if (ev[q] >= 0) {
+#pragma unroll
+          for (int i = 0; i < 8; ++i) nsrc[q][i] = __ldg(entry_src + (int64_t)ev[q] * kTile + r8 + 16 * i);
+        }
+    };
+    int bi = 0, ai = 0;
+    int tma_issued = 0;  // thread 0: operator stages issued
+    bool stop = false;
+    if (j1 > j0) fetch(j0);
+    for (int j = j0; j < j1 && !stop; ++j) {
+      const int cls = ncls;
+      const int ev[kQuad] = {ne4.x, ne4.y, ne4.z, ne4.w};
+#pragma unroll
+      for (int q = 0; q < kQuad; ++q) {
+        if (ev[q] < 0) continue;
+        used |= 1 << q;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) src[q][i] = nsrc[q][i];
+      }
+      if (j + 1 < j1) fetch(j + 1);
+      for (int kb = 0; kb < nkb && !stop; ++kb, ++bi) {
+        const int k0 = kb * kKB;
+        if (r == 0) {
+          const int bs = bi & 1, bround = bi >> 1;
+          if (bround > 0 && !mbar_wait(smem_u32(&bar_bempty[bs]), (bround - 1) & 1, &abort_flag)) {
+            stop = true;
+            break;
+          }
+          // the box is 32 columns wide; columns past Kp (last k-block) read
+          // as zeros and are not used by the MMAs
+          const uint32_t fb = smem_u32(&bar_bfull[bs]);
+          const uint32_t sb = bbase + bs * 2 * stageB;
+          mbar_arrive_expect_tx(fb, 2u * (uint32_t)stageB);
+          tma_load_2d(sb, &tm_ops_hi, k0, cls * Kp, fb);
+          tma_load_2d(sb + stageB, &tm_ops_lo, k0, cls * Kp, fb);
+          tma_issued = bi + 1;
+        }
+        const int nch = min(kKB, Kp - k0) / 4;  // 16-byte chunks in this k-block
+#pragma unroll
+        for (int q = 0; q < kQuad; ++q) {
+          if (ev[q] < 0) continue;
+          const int as = ai % nastage, around = ai / nastage;
+          if (around > 0 && !mbar_wait(smem_u32(&bar_aempty[as]), (around - 1) & 1, &abort_flag)) {
+            stop = true;
+            break;
+          }
+          const uint32_t sa = abase + as * 2 * kStageA;
+          if (c8 < nch) {
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+              const int row = r8 + 16 * i;
+              const int sidx = src[q][i];
+              const int64_t off = (int64_t)(sidx >= 0 ? sidx : 0) * Kp + k0 + 4 * c8;
+              const int bytes = sidx >= 0 ? 16 : 0;
+              cp_async16(sa + swz(row, c8), Mhi + off, bytes);
+              cp_async16(sa + kStageA + swz(row, c8), Mlo + off, bytes);
+            }
+          }
+          asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];\n" ::"r"(smem_u32(&bar_afull[as]))
+                       : "memory");
+          ++ai;
+        }
+      }
+    }
+    // no copy may still be in flight when the CTA ends
+    cp_async_wait<0>();
+    if (r == 0 && tma_issued > 0) {
+      volatile int dummy = 0;
+      const int last = tma_issued - 1;
+      mbar_wait(smem_u32(&bar_bfull[last & 1]), (last >> 1) & 1, &dummy);
+    }
+    // ------------------------------------------------------------ epilogue
+    const bool ok = j1 > j0 && mbar_wait(smem_u32(&bar_done), 0, &abort_flag);
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    if (ok) {
+      for (int q = 0; q < kQuad; ++q) {
+        // partial (chunk ch.w, tile q), column-major ([Kp][128])
+        float* pcol = part + ((int64_t)ch.w * kQuad + q) * kTile * Kp + r;
+        for (int c0 = 0; c0 < Kp; c0 += 16) {
+          uint32_t v[16];
+          if (used & (1 << q)) {
+            const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(q * 128 + c0);
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
+                "[%16];\n"
+                : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+                  "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
+                  "=r"(v[15])
+                : "r"(taddr)
+                : "memory");
+            asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+          } else {
+#pragma unroll
+            for (int k = 0; k < 16; ++k) v[k] = 0u;
+          }
+#pragma unroll
+          for (int k = 0; k < 16; ++k) __stcs(pcol + (int64_t)(c0 + k) * kTile, __uint_as_float(v[k]));
+        }
+      }
+    }
+  } else if (lane == 0) {
+    // ---------------------------------------------------------------- MMA
+    const uint32_t idesc = idesc_tf32(Kp);
+    bool ok = true;
+    bool first[kQuad] = {true, true, true, true};
+    int bi = 0, ai = 0;
+    for (int j = j0; j < j1 && ok; ++j) {
+      const int4 e4 = __ldg(quad_entry + j);
+      const int ev[kQuad] = {e4.x, e4.y, e4.z, e4.w};
+      for (int kb = 0; kb < nkb && ok; ++kb, ++bi) {
+        const int bs = bi & 1, bround = bi >> 1;
+        if (!mbar_wait(smem_u32(&bar_bfull[bs]), bround & 1, &abort_flag)) {
+          ok = false;
+          break;
+        }
+        const uint32_t sb = bbase + bs * 2 * stageB;
+        const int nks = min(kKB, Kp - kb * kKB) / 8;  // tf32 k-steps of 8 elements
+#pragma unroll
+        for (int q = 0; q < kQuad; ++q) {
+          if (ev[q] < 0) continue;
+          const int as = ai % nastage, around = ai / nastage;
+          if (!mbar_wait(smem_u32(&bar_afull[as]), around & 1, &abort_flag)) {
+            ok = false;
+            break;
+          }
+          // the source rows were written through the generic proxy (cp.async)
+          fence_async_smem();
+          asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+          const uint32_t sa = abase + as * 2 * kStageA;
+          const uint32_t acc = tmem + (uint32_t)(q * 128);
+          for (int ks = 0; ks < nks; ++ks) {
+            const uint32_t off = ks * 32;
+            const uint64_t ah = smem_desc(sa + off), al = smem_desc(sa + kStageA + off);
+            const uint64_t bh = smem_desc(sb + off), bl = smem_desc(sb + stageB + off);
+            mma_tf32(acc, ah, bh, idesc, first[q] ? 0u : 1u);
+            first[q] = false;
+            mma_tf32(acc, al, bh, idesc, 1u);
+            mma_tf32(acc, ah, bl, idesc, 1u);
+          }
+          mma_commit(smem_u32(&bar_aempty[as]));
+          ++ai;
+        }
+        // the operator stage is free once the MMAs that read it are done
+        mma_commit(smem_u32(&bar_bempty[bs]));
+      }
+    }
+    // tracks every MMA issued, also after an abort
+    if (j1 > j0) mma_commit(smem_u32(&bar_done));
+    if (!ok) abort_flag = 1;
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  if (abort_flag && tid == 0) atomicExch(err, 1);
+  if (warp == 4) {
+    if (abort_flag && j1 > j0) {
+      volatile int dummy = 0;
+      mbar_wait(smem_u32(&bar_done), 0, &dummy);
+    }
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(512) : "memory");
+  }
+}
+
+// L rows of one tile = compensated (Kahan) sum of the partials of its
+// quad's chunks, in chunk order.  Thread per (coefficient, row).
+__global__ void k_m2l_reduce4(const int32_t* __restrict__ tile_tgt, const int32_t* __restrict__ quad_cptr,
+                              const float* __restrict__ part, int K, int Kp, float* __restrict__ L) {
+  const int tile = blockIdx.x;
+  const int q = tile / kQuad, lq = tile % kQuad;
+  const int c0 = quad_cptr[q], c1 = quad_cptr[q + 1];
+  for (int w = threadIdx.x; w < kTile * K; w += blockDim.x) {
+    const int c = w / kTile, r = w % kTile;
+    const int tgt = tile_tgt[(int64_t)tile * kTile + r];
+    if (tgt < 0) continue;
+    float sum = 0.f, comp = 0.f;
+    for (int chk = c0; chk < c1; ++chk) {
+      const float y = __ldcs(part + (((int64_t)chk * kQuad + lq) * Kp + c) * kTile + r) - comp;
+      const float tt = sum + y;
+      comp = (tt - sum) - y;
+      sum = tt;
+    }
+    L[(int64_t)tgt * Kp + c] = sum;
+  }
+}
+
 // hi = tf32(x) and lo = tf32(x - hi) (both rounded to nearest), for the
 // multipoles.
 __global__ void k_split_tf32(const float* __restrict__ x, int64_t n, float* __restrict__ hi, float* __restrict__ lo) {
@@ -380,9 +649,28 @@ void launch_split_tf32(fmm_tree* t, cudaStream_t s) {
   GB_LAUNCH("k_split_tf32");
 }
 
+// Quad engine source-row stages: what fits next to the two operator stages.
+int m2l_tc4_astages(int Kp) {
+  const int s = (200 * 1024 - 4 * Kp * kRowB) / (2 * kStageA);
+  return s < 2 ? 2 : (s > kMaxAStages ? kMaxAStages : s);
+}
+
 void launch_m2l_tcgen05(fmm_tree* t, cudaStream_t s) {
   if (t->ntile == 0) return;
   const int Kp = t->Kp;
+  if (t->m2l_quad) {
+    const int na = m2l_tc4_astages(Kp);
+    const size_t smem = (size_t)4 * Kp * kRowB + (size_t)na * 2 * kStageA + 1024;
+    GB_CK(cudaFuncSetAttribute(k_m2l_tc4, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const int64_t n = (int64_t)t->ncell * Kp;
+    k_m2l_tc4<<<t->nchunk, kThreadsTC, smem, s>>>(t->m2l_ops_map[0], t->m2l_ops_map[1], t->m2l_chunks, t->quad_class,
+                                                  t->quad_entry, t->entry_src, t->M_lo + n, t->M_lo, Kp, na,
+                                                  t->m2l_part, t->dev_err);
+    GB_LAUNCH("k_m2l_tc4");
+    k_m2l_reduce4<<<t->ntile, 256, 0, s>>>(t->tile_tgt, t->tile_cptr, t->m2l_part, t->K, Kp, (float*)t->L);
+    GB_LAUNCH("k_m2l_reduce4");
+    return;
+  }
   const int nstage = m2l_tc_stages(Kp);
   const size_t smem = (size_t)nstage * (2 * kStageA + 2 * Kp * kRowB) + 1024;
   // the dynamic size this launch needs (static + dynamic must stay within the
@@ -411,7 +699,7 @@ EncodeTiledFn encode_tiled() {
   static EncodeTiledFn fn = [] {
     void* p = nullptr;
     cudaDriverEntryPointQueryResult q;
-    GB_CK(cudaGetDriverEntryPoint("cuTensorMapEncodeTiled", &p, cudaEnableDefault, &q));
+    GB_CK(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q));
     if (q != cudaDriverEntryPointSuccess || !p) fail(FMM_ERR_CUDA, "cuTensorMapEncodeTiled unavailable");
     return reinterpret_cast<EncodeTiledFn>(p);
   }();
@@ -439,12 +727,86 @@ void make_ops_map(CUtensorMap* map, const float* ptr, int64_t rows, int Kp) {
 // (chunk .w); the launch order is chunk-within-tile major, so the CTAs that
 // run at the same time work on the same stretch of every tile's class list
 // and share the translation operators in L2.
+// Quad plan: the class lists of tiles 4q .. 4q + 3 (each sorted by class)
+// merged into quad entries, cut into chunks of at most `per` quad entries.
+void build_m2l_quads(fmm_tree* t, int per, const std::vector<int32_t>& eptr) {
+  Arena& a = t->arena;
+  cudaStream_t s = t->stream;
+  std::vector<int32_t> ecls(t->nentry);
+  if (t->nentry)
+    GB_CK(cudaMemcpyAsync(ecls.data(), t->entry_class, sizeof(int32_t) * t->nentry, cudaMemcpyDeviceToHost, s));
+  GB_CK(cudaStreamSynchronize(s));
+  const int nquad = (t->ntile + kQuad - 1) / kQuad;
+  std::vector<int32_t> qcls, qptr(nquad + 1, 0);
+  std::vector<int4> qent;
+  qcls.reserve(t->nentry);
+  qent.reserve(t->nentry);
+  for (int q = 0; q < nquad; ++q) {
+    int p[kQuad], end[kQuad];
+    for (int l = 0; l < kQuad; ++l) {
+      const int tile = q * kQuad + l;
+      p[l] = tile < t->ntile ? eptr[tile] : 0;
+      end[l] = tile < t->ntile ? eptr[tile + 1] : 0;
+    }
+    for (;;) {
+      int c = -1;
+      for (int l = 0; l < kQuad; ++l)
+        if (p[l] < end[l] && (c < 0 || ecls[p[l]] < c)) c = ecls[p[l]];
+      if (c < 0) break;
+      int e[kQuad];
+      for (int l = 0; l < kQuad; ++l) e[l] = (p[l] < end[l] && ecls[p[l]] == c) ? p[l]++ : -1;
+      qcls.push_back(c);
+      qent.push_back(make_int4(e[0], e[1], e[2], e[3]));
+    }
+    qptr[q + 1] = (int32_t)qcls.size();
+  }
+  std::vector<int32_t> cptr(nquad + 1, 0);
+  int maxc = 0;
+  for (int q = 0; q < nquad; ++q) {
+    const int nc = (qptr[q + 1] - qptr[q] + per - 1) / per;
+    cptr[q + 1] = cptr[q] + nc;
+    maxc = std::max(maxc, nc);
+  }
+  // chunk j of every quad before chunk j + 1 of any (operators shared in L2)
+  std::vector<int4> ch;
+  ch.reserve(cptr[nquad]);
+  for (int j = 0; j < maxc; ++j)
+    for (int q = 0; q < nquad; ++q) {
+      const int e = qptr[q] + j * per;
+      if (e < qptr[q + 1]) ch.push_back(make_int4(q, e, std::min(e + per, qptr[q + 1]), cptr[q] + j));
+    }
+  t->m2l_quad = true;
+  t->nchunk = (int)ch.size();
+  t->m2l_chunks = alloc_n<int4>(a, ch.size());
+  t->tile_cptr = alloc_n<int32_t>(a, cptr.size());
+  t->quad_class = alloc_n<int32_t>(a, qcls.size());
+  t->quad_entry = alloc_n<int4>(a, qent.size());
+  GB_CK(cudaMemcpyAsync(t->m2l_chunks, ch.data(), sizeof(int4) * ch.size(), cudaMemcpyHostToDevice, s));
+  GB_CK(cudaMemcpyAsync(t->tile_cptr, cptr.data(), sizeof(int32_t) * cptr.size(), cudaMemcpyHostToDevice, s));
+  if (!qcls.empty()) {
+    GB_CK(cudaMemcpyAsync(t->quad_class, qcls.data(), sizeof(int32_t) * qcls.size(), cudaMemcpyHostToDevice, s));
+    GB_CK(cudaMemcpyAsync(t->quad_entry, qent.data(), sizeof(int4) * qent.size(), cudaMemcpyHostToDevice, s));
+  }
+  t->m2l_part = alloc_n<float>(a, (size_t)t->nchunk * kQuad * kTile * t->Kp);
+  GB_CK(cudaStreamSynchronize(s));
+}
+
 void build_m2l_chunks(fmm_tree* t, int per) {
   Arena& a = t->arena;
   cudaStream_t s = t->stream;
   std::vector<int32_t> eptr(t->ntile + 1);
   GB_CK(cudaMemcpyAsync(eptr.data(), t->tile_eptr, sizeof(int32_t) * (t->ntile + 1), cudaMemcpyDeviceToHost, s));
   GB_CK(cudaStreamSynchronize(s));
+  t->M_lo = alloc_n<float>(a, 2 * (size_t)t->ncell * t->Kp);
+  if (t->nclass > 0) {
+    const int64_t rows = (int64_t)t->nclass * t->Kp;
+    make_ops_map(&t->m2l_ops_map[0], (const float*)t->m2l_ops, rows, t->Kp);
+    make_ops_map(&t->m2l_ops_map[1], t->m2l_ops_lo, rows, t->Kp);
+  }
+  if (t->Kp <= kQuadMaxKp && !m2l_single_tile_forced()) {
+    build_m2l_quads(t, per, eptr);
+    return;
+  }
   std::vector<int32_t> cptr(t->ntile + 1, 0);
   int maxc = 0;
   for (int tile = 0; tile < t->ntile; ++tile) {
@@ -465,12 +827,6 @@ void build_m2l_chunks(fmm_tree* t, int per) {
   GB_CK(cudaMemcpyAsync(t->m2l_chunks, ch.data(), sizeof(int4) * ch.size(), cudaMemcpyHostToDevice, s));
   GB_CK(cudaMemcpyAsync(t->tile_cptr, cptr.data(), sizeof(int32_t) * cptr.size(), cudaMemcpyHostToDevice, s));
   t->m2l_part = alloc_n<float>(a, (size_t)t->nchunk * kTile * t->Kp);
-  t->M_lo = alloc_n<float>(a, 2 * (size_t)t->ncell * t->Kp);
-  if (t->nclass > 0) {
-    const int64_t rows = (int64_t)t->nclass * t->Kp;
-    make_ops_map(&t->m2l_ops_map[0], (const float*)t->m2l_ops, rows, t->Kp);
-    make_ops_map(&t->m2l_ops_map[1], t->m2l_ops_lo, rows, t->Kp);
-  }
   GB_CK(cudaStreamSynchronize(s));
 }
 
