@@ -17,12 +17,13 @@ int to_code(const Error& e) { return e.code; }
 
 void release_tree(fmm_tree* t) {
   if (!t) return;
-  if (t->side) {
-    cudaStreamSynchronize(t->side);
-    cudaStreamDestroy(t->side);
-  }
-  if (t->fork) cudaEventDestroy(t->fork);
-  if (t->join) cudaEventDestroy(t->join);
+  for (cudaStream_t st : {t->side, t->far})
+    if (st) {
+      cudaStreamSynchronize(st);
+      cudaStreamDestroy(st);
+    }
+  for (cudaEvent_t e : {t->fork, t->join, t->fork_near, t->join_far})
+    if (e) cudaEventDestroy(e);
   for (auto& e : t->ev)
     if (e) cudaEventDestroy(e);
   t->arena.release_all();
@@ -42,9 +43,10 @@ void create_tree(fmm_tree* t, const R* xyzq) {
     int lo = 0, hi = 0;  // numerically greatest = lowest priority
     GB_CK(cudaDeviceGetStreamPriorityRange(&lo, &hi));
     GB_CK(cudaStreamCreateWithPriority(&t->side, cudaStreamNonBlocking, lo));
+    GB_CK(cudaStreamCreateWithPriority(&t->far, cudaStreamNonBlocking, hi));
   }
-  GB_CK(cudaEventCreateWithFlags(&t->fork, cudaEventDisableTiming));
-  GB_CK(cudaEventCreateWithFlags(&t->join, cudaEventDisableTiming));
+  for (cudaEvent_t* e : {&t->fork, &t->join, &t->fork_near, &t->join_far})
+    GB_CK(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
   if (t->flags & FMM_FLAG_TIMING)
     for (auto& e : t->ev) GB_CK(cudaEventCreate(&e));
   Arena& a = t->arena;
@@ -141,45 +143,63 @@ template <class R>
 void run_pass(fmm_tree* t, cudaStream_t s, int mode, R* a, R* b) {
   const bool timing = (t->flags & FMM_FLAG_TIMING) != 0;
   const bool serial = (t->flags & FMM_FLAG_SERIAL_PHASES) != 0;
-  PhaseTimer T{t, s, timing};
-  T.begin(FMM_PH_EVAL_TOTAL);
-  // Near field on the side stream (lower priority), concurrently with the far
-  // field: P2P blocks fill the SMs the tensor-core M2L leaves free.  Serial
-  // mode runs it on the caller's stream first, one phase at a time.
+  // Concurrent mode: the far field runs on the library's highest-priority
+  // stream and the near field on its lowest-priority stream, both forked
+  // from the caller's stream and joined back before L2P.  P2P is released
+  // when M2L is about to start: the M2L CTAs (one per SM, most of its shared
+  // memory) are dispatched first and P2P blocks fill the registers, shared
+  // memory and issue slots they leave free.  Serial mode runs every phase on
+  // the caller's stream, P2P first.
+  cudaStream_t fs = serial ? s : t->far;
   cudaStream_t ps = serial ? s : t->side;
-  if (!serial) {
+  PhaseTimer Ttot{t, s, timing}, T{t, fs, timing}, Tp{t, ps, timing};
+  Ttot.begin(FMM_PH_EVAL_TOTAL);
+  auto near_field = [&] {
+    if (!serial) {
+      GB_CK(cudaEventRecord(t->fork_near, fs));
+      GB_CK(cudaStreamWaitEvent(ps, t->fork_near, 0));
+    }
+    Tp.begin(FMM_PH_P2P);
+    launch_p2p<R>(t, ps);
+    Tp.end(FMM_PH_P2P);
+    if (!serial) GB_CK(cudaEventRecord(t->join, ps));
+  };
+  if (serial) {
+    near_field();
+  } else {
     GB_CK(cudaEventRecord(t->fork, s));
-    GB_CK(cudaStreamWaitEvent(t->side, t->fork, 0));
+    GB_CK(cudaStreamWaitEvent(fs, t->fork, 0));
   }
-  PhaseTimer Tp{t, ps, timing};
-  Tp.begin(FMM_PH_P2P);
-  launch_p2p<R>(t, ps);
-  Tp.end(FMM_PH_P2P);
-  if (!serial) GB_CK(cudaEventRecord(t->join, t->side));
   // far field
-  GB_CK(cudaMemsetAsync(t->L, 0, sizeof(R) * (size_t)t->ncell * t->Kp, s));
+  GB_CK(cudaMemsetAsync(t->L, 0, sizeof(R) * (size_t)t->ncell * t->Kp, fs));
   T.begin(FMM_PH_P2M);
-  launch_p2m<R>(t, s);
+  launch_p2m<R>(t, fs);
   T.end(FMM_PH_P2M);
   T.begin(FMM_PH_M2M);
-  for (int l = t->nlevel - 2; l >= 0; --l) launch_m2m<R>(t, l, s);
+  for (int l = t->nlevel - 2; l >= 0; --l) launch_m2m<R>(t, l, fs);
   T.end(FMM_PH_M2M);
   T.begin(FMM_PH_M2L);
   if (t->m2l_engine == 1) {
-    launch_split_tf32(t, s);
-    launch_m2l_tcgen05(t, s);
+    launch_split_tf32(t, fs);
+    if (!serial) near_field();
+    launch_m2l_tcgen05(t, fs);
   } else {
-    launch_m2l_cuda_core<R>(t, s);
+    if (!serial) near_field();
+    launch_m2l_cuda_core<R>(t, fs);
   }
   T.end(FMM_PH_M2L);
   T.begin(FMM_PH_L2L);
-  for (int l = 1; l < t->nlevel; ++l) launch_l2l<R>(t, l, s);
+  for (int l = 1; l < t->nlevel; ++l) launch_l2l<R>(t, l, fs);
   T.end(FMM_PH_L2L);
-  if (!serial) GB_CK(cudaStreamWaitEvent(s, t->join, 0));
-  T.begin(FMM_PH_L2P);
+  if (!serial) {
+    GB_CK(cudaEventRecord(t->join_far, fs));
+    GB_CK(cudaStreamWaitEvent(s, t->join_far, 0));
+    GB_CK(cudaStreamWaitEvent(s, t->join, 0));
+  }
+  Ttot.begin(FMM_PH_L2P);
   launch_l2p_finalize<R>(t, mode, a, b, s);
-  T.end(FMM_PH_L2P);
-  T.end(FMM_PH_EVAL_TOTAL);
+  Ttot.end(FMM_PH_L2P);
+  Ttot.end(FMM_PH_EVAL_TOTAL);
 }
 
 template <class R>

@@ -146,8 +146,9 @@ struct fmm_tree {
   unsigned long long* check_rec = nullptr;  // self-check record (checked build)
   int* dev_err = nullptr;  // set by a kernel whose bounded wait gave up
   gbfmm::Lim lim{};
-  cudaStream_t side = nullptr;  // P2P runs here, concurrently with the far field
-  cudaEvent_t fork = nullptr, join = nullptr;
+  cudaStream_t side = nullptr;  // P2P runs here (lowest priority), concurrently with the far field
+  cudaStream_t far = nullptr;   // the far field runs here (highest priority)
+  cudaEvent_t fork = nullptr, join = nullptr, fork_near = nullptr, join_far = nullptr;
   cudaEvent_t ev[2 * FMM_PH_COUNT] = {};
   float ms[FMM_PH_COUNT] = {};
 };
