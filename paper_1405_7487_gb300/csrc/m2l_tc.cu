@@ -727,17 +727,88 @@ void make_ops_map(CUtensorMap* map, const float* ptr, int64_t rows, int Kp) {
 // (chunk .w); the launch order is chunk-within-tile major, so the CTAs that
 // run at the same time work on the same stretch of every tile's class list
 // and share the translation operators in L2.
+namespace {
+
+// Quad plan on the device through a dense (quad, class) table: marking the
+// pairs present and scanning the marks numbers the quad entries in (quad,
+// class) order, which is the merge of the four tiles' sorted class lists.
+__device__ __forceinline__ int tile_of_entry(const int32_t* __restrict__ tile_eptr, int ntile, int e) {
+  int lo = 0, hi = ntile;  // last tile whose first entry is <= e
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (tile_eptr[mid] <= e) lo = mid;
+    else hi = mid;
+  }
+  return lo;
+}
+
+__global__ void k_quad_mark(const int32_t* __restrict__ tile_eptr, int ntile, const int32_t* __restrict__ entry_class,
+                            int nentry, int nclass, int64_t* __restrict__ mark) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= nentry) return;
+  const int tile = tile_of_entry(tile_eptr, ntile, e);
+  mark[(int64_t)(tile / kQuad) * nclass + entry_class[e]] = 1;
+}
+
+__global__ void k_quad_fill(const int32_t* __restrict__ tile_eptr, int ntile, const int32_t* __restrict__ entry_class,
+                            int nentry, int nclass, const int64_t* __restrict__ qid, int32_t* __restrict__ qcls,
+                            int32_t* __restrict__ qent) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= nentry) return;
+  const int tile = tile_of_entry(tile_eptr, ntile, e);
+  const int c = entry_class[e];
+  const int64_t j = qid[(int64_t)(tile / kQuad) * nclass + c];
+  qent[4 * j + (tile % kQuad)] = e;
+  qcls[j] = c;  // the entries of one quad entry all write the same class
+}
+
+__global__ void k_quad_ptr(const int64_t* __restrict__ qid, int nquad, int nclass, int64_t total,
+                           int32_t* __restrict__ qptr) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q > nquad) return;
+  qptr[q] = (int32_t)(q < nquad ? qid[(int64_t)q * nclass] : total);
+}
+
+}  // namespace
+
+void build_m2l_quad_chunks(fmm_tree* t, int per, const std::vector<int32_t>& qptr);
+
 // Quad plan: the class lists of tiles 4q .. 4q + 3 (each sorted by class)
 // merged into quad entries, cut into chunks of at most `per` quad entries.
 void build_m2l_quads(fmm_tree* t, int per, const std::vector<int32_t>& eptr) {
   Arena& a = t->arena;
   cudaStream_t s = t->stream;
+  const int nquad = (t->ntile + kQuad - 1) / kQuad;
+  const int64_t nk = (int64_t)nquad * t->nclass;
+  std::vector<int32_t> qptr(nquad + 1, 0);
+  if (nk > 0 && nk <= (1ll << 22) && t->nentry > 0) {
+    int64_t* qid = alloc_n<int64_t>(a, nk);
+    GB_CK(cudaMemsetAsync(qid, 0, sizeof(int64_t) * nk, s));
+    const unsigned nb = (unsigned)((t->nentry + 255) / 256);
+    k_quad_mark<<<nb, 256, 0, s>>>(t->tile_eptr, t->ntile, t->entry_class, (int)t->nentry, t->nclass, qid);
+    GB_LAUNCH("k_quad_mark");
+    const int64_t nq = scan_exclusive_i64_total(a, qid, nk, s);
+    t->quad_class = alloc_n<int32_t>(a, nq);
+    t->quad_entry = alloc_n<int4>(a, nq);
+    GB_CK(cudaMemsetAsync(t->quad_entry, 0xff, sizeof(int4) * nq, s));
+    k_quad_fill<<<nb, 256, 0, s>>>(t->tile_eptr, t->ntile, t->entry_class, (int)t->nentry, t->nclass, qid,
+                                   t->quad_class, reinterpret_cast<int32_t*>(t->quad_entry));
+    GB_LAUNCH("k_quad_fill");
+    int32_t* d_qptr = alloc_n<int32_t>(a, nquad + 1);
+    k_quad_ptr<<<(unsigned)((nquad + 256) / 256), 256, 0, s>>>(qid, nquad, t->nclass, nq, d_qptr);
+    GB_LAUNCH("k_quad_ptr");
+    GB_CK(cudaMemcpyAsync(qptr.data(), d_qptr, sizeof(int32_t) * (nquad + 1), cudaMemcpyDeviceToHost, s));
+    GB_CK(cudaStreamSynchronize(s));
+    a.release(qid);
+    a.release(d_qptr);
+    build_m2l_quad_chunks(t, per, qptr);
+    return;
+  }
   std::vector<int32_t> ecls(t->nentry);
   if (t->nentry)
     GB_CK(cudaMemcpyAsync(ecls.data(), t->entry_class, sizeof(int32_t) * t->nentry, cudaMemcpyDeviceToHost, s));
   GB_CK(cudaStreamSynchronize(s));
-  const int nquad = (t->ntile + kQuad - 1) / kQuad;
-  std::vector<int32_t> qcls, qptr(nquad + 1, 0);
+  std::vector<int32_t> qcls;
   std::vector<int4> qent;
   qcls.reserve(t->nentry);
   qent.reserve(t->nentry);
@@ -760,6 +831,22 @@ void build_m2l_quads(fmm_tree* t, int per, const std::vector<int32_t>& eptr) {
     }
     qptr[q + 1] = (int32_t)qcls.size();
   }
+  t->quad_class = alloc_n<int32_t>(a, qcls.size());
+  t->quad_entry = alloc_n<int4>(a, qent.size());
+  if (!qcls.empty()) {
+    GB_CK(cudaMemcpyAsync(t->quad_class, qcls.data(), sizeof(int32_t) * qcls.size(), cudaMemcpyHostToDevice, s));
+    GB_CK(cudaMemcpyAsync(t->quad_entry, qent.data(), sizeof(int4) * qent.size(), cudaMemcpyHostToDevice, s));
+  }
+  build_m2l_quad_chunks(t, per, qptr);
+}
+
+// Chunks of at most `per` quad entries of every quad, launched chunk j of
+// every quad before chunk j + 1 of any (operators shared in L2), and the
+// partial buffer.
+void build_m2l_quad_chunks(fmm_tree* t, int per, const std::vector<int32_t>& qptr) {
+  Arena& a = t->arena;
+  cudaStream_t s = t->stream;
+  const int nquad = (int)qptr.size() - 1;
   std::vector<int32_t> cptr(nquad + 1, 0);
   int maxc = 0;
   for (int q = 0; q < nquad; ++q) {
@@ -767,7 +854,6 @@ void build_m2l_quads(fmm_tree* t, int per, const std::vector<int32_t>& eptr) {
     cptr[q + 1] = cptr[q] + nc;
     maxc = std::max(maxc, nc);
   }
-  // chunk j of every quad before chunk j + 1 of any (operators shared in L2)
   std::vector<int4> ch;
   ch.reserve(cptr[nquad]);
   for (int j = 0; j < maxc; ++j)
@@ -779,14 +865,8 @@ void build_m2l_quads(fmm_tree* t, int per, const std::vector<int32_t>& eptr) {
   t->nchunk = (int)ch.size();
   t->m2l_chunks = alloc_n<int4>(a, ch.size());
   t->tile_cptr = alloc_n<int32_t>(a, cptr.size());
-  t->quad_class = alloc_n<int32_t>(a, qcls.size());
-  t->quad_entry = alloc_n<int4>(a, qent.size());
   GB_CK(cudaMemcpyAsync(t->m2l_chunks, ch.data(), sizeof(int4) * ch.size(), cudaMemcpyHostToDevice, s));
   GB_CK(cudaMemcpyAsync(t->tile_cptr, cptr.data(), sizeof(int32_t) * cptr.size(), cudaMemcpyHostToDevice, s));
-  if (!qcls.empty()) {
-    GB_CK(cudaMemcpyAsync(t->quad_class, qcls.data(), sizeof(int32_t) * qcls.size(), cudaMemcpyHostToDevice, s));
-    GB_CK(cudaMemcpyAsync(t->quad_entry, qent.data(), sizeof(int4) * qent.size(), cudaMemcpyHostToDevice, s));
-  }
   t->m2l_part = alloc_n<float>(a, (size_t)t->nchunk * kQuad * kTile * t->Kp);
   GB_CK(cudaStreamSynchronize(s));
 }
