@@ -39,6 +39,10 @@ if ROOT not in sys.path:
 METRIC = "FMM particles/sec (pot+force) at N=1M, rel-L2 err vs FP64 direct; P2P % FP32 peak"
 UNIT = "particles/s"
 L2_FLUSH_BYTES = 512 << 20  # > 129 MB L2
+# DRAM bytes (read + write) per launch of the dominant kernel from one ncu
+# capture (profiles/k_m2l_tc4_cube1m_p10_dram.md): workload, N, kernel.
+# Entries are dropped when the kernel changes.
+DRAM_TRAFFIC = {("cube1m_p10", 1048576, "k_m2l_tc4"): 442_070_000 + 581_920_000}
 CPU_SAMPLE_N = 65536
 
 
@@ -246,8 +250,10 @@ def run_gpu(args):
     # the dominant kernel by its time alone (in the timed steps P2P's span
     # stretches under M2L, which it runs beside)
     if iso["ms"]["m2l"] >= iso["ms"]["p2p"]:
-        if stats["m2l_engine"] == 1:
-            dom = {"kernel": "k_m2l_tc (+k_m2l_reduce)", "bound": "tensor", "achieved": m2l_tf, "ms": m2l_avg,
+        if stats["m2l_engine"] in (1, 2):
+            kname = "k_m2l_tc4" if stats["m2l_engine"] == 2 else "k_m2l_tc"
+            dom = {"kernel": f"{kname} (+k_split_tf32, reduce)", "bound": "tensor", "achieved": m2l_tf,
+                   "ms": m2l_avg, "traffic": DRAM_TRAFFIC.get((args.workload, N, kname)),
                    "peak": tf32_peak_tflops,
                    "peak_source": "measured bf16 dense burst (MEASURED_PEAKS.json) x 1.1/2.25 (nominal tf32/bf16)"}
         else:
@@ -259,12 +265,12 @@ def run_gpu(args):
                "peak_source": "FP32 spec formula SMs x 128 lanes x 2 x median SM clock under load"}
     roofline = {"bound": dom["bound"], "kernel": dom["kernel"], "achieved": round(dom["achieved"], 3),
                 "peak": round(dom["peak"], 3), "unit": "TFLOP/s",
-                "frac": round(dom["achieved"] / dom["peak"], 4), "traffic": None,
+                "frac": round(dom["achieved"] / dom["peak"], 4), "traffic": dom.get("traffic"),
                 "peak_source": dom["peak_source"], "avg_launch_ms": round(dom["ms"], 4),
                 "work": "algorithmic: 2 K^2 flops per M2L pair (K = p^2), 20 flops per P2P body pair"}
     slots = stats["n_m2l_slots"]
     Kp = (K + 15) // 16 * 16
-    m2l_exec_flops = 3 * 2.0 * slots * Kp * Kp if stats["m2l_engine"] == 1 else 2.0 * slots * Kp * Kp
+    m2l_exec_flops = 3 * 2.0 * slots * Kp * Kp if stats["m2l_engine"] in (1, 2) else 2.0 * slots * Kp * Kp
 
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,

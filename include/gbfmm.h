@@ -108,7 +108,8 @@ typedef struct {
   int32_t p, K, ncrit, precision_bits;
   double theta;
   uint32_t flags;
-  int32_t m2l_engine;        /* 0 CUDA cores, 1 tensor cores (tcgen05, 3xTF32) */
+  int32_t m2l_engine;        /* 0 CUDA cores; tensor cores (tcgen05, 3xTF32): 1 one tile
+                                per CTA, 2 four tiles per CTA sharing each operator */
   int64_t workspace_bytes;   /* device bytes held by the tree */
   int32_t evaluations;       /* fmm_evaluate calls on this tree */
   int32_t device_errors;     /* nonzero if a kernel's bounded wait gave up (the

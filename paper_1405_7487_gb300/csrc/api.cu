@@ -340,7 +340,7 @@ int fmm_get_stats(const fmm_tree* tc, fmm_stats* o) {
   o->precision_bits = t->precision;
   o->theta = t->theta;
   o->flags = t->flags;
-  o->m2l_engine = t->m2l_engine;
+  o->m2l_engine = t->m2l_engine == 1 && t->m2l_quad ? 2 : t->m2l_engine;
   o->workspace_bytes = (int64_t)t->arena.bytes;
   o->evaluations = t->evaluations;
   if (t->dev_err) {

@@ -577,22 +577,32 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
 }
 
 // L rows of one tile = compensated (Kahan) sum of the partials of its
-// quad's chunks, in chunk order.  Thread per (coefficient, row).
+// quad's chunks, in chunk order.  Thread per (coefficient, row); the
+// partials are loaded eight chunks at a time so that the loads overlap.
 __global__ void k_m2l_reduce4(const int32_t* __restrict__ tile_tgt, const int32_t* __restrict__ quad_cptr,
                               const float* __restrict__ part, int K, int Kp, float* __restrict__ L) {
   const int tile = blockIdx.x;
   const int q = tile / kQuad, lq = tile % kQuad;
   const int c0 = quad_cptr[q], c1 = quad_cptr[q + 1];
+  const int64_t cstride = (int64_t)kQuad * Kp * kTile;  // floats between chunks
   for (int w = threadIdx.x; w < kTile * K; w += blockDim.x) {
     const int c = w / kTile, r = w % kTile;
     const int tgt = tile_tgt[(int64_t)tile * kTile + r];
     if (tgt < 0) continue;
+    const float* pp = part + ((int64_t)lq * Kp + c) * kTile + r;
     float sum = 0.f, comp = 0.f;
-    for (int chk = c0; chk < c1; ++chk) {
-      const float y = __ldcs(part + (((int64_t)chk * kQuad + lq) * Kp + c) * kTile + r) - comp;
-      const float tt = sum + y;
-      comp = (tt - sum) - y;
-      sum = tt;
+    for (int b = c0; b < c1; b += 8) {
+      float v[8];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) v[k] = b + k < c1 ? __ldcs(pp + (int64_t)(b + k) * cstride) : 0.f;
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        if (b + k >= c1) break;
+        const float y = v[k] - comp;
+        const float tt = sum + y;
+        comp = (tt - sum) - y;
+        sum = tt;
+      }
     }
     L[(int64_t)tgt * Kp + c] = sum;
   }
@@ -667,7 +677,7 @@ void launch_m2l_tcgen05(fmm_tree* t, cudaStream_t s) {
                                                   t->quad_entry, t->entry_src, t->M_lo + n, t->M_lo, Kp, na,
                                                   t->m2l_part, t->dev_err);
     GB_LAUNCH("k_m2l_tc4");
-    k_m2l_reduce4<<<t->ntile, 256, 0, s>>>(t->tile_tgt, t->tile_cptr, t->m2l_part, t->K, Kp, (float*)t->L);
+    k_m2l_reduce4<<<t->ntile, 512, 0, s>>>(t->tile_tgt, t->tile_cptr, t->m2l_part, t->K, Kp, (float*)t->L);
     GB_LAUNCH("k_m2l_reduce4");
     return;
   }
