@@ -79,6 +79,8 @@ WORKLOADS = {
     "plummer1m_p8": dict(dist="plummer", n=1 << 20, seed=3, p=8, theta=0.5, ncrit=32),
     "cube256k_p8_grad": dict(dist="cube", n=1 << 18, seed=4, p=8, theta=0.4, ncrit=64, wseed=40),
     "cube16m": dict(dist="cube", n=1 << 24, seed=5, p=(4, 8, 12, 16), theta=0.4, ncrit=64),
+    # Table 1 case 2: bodies on a sphere surface, P = 10, theta = 0.4, N_crit = 512
+    "sphere1m_p10": dict(dist="sphere", n=1 << 20, seed=6, p=10, theta=0.4, ncrit=512),
 }
 
 

@@ -144,7 +144,7 @@ def test_force_optional(fmm):
     assert torch.equal(pot, pot2)
 
 
-@pytest.mark.parametrize("wl", ["cube1m_p10", "plummer1m_p8"])
+@pytest.mark.parametrize("wl", ["cube1m_p10", "plummer1m_p8", "sphere1m_p10"])
 def test_full_size_sampled_parity(fmm, orc, wl):
     """The benchmark workloads at full size: 4096 sampled targets against the
     oracle (same tree) and the error against the double direct sum."""
