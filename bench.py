@@ -165,8 +165,10 @@ def run_gpu(args):
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream(dev)
 
+    extra = F.FMM_FLAG_MUTUAL_P2P if args.p2p == "mutual" else 0
+
     def step(flags=F.FMM_FLAG_TIMING):
-        T = F.Tree(x, p, theta, ncrit, flags)
+        T = F.Tree(x, p, theta, ncrit, flags | extra)
         pot, force = T.evaluate()
         dq, dx = T.backward(w)
         st = T.stats()
@@ -219,12 +221,12 @@ def run_gpu(args):
     # end to end through host buffers (pinned), copies inside the timed region
     xh = torch.from_numpy(x_h).pin_memory().numpy()
     wh = torch.from_numpy(w_h).pin_memory().numpy()
-    F.solve_host(xh, wh, p, theta, ncrit)
+    F.solve_host(xh, wh, p, theta, ncrit, flags=extra)
     if world > 1:
         dist.barrier()
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        F.solve_host(xh, wh, p, theta, ncrit)
+        F.solve_host(xh, wh, p, theta, ncrit, flags=extra)
     e2e_s = reduce_max(time.perf_counter() - t0, dev)
     e2e = {"value": aggregate(N, args.steps, world, e2e_s), "unit": UNIT,
            "h2d_bytes_per_step": int(x_h.nbytes + w_h.nbytes),
@@ -278,7 +280,8 @@ def run_gpu(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": args.workload, "distribution": spec["dist"], "N": N, "p": p, "theta": theta,
                    "ncrit": ncrit, "step": "fmm_build + fmm_evaluate (pot, force) + fmm_backward",
-                   "l2": "flushed between timed steps (512 MiB write)", "parallelism": f"replicas x{world}"},
+                   "l2": "flushed between timed steps (512 MiB write)", "parallelism": f"replicas x{world}",
+                   **({"p2p": "mutual"} if args.p2p == "mutual" else {})},
         "e2e": e2e, "gpu_launches": int(launches), "roofline": roofline,
         "p2p_frac_fp32_peak": round(p2p_tf_iso / fp32_peak_tflops, 4),
         # P2P span in the timed steps, where it shares the GPU with M2L
@@ -359,6 +362,8 @@ def main():
     ap.add_argument("--workload", default="cube1m_p10")
     ap.add_argument("--n", type=int, default=None, help="bodies (default: the workload's size)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--p2p", default="one-sided", choices=["one-sided", "mutual"],
+                    help="near field: one block per target leaf, or mutual interaction")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

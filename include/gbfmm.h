@@ -67,9 +67,12 @@ enum {
   FMM_FLAG_SORTED_PLAN = 1u << 3,   /* number the M2L classes and (tile, class) entries by
                                        sorting the pairs, also where the dense key tables
                                        would be used; the plan is identical either way */
-  FMM_FLAG_SERIAL_PHASES = 1u << 4  /* run the near field on the caller's stream after the
+  FMM_FLAG_SERIAL_PHASES = 1u << 4, /* run the near field on the caller's stream after the
                                        far field instead of concurrently on a second stream
                                        (with FMM_FLAG_TIMING: each phase timed alone) */
+  FMM_FLAG_MUTUAL_P2P = 1u << 5     /* near field by mutual interaction: each unordered leaf
+                                       pair visited once, both leaves updated (floating-point
+                                       atomics: results are not bit-reproducible) */
 };
 
 /* Optional stream-ordered allocator.  NULL selects the library's memory pool

@@ -109,6 +109,8 @@ struct fmm_tree {
   int32_t *p2p_tgt = nullptr, *p2p_src = nullptr, *m2l_tgt = nullptr, *m2l_src = nullptr;
   int32_t* p2p_rptr = nullptr;  // per leaf: ranges [rptr[l], rptr[l+1])
   int2* p2p_ranges = nullptr;   // (begin, end) sorted body ranges, self excluded
+  int64_t n_p2p_upairs = 0;     // mutual interaction: unordered leaf pairs (cells a < b)
+  int2* p2p_upairs = nullptr;
 
   // M2L engine: targets tiled kTile at a time, per tile one entry per
   // translation operator with the source of each tile row (or -1).

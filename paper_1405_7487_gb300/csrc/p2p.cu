@@ -462,11 +462,114 @@ __global__ void __launch_bounds__(kThreads) k_p2p_f2(const float4* __restrict__ 
   }
 }
 
+// ---------------------------------------------------------------------------
+// Mutual interaction (FMM_FLAG_MUTUAL_P2P): a block per unordered leaf pair
+// (A, B), A < B, computes each body pair once and updates both sides: the
+// target side in registers (thread per body of A), the source side in
+// shared memory, where thread i at step k takes body (i + k) mod n of the
+// staged tile of B so that a warp's updates hit distinct addresses.  Every
+// result reaches `near` through atomic additions (near starts at zero), so
+// the order of the additions, and the last bits, vary from run to run.
+// Blocks past the pairs take one leaf each: its self interaction, one-sided
+// and masked.
+template <class R>
+__device__ __forceinline__ void atomic_add4(typename Vec4<R>::type* p, R a, R b, R c, R d) {
+  R* q = reinterpret_cast<R*>(p);
+  atomicAdd(q + 0, a);
+  atomicAdd(q + 1, b);
+  atomicAdd(q + 2, c);
+  atomicAdd(q + 3, d);
+}
+
+template <class R, class R4>
+__global__ void __launch_bounds__(kThreads) k_p2p_mutual(const R4* __restrict__ bodies,
+                                                         const int2* __restrict__ upairs, int64_t nup,
+                                                         const int32_t* __restrict__ leaves,
+                                                         const int32_t* __restrict__ bbeg,
+                                                         const int32_t* __restrict__ bend, R4* __restrict__ near,
+                                                         Lim lim) {
+  __shared__ R4 tile[kSrcTile];
+  __shared__ R acc[4][kSrcTile];
+  const int tid = threadIdx.x;
+  const int64_t b = blockIdx.x;
+  if (b >= nup) {
+    // self interaction of one leaf
+    const int cell = GB_LD(leaves, (int)(b - nup), lim.nleaf, 111);
+    const int s = GB_LD(bbeg, cell, lim.ncell, 112), e = GB_LD(bend, cell, lim.ncell, 113);
+    for (int t0 = s; t0 < e; t0 += kThreads) {
+      const int i = t0 + tid;
+      Acc<R> a{0, 0, 0, 0};
+      const bool act = i < e;
+      const R4 bi = act ? GB_LD(bodies, i, lim.N, 114) : R4{};
+      for (int c0 = s; c0 < e; c0 += kSrcTile) {
+        const int cnt = min(kSrcTile, e - c0);
+        __syncthreads();
+        for (int k = tid; k < cnt; k += kThreads) tile[k] = GB_LD(bodies, c0 + k, lim.N, 115);
+        __syncthreads();
+        if (act)
+          for (int k = 0; k < cnt; ++k) pair<R, R4, true>(tile[k], bi.x, bi.y, bi.z, a);
+      }
+      if (act) atomic_add4<R>(near + i, a.p, a.x, a.y, a.z);
+    }
+    return;
+  }
+  const int2 up = GB_LD(upairs, b, nup, 116);
+  const int sA = GB_LD(bbeg, up.x, lim.ncell, 117), eA = GB_LD(bend, up.x, lim.ncell, 118);
+  const int sB = GB_LD(bbeg, up.y, lim.ncell, 119), eB = GB_LD(bend, up.y, lim.ncell, 120);
+  for (int b0 = sB; b0 < eB; b0 += kSrcTile) {
+    const int nb = min(kSrcTile, eB - b0);
+    __syncthreads();
+    for (int k = tid; k < nb; k += kThreads) {
+      tile[k] = GB_LD(bodies, b0 + k, lim.N, 121);
+      acc[0][k] = acc[1][k] = acc[2][k] = acc[3][k] = (R)0;
+    }
+    __syncthreads();
+    for (int a0 = sA; a0 < eA; a0 += kThreads) {
+      const int i = a0 + tid;
+      if (i < eA) {
+        const R4 bi = GB_LD(bodies, i, lim.N, 122);
+        R p = 0, ax = 0, ay = 0, az = 0;
+        int j = tid % nb;
+        for (int k = 0; k < nb; ++k) {
+          const R4 bj = tile[j];
+          const R dx = bj.x - bi.x, dy = bj.y - bi.y, dz = bj.z - bi.z;
+          const R r2 = dx * dx + dy * dy + dz * dz;
+          const R inv = rsqrt_fast(r2);  // bodies of two leaves never coincide
+          const R inv3 = inv * inv * inv;
+          p += bj.w * inv;
+          const R fj = bj.w * inv3;
+          ax += fj * dx;
+          ay += fj * dy;
+          az += fj * dz;
+          // reaction on body j: potential q_i / r, gradient q_i (x_i - x_j) / r^3
+          const R fi = bi.w * inv3;
+          atomicAdd(&acc[0][j], bi.w * inv);
+          atomicAdd(&acc[1][j], -fi * dx);
+          atomicAdd(&acc[2][j], -fi * dy);
+          atomicAdd(&acc[3][j], -fi * dz);
+          j = j + 1 == nb ? 0 : j + 1;
+        }
+        atomic_add4<R>(near + i, p, ax, ay, az);
+      }
+    }
+    __syncthreads();
+    for (int k = tid; k < nb; k += kThreads) atomic_add4<R>(near + b0 + k, acc[0][k], acc[1][k], acc[2][k], acc[3][k]);
+  }
+}
+
 }  // namespace
 
 template <class R>
 void launch_p2p(fmm_tree* t, cudaStream_t s) {
   using R4 = typename Vec4<R>::type;
+  if (t->flags & FMM_FLAG_MUTUAL_P2P) {
+    GB_CK(cudaMemsetAsync(t->near, 0, sizeof(R4) * (size_t)t->N, s));
+    const int64_t nblk = t->n_p2p_upairs + t->nleaf;
+    k_p2p_mutual<R, R4><<<(unsigned)nblk, kThreads, 0, s>>>((const R4*)t->work, t->p2p_upairs, t->n_p2p_upairs,
+                                                            t->leaves, t->c.bbeg, t->c.bend, (R4*)t->near, t->lim);
+    GB_LAUNCH("k_p2p_mutual");
+    return;
+  }
   if (std::is_same<R, float>::value) {
     k_p2p_f2<<<t->nleaf, kThreads, 0, s>>>((const float4*)t->work, t->leaves, t->c.bbeg, t->c.bend, t->p2p_rptr,
                                            t->p2p_ranges, (float4*)t->near, t->lim);

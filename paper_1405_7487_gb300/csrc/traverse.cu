@@ -220,6 +220,20 @@ __global__ void k_i64_to_i32(const int64_t* __restrict__ a, int64_t n, int32_t* 
   if (i < n) b[i] = (int32_t)a[i];
 }
 
+// Mutual interaction: the unordered leaf pairs (source cell < target cell)
+// of the symmetric P2P list.
+__global__ void k_upair_flags(const int32_t* __restrict__ tgt, const int32_t* __restrict__ src, int64_t n,
+                              int64_t* __restrict__ f) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) f[i] = src[i] < tgt[i] ? 1 : 0;
+}
+
+__global__ void k_upair_write(const int32_t* __restrict__ tgt, const int32_t* __restrict__ src, int64_t n,
+                              const int64_t* __restrict__ off, int2* __restrict__ up) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n && src[i] < tgt[i]) up[off[i]] = make_int2(src[i], tgt[i]);
+}
+
 }  // namespace
 
 // Smallest b with 2^b > v.
@@ -353,6 +367,16 @@ void build_lists(fmm_tree* t) {
   a.release(rval);
   a.release(eptr);
   a.release(rcount);
+  if (t->flags & FMM_FLAG_MUTUAL_P2P) {
+    int64_t* off = alloc_n<int64_t>(a, np);
+    k_upair_flags<<<blocks(np), kThreads, 0, s>>>(t->p2p_tgt, t->p2p_src, np, off);
+    GB_LAUNCH("k_upair_flags");
+    t->n_p2p_upairs = scan_exclusive_i64_total(a, off, np, s);
+    t->p2p_upairs = alloc_n<int2>(a, t->n_p2p_upairs);
+    k_upair_write<<<blocks(np), kThreads, 0, s>>>(t->p2p_tgt, t->p2p_src, np, off, t->p2p_upairs);
+    GB_LAUNCH("k_upair_write");
+    a.release(off);
+  }
 }
 
 }  // namespace gbfmm

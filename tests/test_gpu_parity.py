@@ -121,6 +121,29 @@ def test_forward_matches_oracle(fmm, orc, name):
     assert rel(f, -go) < TOL_F
 
 
+@pytest.mark.parametrize("name,f64", [("cube65k_p10", False), ("plummer60k_p8", False), ("sphere40k_p6", False),
+                                      ("cube4k_p4", True)])
+def test_mutual_p2p_matches_oracle(fmm, orc, name, f64):
+    """Mutual interaction (each unordered leaf pair once, both sides updated
+    through atomics) gives the oracle's result, forward and backward."""
+    gen, p, theta, ncrit = CASES[name]
+    x = gen()
+    T = gpu_tree(fmm, x, p, theta, ncrit, fmm.FMM_FLAG_MUTUAL_P2P, f64=f64)
+    ph, f = evaluate(T)
+    O = orc.OracleTree(x, p, theta, ncrit)
+    po, go = O.evaluate()
+    tp, tf = (1e-11, 1e-10) if f64 else (TOL_PHI, TOL_F)
+    assert rel(ph, po) < tp
+    assert rel(f, -go) < tf
+    w = W.weights(x.shape[0], 31)
+    wt = torch.from_numpy(w.astype(np.float64 if f64 else np.float32)).cuda()
+    dq, dx = T.backward(wt)
+    torch.cuda.synchronize()
+    dqo, dxo = O.backward(w.astype(np.float64))
+    assert rel(dq.double().cpu().numpy(), dqo) < tp
+    assert rel(dx.double().cpu().numpy(), dxo) < tf
+
+
 def test_charges_override_and_repeat(fmm, orc):
     x = W.cube(20000, 19)
     q2 = W.weights(20000, 20)
