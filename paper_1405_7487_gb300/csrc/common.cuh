@@ -53,6 +53,8 @@ T* alloc_n(Arena& a, size_t n) {
 // Exclusive scan of n int64 values in place; returns the total (synchronises
 // the stream to read it back when `total` is requested).
 void scan_exclusive_i64(Arena& a, int64_t* d, int64_t n, cudaStream_t s);
+// the total is left in device memory (no host synchronisation)
+void scan_exclusive_i64_dev(Arena& a, int64_t* d, int64_t n, int64_t* total_dev, cudaStream_t s);
 int64_t scan_exclusive_i64_total(Arena& a, int64_t* d, int64_t n, cudaStream_t s);
 
 // LSD radix sort of (key, value) pairs on bits [0, bits) of the key; stable.

@@ -94,12 +94,11 @@ struct Coef {
   int kind;
   int eA, eB;  // M2L: R_A / r = 2^eA and R_B / r = 2^eB
   const cd* X;
+  const double* scale;  // M2L: scale[a * kMaxP + c] = (-1)^a 2^(eB (a + 1) + eA c)
   __device__ cd operator()(int a, int b, int c, int d) const {
     if (kind == kM2L) {
       // out (k = a, l = b), in (n = c, m = d)
-      cd t = hget(X, a + c, d + b);
-      double f = ldexp((a & 1) ? -1.0 : 1.0, eB * (a + 1) + eA * c);
-      return cscale(t, f);
+      return cscale(hget(X, a + c, d + b), scale[a * kMaxP + c]);
     }
     if (kind == kM2M) {
       // out (n = a, m = b), in (k = c, l = d)
@@ -130,16 +129,23 @@ __global__ void k_build_ops(int kind, int p, int Kp, const double* __restrict__ 
                             R* __restrict__ ops, float* __restrict__ ops_lo, bool out_major,
                             int* __restrict__ range_bad) {
   extern __shared__ cd X[];
+  __shared__ double scale[kMaxP * kMaxP];
   const int op = blockIdx.x;
   if (op >= nops) return;
   const double* g = geom + 5 * (int64_t)op;
   const int P = kind == kM2L ? 2 * p - 1 : p;
+  const int eA = (int)g[3], eB = (int)g[4];
   if (threadIdx.x == 0) {
     if (kind == kM2L) irregular_tri(g[0], g[1], g[2], P, X);
     else regular_tri(g[0], g[1], g[2], P, X);
   }
+  // the M2L scale factors, one exponent per (output degree, input degree)
+  for (int w = threadIdx.x; w < kMaxP * kMaxP; w += blockDim.x) {
+    const int a = w / kMaxP, c = w % kMaxP;
+    scale[w] = ldexp((a & 1) ? -1.0 : 1.0, eB * (a + 1) + eA * c);
+  }
   __syncthreads();
-  Coef C{kind, (int)g[3], (int)g[4], X};
+  Coef C{kind, eA, eB, X, scale};
   R* o = ops + (int64_t)op * Kp * Kp;
   float* olo = ops_lo ? ops_lo + (int64_t)op * Kp * Kp : nullptr;
   // zero (padding rows/columns stay zero)
@@ -473,17 +479,23 @@ void build_m2l_plan(fmm_tree* t) {
   k_target_flags<<<blocks(nm), kThreads, 0, s>>>(t->m2l_tgt, nm, has);
   GB_LAUNCH("k_target_flags");
   uint64_t* tkey = alloc_n<uint64_t>(a, t->ncell);
-  unsigned long long* d_cnt = alloc_n<unsigned long long>(a, 1);
+  unsigned long long* d_cnt = alloc_n<unsigned long long>(a, 2);  // target count, largest offset
   GB_CK(cudaMemsetAsync(d_cnt, 0, sizeof(unsigned long long), s));
   // 2^cbits > ncell, so a real key never equals the all-ones key of a non-target
   int cbits = 1;
   while ((1ll << cbits) <= (int64_t)t->ncell) ++cbits;
   k_target_keys<<<blocks(t->ncell), kThreads, 0, s>>>(has, cv, t->ncell, cbits, tkey, d_cnt);
   GB_LAUNCH("k_target_keys");
+  // the largest offset of the translation classes, read back together with
+  // the target count (one host synchronisation)
+  GB_CK(cudaMemsetAsync(d_cnt + 1, 0, sizeof(unsigned long long), s));
+  k_class_maxd<<<blocks(nm), kThreads, 0, s>>>(t->m2l_tgt, t->m2l_src, nm, cv, d_cnt + 1);
+  GB_LAUNCH("k_class_maxd");
   radix_sort_keys(a, tkey, t->ncell, cbits + 3, s);
-  unsigned long long ntgt = 0;
-  GB_CK(cudaMemcpyAsync(&ntgt, d_cnt, sizeof(ntgt), cudaMemcpyDeviceToHost, s));
+  unsigned long long hc[2] = {0, 0};
+  GB_CK(cudaMemcpyAsync(hc, d_cnt, sizeof(hc), cudaMemcpyDeviceToHost, s));
   GB_CK(cudaStreamSynchronize(s));
+  const unsigned long long ntgt = hc[0], maxd = hc[1];
   t->ntile = (int)((ntgt + kTile - 1) / kTile);
   const int64_t padded = (int64_t)t->ntile * kTile;
   t->tile_tgt = alloc_n<int32_t>(a, padded);
@@ -495,14 +507,6 @@ void build_m2l_plan(fmm_tree* t) {
   a.release(d_cnt);
 
   // --- translation classes
-  unsigned long long* d_maxd = alloc_n<unsigned long long>(a, 1);
-  GB_CK(cudaMemsetAsync(d_maxd, 0, sizeof(unsigned long long), s));
-  k_class_maxd<<<blocks(nm), kThreads, 0, s>>>(t->m2l_tgt, t->m2l_src, nm, cv, d_maxd);
-  GB_LAUNCH("k_class_maxd");
-  unsigned long long maxd = 0;
-  GB_CK(cudaMemcpyAsync(&maxd, d_maxd, sizeof(maxd), cudaMemcpyDeviceToHost, s));
-  GB_CK(cudaStreamSynchronize(s));
-  a.release(d_maxd);
   int b = 1;
   while ((1ull << b) <= 2 * maxd) ++b;
   // dense numbering while the key table stays small (2^22 keys), else sort

@@ -194,6 +194,10 @@ void scan_exclusive_i64(Arena& a, int64_t* d, int64_t n, cudaStream_t s) {
   scan_rec(a, d, n, nullptr, s);
 }
 
+void scan_exclusive_i64_dev(Arena& a, int64_t* d, int64_t n, int64_t* total_dev, cudaStream_t s) {
+  scan_rec(a, d, n, total_dev, s);
+}
+
 int64_t scan_exclusive_i64_total(Arena& a, int64_t* d, int64_t n, cudaStream_t s) {
   int64_t* tot = alloc_n<int64_t>(a, 1);
   scan_rec(a, d, n, tot, s);

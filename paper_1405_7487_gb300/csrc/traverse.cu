@@ -270,6 +270,7 @@ void build_lists(fmm_tree* t) {
   int64_t nm = 0, np = 0;
 
   int64_t nf = 1;
+  int64_t* d_seg = alloc_n<int64_t>(a, 3);
   int2* fr = alloc_n<int2>(a, 1);
   {
     int2 h = make_int2(0, 0);
@@ -279,13 +280,16 @@ void build_lists(fmm_tree* t) {
     int64_t* cnt = alloc_n<int64_t>(a, 3 * nf);
     k_trav_count<<<blocks(nf), kThreads, 0, s>>>(fr, nf, cv, theta2, circ, cnt);
     GB_LAUNCH("k_trav_count");
-    // one scan over the three count segments; segment totals read back
+    // one scan over the three count segments; the segment starts and the
+    // total are read back together (one host synchronisation per level)
     int64_t* scanned = cnt;
-    const int64_t total = scan_exclusive_i64_total(a, scanned, 3 * nf, s);
-    int64_t seg[2];
-    GB_CK(cudaMemcpyAsync(&seg[0], scanned + nf, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-    GB_CK(cudaMemcpyAsync(&seg[1], scanned + 2 * nf, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    scan_exclusive_i64_dev(a, scanned, 3 * nf, d_seg + 2, s);
+    GB_CK(cudaMemcpyAsync(&d_seg[0], scanned + nf, sizeof(int64_t), cudaMemcpyDeviceToDevice, s));
+    GB_CK(cudaMemcpyAsync(&d_seg[1], scanned + 2 * nf, sizeof(int64_t), cudaMemcpyDeviceToDevice, s));
+    int64_t seg[3];
+    GB_CK(cudaMemcpyAsync(seg, d_seg, sizeof(seg), cudaMemcpyDeviceToHost, s));
     GB_CK(cudaStreamSynchronize(s));
+    const int64_t total = seg[2];
     const int64_t n_next = seg[0], n_m = seg[1] - seg[0], n_p = total - seg[1];
     auto grow = [&](uint64_t*& buf, int64_t& cap, int64_t used, int64_t need) {
       if (used + need <= cap) return;
@@ -310,6 +314,7 @@ void build_lists(fmm_tree* t) {
     nf = n_next;
   }
   a.release(fr);
+  a.release(d_seg);
 
   // The pairs stay in traversal order (deterministic: every offset comes from
   // an exclusive scan); only the inspection call sorts a copy by (target,
