@@ -145,31 +145,27 @@ void run_pass(fmm_tree* t, cudaStream_t s, int mode, R* a, R* b) {
   const bool serial = (t->flags & FMM_FLAG_SERIAL_PHASES) != 0;
   // Concurrent mode: the far field runs on the library's highest-priority
   // stream and the near field on its lowest-priority stream, both forked
-  // from the caller's stream and joined back before L2P.  P2P is released
-  // when M2L is about to start: the M2L CTAs (one per SM, most of its shared
-  // memory) are dispatched first and P2P blocks fill the registers, shared
-  // memory and issue slots they leave free.  Serial mode runs every phase on
-  // the caller's stream, P2P first.
+  // from the caller's stream and joined back before L2P.  P2P fills the GPU
+  // during P2M and M2M; once M2L is launched its CTAs (one per SM, most of
+  // its shared memory) are dispatched first as P2P blocks retire, and P2P
+  // blocks fill the registers, shared memory and issue slots they leave
+  // free.  Serial mode runs every phase on the caller's stream, P2P first.
   cudaStream_t fs = serial ? s : t->far;
   cudaStream_t ps = serial ? s : t->side;
   PhaseTimer Ttot{t, s, timing}, T{t, fs, timing}, Tp{t, ps, timing};
   Ttot.begin(FMM_PH_EVAL_TOTAL);
   auto near_field = [&] {
-    if (!serial) {
-      GB_CK(cudaEventRecord(t->fork_near, fs));
-      GB_CK(cudaStreamWaitEvent(ps, t->fork_near, 0));
-    }
+    if (!serial) GB_CK(cudaStreamWaitEvent(ps, t->fork, 0));
     Tp.begin(FMM_PH_P2P);
     launch_p2p<R>(t, ps);
     Tp.end(FMM_PH_P2P);
     if (!serial) GB_CK(cudaEventRecord(t->join, ps));
   };
-  if (serial) {
-    near_field();
-  } else {
+  if (!serial) {
     GB_CK(cudaEventRecord(t->fork, s));
     GB_CK(cudaStreamWaitEvent(fs, t->fork, 0));
   }
+  near_field();
   // far field
   GB_CK(cudaMemsetAsync(t->L, 0, sizeof(R) * (size_t)t->ncell * t->Kp, fs));
   T.begin(FMM_PH_P2M);
@@ -181,10 +177,8 @@ void run_pass(fmm_tree* t, cudaStream_t s, int mode, R* a, R* b) {
   T.begin(FMM_PH_M2L);
   if (t->m2l_engine == 1) {
     launch_split_tf32(t, fs);
-    if (!serial) near_field();
     launch_m2l_tcgen05(t, fs);
   } else {
-    if (!serial) near_field();
     launch_m2l_cuda_core<R>(t, fs);
   }
   T.end(FMM_PH_M2L);
