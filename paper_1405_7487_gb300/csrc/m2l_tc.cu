@@ -356,7 +356,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
     k_m2l_tc4(const __grid_constant__ CUtensorMap tm_ops_hi, const __grid_constant__ CUtensorMap tm_ops_lo,
               const int4* __restrict__ chunks, const int32_t* __restrict__ quad_class,
               const int4* __restrict__ quad_entry, const int32_t* __restrict__ entry_src,
-              const float* __restrict__ Mhi, const float* __restrict__ Mlo, int Kp, int nastage,
+              const float* __restrict__ Mhi, const float* __restrict__ Mlo, int Kp, int Kin, int nastage,
               float* __restrict__ part, int* __restrict__ err) {
   extern __shared__ unsigned char smem_raw[];
   __shared__ uint64_t bar_bfull[2], bar_bempty[2], bar_afull[kMaxAStages], bar_aempty[kMaxAStages], bar_done;
@@ -372,7 +372,9 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int4 ch = chunks[blockIdx.x];
   const int j0 = ch.y, j1 = ch.z;
-  const int nkb = (Kp + kKB - 1) / kKB;
+  // the inputs span Kin = K rounded up to the 8-element k-step (columns
+  // K .. Kp of M and of the operators are zero); the outputs span Kp
+  const int nkb = (Kin + kKB - 1) / kKB;
 
   if (tid == 0) {
     abort_flag = 0;
@@ -450,7 +452,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
           tma_load_2d(sb + stageB, &tm_ops_lo, k0, cls * Kp, fb);
           tma_issued = bi + 1;
         }
-        const int nch = min(kKB, Kp - k0) / 4;  // 16-byte chunks in this k-block
+        const int nch = min(kKB, Kin - k0) / 4;  // 16-byte chunks in this k-block
 #pragma unroll
         for (int q = 0; q < kQuad; ++q) {
           if (ev[q] < 0) continue;
@@ -529,7 +531,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
           break;
         }
         const uint32_t sb = bbase + bs * 2 * stageB;
-        const int nks = min(kKB, Kp - kb * kKB) / 8;  // tf32 k-steps of 8 elements
+        const int nks = min(kKB, Kin - kb * kKB) / 8;  // tf32 k-steps of 8 elements
 #pragma unroll
         for (int q = 0; q < kQuad; ++q) {
           if (ev[q] < 0) continue;
@@ -674,7 +676,7 @@ void launch_m2l_tcgen05(fmm_tree* t, cudaStream_t s) {
     GB_CK(cudaFuncSetAttribute(k_m2l_tc4, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     const int64_t n = (int64_t)t->ncell * Kp;
     k_m2l_tc4<<<t->nchunk, kThreadsTC, smem, s>>>(t->m2l_ops_map[0], t->m2l_ops_map[1], t->m2l_chunks, t->quad_class,
-                                                  t->quad_entry, t->entry_src, t->M_lo + n, t->M_lo, Kp, na,
+                                                  t->quad_entry, t->entry_src, t->M_lo + n, t->M_lo, Kp, (t->K + 7) & ~7, na,
                                                   t->m2l_part, t->dev_err);
     GB_LAUNCH("k_m2l_tc4");
     k_m2l_reduce4<<<t->ntile, 512, 0, s>>>(t->tile_tgt, t->tile_cptr, t->m2l_part, t->K, Kp, (float*)t->L);
