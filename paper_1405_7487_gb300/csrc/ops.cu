@@ -384,7 +384,7 @@ __global__ void k_class_mark(const int32_t* __restrict__ tgt, const int32_t* __r
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= n) return;
   const uint64_t k = class_key(c, src[i], tgt[i], b, maxd);
-  if (mark[k] == 0) mark[k] = 1;
+  mark[k] = 1;  // plain store: no read of the table
 }
 
 // After the scan: class id of every pair.
@@ -417,7 +417,7 @@ __global__ void k_entry_mark(const int32_t* __restrict__ tgt, const int32_t* __r
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= n) return;
   const int64_t e = (int64_t)(rank_of[tgt[i]] / kTile) * nclass + class_of[i];
-  if (mark[e] == 0) mark[e] = 1;
+  mark[e] = 1;  // plain store: no read of the table
 }
 
 __global__ void k_entry_fill_dense(const int32_t* __restrict__ tgt, const int32_t* __restrict__ src,
