@@ -411,24 +411,39 @@ __global__ void k_class_desc_dense(const int64_t* __restrict__ excl, int64_t nke
   desc[4 * cid + 3] = (int32_t)((int64_t)((uint64_t)k & m) - maxd);
 }
 
-__global__ void k_entry_mark(const int32_t* __restrict__ tgt, const int32_t* __restrict__ class_of,
+// Class of pair i: from the per-pair array of the sorted numbering, or
+// looked up in the scanned dense key table.
+struct ClassOf {
+  const int32_t* class_of;  // sorted numbering, else null
+  const int64_t* key_excl;  // dense numbering: scanned key table
+  CellView c;
+  int b;
+  int64_t maxd;
+  __device__ __forceinline__ int operator()(int64_t i, int src, int tgt) const {
+    if (class_of) return class_of[i];
+    return (int)key_excl[class_key(c, src, tgt, b, maxd)];
+  }
+};
+
+__global__ void k_entry_mark(const int32_t* __restrict__ tgt, const int32_t* __restrict__ src, ClassOf cls,
                              const int32_t* __restrict__ rank_of, int64_t n, int nclass,
                              int64_t* __restrict__ mark) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= n) return;
-  const int64_t e = (int64_t)(rank_of[tgt[i]] / kTile) * nclass + class_of[i];
+  const int t = tgt[i];
+  const int64_t e = (int64_t)(rank_of[t] / kTile) * nclass + cls(i, src[i], t);
   mark[e] = 1;  // plain store: no read of the table
 }
 
-__global__ void k_entry_fill_dense(const int32_t* __restrict__ tgt, const int32_t* __restrict__ src,
-                                   const int32_t* __restrict__ class_of, const int32_t* __restrict__ rank_of,
-                                   int64_t n, int nclass, const int64_t* __restrict__ excl,
-                                   int32_t* __restrict__ entry_src) {
+__global__ void k_entry_fill_dense(const int32_t* __restrict__ tgt, const int32_t* __restrict__ src, ClassOf cls,
+                                   const int32_t* __restrict__ rank_of, int64_t n, int nclass,
+                                   const int64_t* __restrict__ excl, int32_t* __restrict__ entry_src) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= n) return;
-  const int r = rank_of[tgt[i]];
-  const int64_t e = excl[(int64_t)(r / kTile) * nclass + class_of[i]];
-  entry_src[e * kTile + (r % kTile)] = src[i];
+  const int t = tgt[i], sr = src[i];
+  const int r = rank_of[t];
+  const int64_t e = excl[(int64_t)(r / kTile) * nclass + cls(i, sr, t)];
+  entry_src[e * kTile + (r % kTile)] = sr;
 }
 
 // Entry classes and tile pointers from the scanned (tile, class) table.
@@ -514,22 +529,18 @@ void build_m2l_plan(fmm_tree* t) {
   const bool sorted_only = (t->flags & FMM_FLAG_SORTED_PLAN) != 0;
   const bool dense_cls = !sorted_only && b <= 19 && kbits <= kDenseBits;
   int32_t* class_of = nullptr;
+  int64_t* key_excl = nullptr;  // dense numbering: kept for the entry kernels
   if (dense_cls) {
     const int64_t nkey = 1ll << kbits;
-    int64_t* mark = alloc_n<int64_t>(a, nkey);
-    GB_CK(cudaMemsetAsync(mark, 0, sizeof(int64_t) * nkey, s));
-    k_class_mark<<<blocks(nm), kThreads, 0, s>>>(t->m2l_tgt, t->m2l_src, nm, cv, b, (int64_t)maxd, mark);
+    key_excl = alloc_n<int64_t>(a, nkey);
+    GB_CK(cudaMemsetAsync(key_excl, 0, sizeof(int64_t) * nkey, s));
+    k_class_mark<<<blocks(nm), kThreads, 0, s>>>(t->m2l_tgt, t->m2l_src, nm, cv, b, (int64_t)maxd, key_excl);
     GB_LAUNCH("k_class_mark");
-    const int64_t ncls = scan_exclusive_i64_total(a, mark, nkey, s);
+    const int64_t ncls = scan_exclusive_i64_total(a, key_excl, nkey, s);
     t->nclass = (int)ncls;
     t->class_desc = alloc_n<int32_t>(a, 4 * ncls);
-    class_of = alloc_n<int32_t>(a, nm);
-    k_class_lookup<<<blocks(nm), kThreads, 0, s>>>(t->m2l_tgt, t->m2l_src, nm, cv, b, (int64_t)maxd, mark,
-                                                   class_of);
-    GB_LAUNCH("k_class_lookup");
-    k_class_desc_dense<<<blocks(nkey), kThreads, 0, s>>>(mark, nkey, ncls, b, (int64_t)maxd, t->class_desc);
+    k_class_desc_dense<<<blocks(nkey), kThreads, 0, s>>>(key_excl, nkey, ncls, b, (int64_t)maxd, t->class_desc);
     GB_LAUNCH("k_class_desc_dense");
-    a.release(mark);
   } else {
     uint64_t* ckey = alloc_n<uint64_t>(a, nm);
     int32_t* cval = alloc_n<int32_t>(a, nm);
@@ -557,25 +568,35 @@ void build_m2l_plan(fmm_tree* t) {
     const int64_t nk = (int64_t)t->ntile * t->nclass;
     int64_t* mark = alloc_n<int64_t>(a, nk);
     GB_CK(cudaMemsetAsync(mark, 0, sizeof(int64_t) * nk, s));
-    k_entry_mark<<<blocks(nm), kThreads, 0, s>>>(t->m2l_tgt, class_of, rank_of, nm, t->nclass, mark);
+    const ClassOf cls{class_of, key_excl, cv, b, (int64_t)maxd};
+    k_entry_mark<<<blocks(nm), kThreads, 0, s>>>(t->m2l_tgt, t->m2l_src, cls, rank_of, nm, t->nclass, mark);
     GB_LAUNCH("k_entry_mark");
     const int64_t ne = scan_exclusive_i64_total(a, mark, nk, s);
     t->nentry = ne;
     t->entry_class = alloc_n<int32_t>(a, ne);
     t->entry_src = alloc_n<int32_t>(a, ne * kTile);
     GB_CK(cudaMemsetAsync(t->entry_src, 0xff, sizeof(int32_t) * ne * kTile, s));
-    k_entry_fill_dense<<<blocks(nm), kThreads, 0, s>>>(t->m2l_tgt, t->m2l_src, class_of, rank_of, nm, t->nclass,
-                                                       mark, t->entry_src);
+    k_entry_fill_dense<<<blocks(nm), kThreads, 0, s>>>(t->m2l_tgt, t->m2l_src, cls, rank_of, nm, t->nclass, mark,
+                                                       t->entry_src);
     GB_LAUNCH("k_entry_fill_dense");
     t->tile_eptr = alloc_n<int32_t>(a, t->ntile + 1);
     k_entry_table<<<blocks(nk + 1), kThreads, 0, s>>>(mark, t->ntile, t->nclass, ne, t->entry_class,
                                                       t->tile_eptr);
     GB_LAUNCH("k_entry_table");
     a.release(mark);
-    a.release(class_of);
+    if (class_of) a.release(class_of);
+    if (key_excl) a.release(key_excl);
     a.release(rank_of);
     return;
   }
+  if (!class_of) {
+    // dense class numbering, sorted entries: the per-pair classes
+    class_of = alloc_n<int32_t>(a, nm);
+    k_class_lookup<<<blocks(nm), kThreads, 0, s>>>(t->m2l_tgt, t->m2l_src, nm, cv, b, (int64_t)maxd, key_excl,
+                                                   class_of);
+    GB_LAUNCH("k_class_lookup");
+  }
+  if (key_excl) a.release(key_excl);
   uint64_t* ekey = alloc_n<uint64_t>(a, nm);
   int32_t* eval = alloc_n<int32_t>(a, nm);
   int cb = 1, tb = 1;
