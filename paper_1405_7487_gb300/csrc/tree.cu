@@ -246,11 +246,6 @@ __global__ void k_split_write(const uint64_t* __restrict__ keys, const int32_t* 
   }
 }
 
-__global__ void k_fill_i32(int32_t* __restrict__ p, int64_t n, int32_t v) {
-  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i < n) p[i] = v;
-}
-
 __global__ void k_leaf_flags(const int32_t* __restrict__ nch, int n, int64_t* __restrict__ f) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) f[i] = nch[i] == 0;
@@ -270,10 +265,53 @@ __global__ void k_leaf_compact(const int32_t* __restrict__ nch, const int64_t* _
 
 inline unsigned blocks(int64_t n, int t = kThreads) { return (unsigned)((n + t - 1) / t); }
 
+// The root cell: all bodies, integer coordinates 0, no parent.
+__global__ void k_root_cell(int32_t n, int32_t* bbeg, int32_t* bend, int32_t* ix, int32_t* iy, int32_t* iz,
+                            int32_t* parent) {
+  *bbeg = 0;
+  *bend = n;
+  *ix = *iy = *iz = 0;
+  *parent = -1;
+}
+
 struct LevelArrays {
   int n = 0;
   int32_t *bbeg, *bend, *ix, *iy, *iz, *parent, *cbeg, *nch;
 };
+
+// One level's arrays for the concatenation kernel: its first cell and the
+// eight per-cell fields (ix, iy, iz, bbeg, bend, cbeg, nch, parent).
+struct LevelSrc {
+  int first;
+  const int32_t* f[8];
+};
+
+// Breadth-first cell arrays from the per-level arrays, every level in one
+// launch: cell i finds its level by binary search over the first cells.
+__global__ void k_concat_levels(const LevelSrc* __restrict__ lv, int nlevel, int ncell, int32_t* __restrict__ level,
+                                int32_t* __restrict__ o0, int32_t* __restrict__ o1, int32_t* __restrict__ o2,
+                                int32_t* __restrict__ o3, int32_t* __restrict__ o4, int32_t* __restrict__ o5,
+                                int32_t* __restrict__ o6, int32_t* __restrict__ o7) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= ncell) return;
+  int lo = 0, hi = nlevel;  // last level whose first cell is <= i
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (lv[mid].first <= i) lo = mid;
+    else hi = mid;
+  }
+  const LevelSrc& L = lv[lo];
+  const int k = i - L.first;
+  level[i] = lo;
+  o0[i] = L.f[0][k];
+  o1[i] = L.f[1][k];
+  o2[i] = L.f[2][k];
+  o3[i] = L.f[3][k];
+  o4[i] = L.f[4][k];
+  o5[i] = L.f[5][k];
+  o6[i] = L.f[6][k];
+  o7[i] = L.f[7][k];
+}
 
 template <class R>
 void build_tree_impl(fmm_tree* t, const R* xyzq) {
@@ -331,13 +369,8 @@ void build_tree_impl(fmm_tree* t, const R* xyzq) {
   root.iy = alloc_n<int32_t>(a, 1);
   root.iz = alloc_n<int32_t>(a, 1);
   root.parent = alloc_n<int32_t>(a, 1);
-  {
-    int32_t h[6] = {0, (int32_t)N, 0, 0, 0, -1};
-    int32_t* dst[6] = {root.bbeg, root.bend, root.ix, root.iy, root.iz, root.parent};
-    for (int k = 0; k < 6; ++k)
-      GB_CK(cudaMemcpyAsync(dst[k], &h[k], sizeof(int32_t), cudaMemcpyHostToDevice, s));
-    GB_CK(cudaStreamSynchronize(s));
-  }
+  k_root_cell<<<1, 1, 0, s>>>((int32_t)N, root.bbeg, root.bend, root.ix, root.iy, root.iz, root.parent);
+  GB_LAUNCH("k_root_cell");
   lv.push_back(root);
   int first = 0;
   for (int l = 0;; ++l) {
@@ -378,15 +411,21 @@ void build_tree_impl(fmm_tree* t, const R* xyzq) {
   Cells& c = t->c;
   int32_t** fields[9] = {&c.level, &c.ix, &c.iy, &c.iz, &c.bbeg, &c.bend, &c.cbeg, &c.nch, &c.parent};
   for (auto f : fields) *f = alloc_n<int32_t>(a, nc);
-  for (size_t l = 0; l < lv.size(); ++l) {
-    LevelArrays& L = lv[l];
-    const int o = t->level_begin[l];
-    k_fill_i32<<<blocks(L.n), kThreads, 0, s>>>(c.level + o, L.n, (int32_t)l);
-    GB_LAUNCH("k_fill_i32");
-    int32_t* src[8] = {L.ix, L.iy, L.iz, L.bbeg, L.bend, L.cbeg, L.nch, L.parent};
-    int32_t* dst[8] = {c.ix, c.iy, c.iz, c.bbeg, c.bend, c.cbeg, c.nch, c.parent};
-    for (int k = 0; k < 8; ++k)
-      GB_CK(cudaMemcpyAsync(dst[k] + o, src[k], sizeof(int32_t) * L.n, cudaMemcpyDeviceToDevice, s));
+  {
+    std::vector<LevelSrc> h(lv.size());
+    for (size_t l = 0; l < lv.size(); ++l) {
+      const LevelArrays& L = lv[l];
+      h[l].first = t->level_begin[l];
+      const int32_t* f[8] = {L.ix, L.iy, L.iz, L.bbeg, L.bend, L.cbeg, L.nch, L.parent};
+      for (int k = 0; k < 8; ++k) h[l].f[k] = f[k];
+    }
+    LevelSrc* d = alloc_n<LevelSrc>(a, h.size());
+    GB_CK(cudaMemcpyAsync(d, h.data(), sizeof(LevelSrc) * h.size(), cudaMemcpyHostToDevice, s));
+    k_concat_levels<<<blocks(nc), kThreads, 0, s>>>(d, (int)h.size(), nc, c.level, c.ix, c.iy, c.iz, c.bbeg,
+                                                     c.bend, c.cbeg, c.nch, c.parent);
+    GB_LAUNCH("k_concat_levels");
+    // the H2D copy reads h (pageable) before returning; d is freed in order
+    a.release(d);
   }
   for (auto& L : lv) {
     int32_t* all[8] = {L.ix, L.iy, L.iz, L.bbeg, L.bend, L.cbeg, L.nch, L.parent};
