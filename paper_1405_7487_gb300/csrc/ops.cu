@@ -218,16 +218,31 @@ __global__ void k_target_flags(const int32_t* __restrict__ tgt, int64_t n, int32
   if (i == 0 || tgt[i] != tgt[i - 1]) has[tgt[i]] = 1;
 }
 
-// Targets ordered by (octant within the parent, cell): cells sharing an
-// octant see the same relative source pattern, so a tile of them needs few
-// distinct operators.
+// Targets ordered by (level, octant within the parent, boundary pattern,
+// cell).  The pattern is, per axis, how many cells (up to kPatternReach) the
+// domain still holds below and above the cell: interior cells and cells at
+// the same place on the boundary have the same set of translation offsets,
+// so tiles of them need fewer distinct operators (fewer, fuller entries).
+constexpr int kPatternReach = 4;
+constexpr int kPatternBits = 14;  // (reach + 1)^6 = 15625 patterns < 2^14
+constexpr int kTargetKeyExtra = 5 + 3 + kPatternBits;  // level, octant, pattern
+
 __global__ void k_target_keys(const int32_t* __restrict__ has, CellView c, int ncell, int cbits,
                               uint64_t* __restrict__ key, unsigned long long* __restrict__ count) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= ncell) return;
   if (has[i]) {
-    const uint64_t oct = ((c.ix[i] & 1) << 2) | ((c.iy[i] & 1) << 1) | (c.iz[i] & 1);
-    key[i] = (oct << cbits) | (uint32_t)i;
+    const int l = c.level[i];
+    const int side = (1 << l) - 1;
+    const int co[3] = {c.ix[i], c.iy[i], c.iz[i]};
+    uint64_t pat = 0;
+    for (int d = 0; d < 3; ++d) {
+      const int lo = min(co[d], kPatternReach), hi = min(side - co[d], kPatternReach);
+      pat = pat * ((kPatternReach + 1) * (kPatternReach + 1)) + (uint64_t)(lo * (kPatternReach + 1) + hi);
+    }
+    const uint64_t oct = ((co[0] & 1) << 2) | ((co[1] & 1) << 1) | (co[2] & 1);
+    key[i] = ((uint64_t)l << (3 + kPatternBits + cbits)) | (oct << (kPatternBits + cbits)) | (pat << cbits) |
+             (uint32_t)i;
     atomicAdd(count, 1ull);
   } else {
     key[i] = ~0ull;
@@ -506,7 +521,7 @@ void build_m2l_plan(fmm_tree* t) {
   GB_CK(cudaMemsetAsync(d_cnt + 1, 0, sizeof(unsigned long long), s));
   k_class_maxd<<<blocks(nm), kThreads, 0, s>>>(t->m2l_tgt, t->m2l_src, nm, cv, d_cnt + 1);
   GB_LAUNCH("k_class_maxd");
-  radix_sort_keys(a, tkey, t->ncell, cbits + 3, s);
+  radix_sort_keys(a, tkey, t->ncell, cbits + kTargetKeyExtra, s);
   unsigned long long hc[2] = {0, 0};
   GB_CK(cudaMemcpyAsync(hc, d_cnt, sizeof(hc), cudaMemcpyDeviceToHost, s));
   GB_CK(cudaStreamSynchronize(s));
