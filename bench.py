@@ -333,6 +333,95 @@ def cpu_baseline(workload: str, steps: int) -> dict:
                       f"build + forward + backward, {steps} step(s), {dt:.2f} s"}
 
 
+# ------------------------------------------------- precision / scale sweep
+
+def run_sweep(args):
+    """The precision and scale sweep: N bodies of the cube16m workload
+    (16,777,216 by default), p in {4, 8, 12, 16}.  The single-precision path
+    (FP32 P2P with compensation, 3xTF32 M2L) and the all-double path each run
+    build + forward + backward, timed with CUDA events after one warm-up step,
+    and their errors against the double direct sum on 4,096 sampled targets
+    are measured.  One JSON line per (p, path), then one line comparing the
+    paths at matched error: for each error level both paths reach, the time
+    of each, interpolated log-linearly between neighbouring p."""
+    import math
+
+    import numpy as np
+    import torch
+    from paper_1405_7487_gb300 import build_lib
+    build_lib.build()
+    from paper_1405_7487_gb300 import fmm as F
+    from paper_1405_7487_gb300 import workloads as W
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    spec = W.WORKLOADS["cube16m"]
+    x_h = W.make("cube16m", n=args.n)
+    N = x_h.shape[0]
+    w_h = W.weights(N, 41)
+    x32 = torch.from_numpy(x_h).to(dev)
+    idx = torch.from_numpy(W.sample_targets(N, 4096)).to(dev)
+    pd, fd = F.direct_f64(x32, idx)
+    ii = idx.long()
+    stream = torch.cuda.current_stream(dev)
+    rows = []
+    for p in spec["p"]:
+        for prec in ("f32", "f64"):
+            if prec == "f64" and p > args.sweep_max_p_f64:
+                continue
+            dt = torch.float32 if prec == "f32" else torch.float64
+            x = x32.to(dt)
+            w = torch.from_numpy(w_h).to(dev, dt)
+
+            def step():
+                T = F.Tree(x, p, spec["theta"], spec["ncrit"], F.FMM_FLAG_TIMING)
+                pot, force = T.evaluate()
+                T.backward(w)
+                st = T.stats()
+                T.close()
+                return pot, force, st
+
+            step()
+            torch.cuda.synchronize(dev)
+            times = []
+            for _ in range(args.steps):
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                pot, force, st = step()
+                e1.record(stream)
+                e1.synchronize()
+                times.append(e0.elapsed_time(e1))
+            err_p = float(torch.linalg.norm(pot[ii].double() - pd) / torch.linalg.norm(pd))
+            err_f = float(torch.linalg.norm(force[ii].double() - fd) / torch.linalg.norm(fd))
+            row = {"sweep": "precision", "N": N, "p": p, "path": prec, "ms_per_step": statistics.mean(times),
+                   "step": "fmm_build + fmm_evaluate + fmm_backward", "err_vs_direct": {"pot": err_p, "force": err_f},
+                   "phase_ms": {k: round(v, 3) for k, v in st["ms"].items()}, "m2l_engine": st["m2l_engine"],
+                   "n_m2l": st["n_m2l"], "n_p2p_body_pairs": st["n_p2p_body_pairs"]}
+            rows.append(row)
+            print(json.dumps(row), flush=True)
+            del pot, force
+            torch.cuda.empty_cache()
+
+    def at_error(path, e):
+        pts = sorted((r["p"], r["err_vs_direct"]["pot"], r["ms_per_step"]) for r in rows if r["path"] == path)
+        for (p0, e0, t0), (p1, e1, t1) in zip(pts, pts[1:]):
+            if (e0 - e) * (e1 - e) <= 0 and e0 != e1:
+                u = (math.log(e) - math.log(e0)) / (math.log(e1) - math.log(e0))
+                return math.exp(math.log(t0) + u * (math.log(t1) - math.log(t0)))
+        for pp, ee, tt in pts:  # exactly reached at a measured p
+            if ee == e:
+                return tt
+        return None
+
+    cmp = {}
+    for e in (1e-2, 1e-3, 1e-4, 1e-5):
+        a, b = at_error("f32", e), at_error("f64", e)
+        if a is not None and b is not None:
+            cmp[f"{e:.0e}"] = {"f32_ms": round(a, 2), "f64_ms": round(b, 2), "f64_over_f32": round(b / a, 2)}
+    print(json.dumps({"sweep": "precision", "N": N, "matched_error": cmp}), flush=True)
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -362,10 +451,15 @@ def main():
     ap.add_argument("--workload", default="cube1m_p10")
     ap.add_argument("--n", type=int, default=None, help="bodies (default: the workload's size)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--sweep", default=None, choices=["precision"],
+                    help="precision/scale sweep (cube16m: FP32 vs all-FP64 at p = 4..16), JSON lines")
+    ap.add_argument("--sweep-max-p-f64", type=int, default=16, help="largest p of the double path in the sweep")
     ap.add_argument("--p2p", default="one-sided", choices=["one-sided", "mutual"],
                     help="near field: one block per target leaf, or mutual interaction")
     args = ap.parse_args()
-    if args.impl == "reference":
+    if args.sweep == "precision":
+        run_sweep(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_gpu(args)
