@@ -318,6 +318,31 @@ __device__ __forceinline__ int plan_tile(const int2* __restrict__ ranges, Cursor
   return filled;
 }
 
+// The same plan from the leaf's ranges staged in shared memory with their
+// exclusive prefix sums (pre[r] = bodies before range r): stream position S
+// lies in the last range r with pre[r] <= S.  Each thread's positions only
+// grow (slots within a tile, then tiles), so its cursor r only moves
+// forward: planning costs O(ranges + slots) per leaf and thread instead of
+// a walk over every range for every tile.
+constexpr int kStagedRanges = 256;
+
+__device__ __forceinline__ int plan_tile_staged(const int2* __restrict__ rng, const int* __restrict__ pre, int nr,
+                                                int T, int& cur, int (&gidx)[kSlots]) {
+  const int total = pre[nr];
+  const int cnt = min(kSrcTile, total - T);
+#pragma unroll
+  for (int m = 0; m < kSlots; ++m) {
+    const int sl = threadIdx.x + m * kThreads;
+    gidx[m] = -1;
+    if (sl < cnt) {
+      const int S = T + sl;
+      while (pre[cur + 1] <= S) ++cur;
+      gidx[m] = rng[cur].x + (S - pre[cur]);
+    }
+  }
+  return cnt > 0 ? cnt : 0;
+}
+
 __device__ __forceinline__ void load_slots(const float4* __restrict__ bodies, const int (&gidx)[kSlots],
                                            float4 (&v)[kSlots], const Lim& lim) {
 #pragma unroll
@@ -353,12 +378,39 @@ __global__ void __launch_bounds__(kThreads) k_p2p_f2(const float4* __restrict__ 
                                                      float4* __restrict__ near, Lim lim) {
   __shared__ SrcPair tiles[2][kPairTile];
   __shared__ Acc<float> red[2][kThreads];
+  __shared__ int2 srng[kStagedRanges];
+  __shared__ int spre[kStagedRanges + 1];
   const int li = blockIdx.x;
   const int cell = GB_LD(leaves, li, lim.nleaf, 101);
   const int s = GB_LD(bbeg, cell, lim.ncell, 102), e = GB_LD(bend, cell, lim.ncell, 103);
   const int r0 = GB_LD(rptr, li, lim.nleaf + 1, 104), r1 = GB_LD(rptr, li + 1, lim.nleaf + 1, 105);
   const int tid = threadIdx.x;
   const f2 zero = 0ull;
+  // the leaf's neighbour ranges and their prefix sums in shared memory (warp
+  // 0 scans 32 ranges at a time); larger lists take the uniform range walk
+  const int nr = r1 - r0;
+  const bool staged = nr <= kStagedRanges;
+  if (staged && tid < 32) {
+    int base = 0;
+    for (int r = tid; r - tid < nr; r += 32) {
+      int len = 0;
+      if (r < nr) {
+        const int2 rg = GB_LD(ranges, r0 + r, lim.nranges, 107);
+        srng[r] = rg;
+        len = rg.y - rg.x;
+      }
+      int incl = len;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(0xffffffffu, incl, o);
+        if (tid >= o) incl += v;
+      }
+      if (r < nr) spre[r] = base + incl - len;
+      base += __shfl_sync(0xffffffffu, incl, 31);
+    }
+    if (tid == 0) spre[nr] = base;
+  }
+  __syncthreads();
   for (int t0 = s; t0 < e; t0 += kTgtChunk) {
     const int nt = min(kTgtChunk, e - t0);
     const int T2 = (nt + 1) >> 1;
@@ -419,16 +471,25 @@ __global__ void __launch_bounds__(kThreads) k_p2p_f2(const float4* __restrict__ 
     // neighbour stream: the next tile is loaded into registers while the
     // current one is summed
     Cursor cur{r0, 0};
+    int scur = 0, T = 0;
+    auto plan = [&](int (&gi)[kSlots]) {
+      if (staged) {
+        const int c = plan_tile_staged(srng, spre, nr, T, scur, gi);
+        T += kSrcTile;
+        return c;
+      }
+      return plan_tile(ranges, cur, r1, gi, lim);
+    };
     int gidx[kSlots];
     float4 v[kSlots];
-    int cnt = plan_tile(ranges, cur, r1, gidx, lim);
+    int cnt = plan(gidx);
     load_slots(bodies, gidx, v, lim);
     __syncthreads();
     store_slots(tiles[0], cnt, v);
     __syncthreads();
     int buf = 0;
     while (cnt > 0) {
-      const int nxt = plan_tile(ranges, cur, r1, gidx, lim);
+      const int nxt = plan(gidx);
       if (nxt > 0) load_slots(bodies, gidx, v, lim);
       if (active) {
         const int np = (cnt + 1) >> 1;
