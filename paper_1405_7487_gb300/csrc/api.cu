@@ -72,6 +72,7 @@ void create_tree(fmm_tree* t, const R* xyzq) {
   t->L = a.alloc(rs * (size_t)t->ncell * t->Kp);
   GB_CK(cudaMemsetAsync(t->M, 0, rs * (size_t)t->ncell * t->Kp, s));
   t->near = a.alloc(rs * 4 * (size_t)t->N);
+  if (!f64) t->near_src = a.alloc(32 * (size_t)((t->N + 1) / 2));
   t->grad_q = a.alloc(rs * 4 * (size_t)t->N);
   t->q_last = a.alloc(rs * (size_t)t->N);
   if (t->m2l_engine == 1) {

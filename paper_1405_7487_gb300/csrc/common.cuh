@@ -143,6 +143,7 @@ struct fmm_tree {
   int32_t* quad_class = nullptr;   // per quad entry: the class
   int4* quad_entry = nullptr;      // per quad entry: the entry of each of the quad's tiles (-1: none)
   void* near = nullptr;   // N x 4 (phi, grad) sorted, P2P part
+  void* near_src = nullptr;  // single precision: the P2P sources, bodies 2m and 2m + 1 in 32-byte pair m
   void* grad_q = nullptr; // N x 4 (phi, grad) sorted, of the last evaluate
   void* q_last = nullptr; // N sorted charges of the last evaluate
   int evaluations = 0;

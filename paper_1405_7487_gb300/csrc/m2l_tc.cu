@@ -39,6 +39,7 @@
 #include <vector>
 
 #include "kernels.cuh"
+#include "mbarrier.cuh"
 
 namespace gbfmm {
 namespace {
@@ -46,15 +47,10 @@ namespace {
 constexpr int kProducers = 128;
 constexpr int kThreadsTC = 160;
 constexpr int kMaxStages = 8;
-constexpr long long kSpinLimit = 1ll << 20;
 
 constexpr int kKB = 32;               // fp32 elements per k-block (128 bytes per row)
 constexpr int kRowB = kKB * 4;        // bytes per row of a k-block
 constexpr int kStageA = 128 * kRowB;  // bytes of one 128-row operand block
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
 
 // Byte offset of 16-byte chunk c (0..7) of row r in a [rows][128 B] block
 // with the 128-byte swizzle: address bits [4,6] are XORed with bits [7,9],
@@ -85,39 +81,12 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map
       : "memory");
 }
 
-__device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, uint32_t bytes) {
-  asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n}\n" ::"r"(bar),
-               "r"(bytes)
-               : "memory");
-}
-
 __device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, int bytes) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(dst), "l"(src), "r"(bytes) : "memory");
 }
 template <int N>
 __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
-}
-__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
-
-__device__ __forceinline__ void mbar_init(uint32_t bar, int count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(bar), "r"(count) : "memory");
-}
-// Bounded wait for the phase with the given parity; false if it gave up (or
-// another role aborted).
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag) {
-  for (long long it = 0; it < kSpinLimit; ++it) {
-    uint32_t done;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(done)
-        : "r"(bar), "r"(parity)
-        : "memory");
-    if (done) return true;
-    if ((it & 1023) == 1023 && *abort_flag) return false;
-  }
-  *abort_flag = 1;
-  return false;
 }
 
 // Instruction descriptor, kind::tf32: D fp32, A and B tf32, both K-major,

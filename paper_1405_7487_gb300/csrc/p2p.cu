@@ -15,6 +15,7 @@
 // Within a tile each thread sums naively; tile sums are combined with
 // compensated (Kahan) addition.
 #include "kernels.cuh"
+#include "mbarrier.cuh"
 
 namespace gbfmm {
 namespace {
@@ -208,54 +209,43 @@ __global__ void __launch_bounds__(kThreads) k_p2p(const R4* __restrict__ bodies,
 }
 
 // ---------------------------------------------------------------------------
-// Single precision with packed FP32 pairs (add/sub/mul/fma.rn.f32x2, sm_100
-// and later): one instruction evaluates one target against two sources.  The
-// staged tile holds the sources two by two, {x0,x1,y0,y1} {z0,z1,q0,q1}, so a
-// pair of sources is two 16-byte shared loads.  Each thread owns two targets
-// as in the generic kernel; its sums are kept per source parity (the low and
-// high halves) and added at the end.  A padding source (odd tile length) sits
-// at 1e30 with zero charge: r^2 overflows to +inf, rsqrt gives 0, and it adds
-// exactly zero.
+// Single precision with packed FP32 pairs (the float2 add/mul/fma of sm_100
+// and later, __fadd2_rn and friends): one instruction evaluates one target
+// against two sources.
+// Sources are read from a pair-major copy of the sorted bodies (k_pair_bodies:
+// pair m = bodies 2m and 2m + 1 as {x0,x1,y0,y1} {z0,z1,q0,q1}, 32 bytes), so a
+// pair of sources is two 16-byte shared loads and a body range of the
+// neighbour stream is a contiguous run of pairs.  Each run is copied to
+// shared memory by one bulk copy (cp.async.bulk) per tile it touches, and the
+// copies of a tile complete on the tile's mbarrier; while a tile is summed the
+// next one is in flight (two buffers, one block barrier per tile).  A range
+// with an odd first body (or an odd end) brings one body too many into its
+// first (last) pair; once the tile has landed, that half is overwritten with a
+// far-away zero charge.  Each thread owns two targets as in the generic
+// kernel, and the G groups of a target chunk take the pairs of a tile
+// round-robin.  Its sums are kept per source parity (the low and high halves)
+// and folded at the end of each tile.
 
-typedef unsigned long long f2;  // two packed floats (low half first in memory)
+typedef float2 f2;  // two packed floats (.x: the low half)
 
-__device__ __forceinline__ f2 f2_pack(float lo, float hi) {
-  f2 r;
-  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
-  return r;
-}
+__device__ __forceinline__ f2 f2_pack(float lo, float hi) { return make_float2(lo, hi); }
 __device__ __forceinline__ void f2_unpack(f2 v, float& lo, float& hi) {
-  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+  lo = v.x;
+  hi = v.y;
 }
-__device__ __forceinline__ f2 f2_add(f2 a, f2 b) {
-  f2 r;
-  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
-  return r;
-}
-__device__ __forceinline__ f2 f2_sub(f2 a, f2 b) {
-  f2 r;
-  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
-  return r;
-}
-__device__ __forceinline__ f2 f2_mul(f2 a, f2 b) {
-  f2 r;
-  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
-  return r;
-}
-__device__ __forceinline__ f2 f2_fma(f2 a, f2 b, f2 c) {
-  f2 r;
-  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
-  return r;
-}
+__device__ __forceinline__ f2 f2_add(f2 a, f2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ f2 f2_mul(f2 a, f2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ f2 f2_fma(f2 a, f2 b, f2 c) { return __ffma2_rn(a, b, c); }
 
 struct Acc2 {
   f2 p, x, y, z;
 };
 
-// One target (X, Y, Z duplicated in both halves) against the source pair.
+// One target (its negated coordinates duplicated in both halves) against the
+// source pair.
 template <bool MASK>
-__device__ __forceinline__ void pair2(f2 XX, f2 YY, f2 ZZ, f2 QQ, f2 X, f2 Y, f2 Z, Acc2& a) {
-  const f2 dx = f2_sub(XX, X), dy = f2_sub(YY, Y), dz = f2_sub(ZZ, Z);
+__device__ __forceinline__ void pair2(f2 XX, f2 YY, f2 ZZ, f2 QQ, f2 NX, f2 NY, f2 NZ, Acc2& a) {
+  const f2 dx = f2_add(XX, NX), dy = f2_add(YY, NY), dz = f2_add(ZZ, NZ);
   f2 r2 = f2_mul(dx, dx);
   r2 = f2_fma(dy, dy, r2);
   r2 = f2_fma(dz, dz, r2);
@@ -275,142 +265,146 @@ __device__ __forceinline__ void pair2(f2 XX, f2 YY, f2 ZZ, f2 QQ, f2 X, f2 Y, f2
   a.z = f2_fma(f, dz, a.z);
 }
 
-constexpr int kPairTile = kSrcTile / 2;
-constexpr int kSlots = kSrcTile / kThreads;  // bodies staged per thread per tile
+constexpr int kTilePairs = 512;  // source pairs per staged tile (1,024 bodies, 16 KB)
+constexpr int kWindow = 256;     // neighbour ranges staged at a time
 constexpr float kFar = 1e30f;
 
 struct __align__(16) SrcPair {
   float w[8];  // x0 x1 y0 y1 z0 z1 q0 q1
 };
 
-__device__ __forceinline__ void put_body(SrcPair* tile, int slot, float4 b) {
-  float* w = tile[slot >> 1].w + (slot & 1);
-  w[0] = b.x;
-  w[2] = b.y;
-  w[4] = b.z;
-  w[6] = b.w;
+// The sorted bodies in pair-major form: pair m holds bodies 2m and 2m + 1
+// (the high half of the last pair of an odd count is a far-away zero charge).
+__global__ void k_pair_bodies(const float4* __restrict__ b, long long n, SrcPair* __restrict__ out) {
+  const long long m = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (2 * m >= n) return;
+  const float4 u = b[2 * m];
+  const float4 v = 2 * m + 1 < n ? b[2 * m + 1] : make_float4(kFar, kFar, kFar, 0.f);
+  float4* o = reinterpret_cast<float4*>(out + m);
+  o[0] = make_float4(u.x, v.x, u.y, v.y);
+  o[1] = make_float4(u.z, v.z, u.w, v.w);
 }
 
-// Global indices of this thread's slots of the next tile of the neighbour
-// stream (-1: none); returns the tile length (uniform over the block).
-__device__ __forceinline__ int plan_tile(const int2* __restrict__ ranges, Cursor& cur, int r1, int (&gidx)[kSlots],
-                                         const Lim& lim) {
-  int filled = 0;
-#pragma unroll
-  for (int m = 0; m < kSlots; ++m) gidx[m] = -1;
-  while (filled < kSrcTile && cur.r < r1) {
-    const int2 rg = GB_LD(ranges, cur.r, lim.nranges, 107);
-    const int b = rg.x + cur.off;
-    const int take = min(rg.y - b, kSrcTile - filled);
-#pragma unroll
-    for (int m = 0; m < kSlots; ++m) {
-      const int sl = threadIdx.x + m * kThreads - filled;
-      if (sl >= 0 && sl < take) gidx[m] = b + sl;
+// A source stream in shared memory: body ranges [a, b) as pair ranges
+// [a/2, (b+1)/2), each as (first pair, pad bits) -- bit 0: the low half of the
+// first pair (body a - 1) is not in the range, bit 1: the high half of the
+// last pair (body b) is not -- and the exclusive prefix sums of the pair
+// counts (pre[n] = the stream length in pairs).
+struct Stream {
+  int2 rng[kWindow];
+  int pre[kWindow + 1];
+};
+
+// Warp 0 stages ranges [r0, r0 + nw) of the list (nw <= kWindow); every lane
+// returns the stream length.
+__device__ __forceinline__ int stage_window(Stream& st, const int2* __restrict__ ranges, int r0, int nw,
+                                            const Lim& lim) {
+  const int lane = threadIdx.x;
+  int base = 0;
+  for (int r = lane; r - lane < nw; r += 32) {
+    int len = 0;
+    if (r < nw) {
+      const int2 rg = GB_LD(ranges, r0 + r, lim.nranges, 107);
+      const int ps = rg.x >> 1, pe = (rg.y + 1) >> 1;
+      st.rng[r] = make_int2(ps, (rg.x & 1) | ((rg.y & 1) << 1));
+      len = pe - ps;
     }
-    filled += take;
-    if (b + take == rg.y) {
-      ++cur.r;
-      cur.off = 0;
-    } else {
-      cur.off += take;
+    int incl = len;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int v = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += v;
     }
+    if (r < nw) st.pre[r] = base + incl - len;
+    base += __shfl_sync(0xffffffffu, incl, 31);
   }
-  return filled;
+  if (lane == 0) st.pre[nw] = base;
+  return base;
 }
 
-// The same plan from the leaf's ranges staged in shared memory with their
-// exclusive prefix sums (pre[r] = bodies before range r): stream position S
-// lies in the last range r with pre[r] <= S.  Each thread's positions only
-// grow (slots within a tile, then tiles), so its cursor r only moves
-// forward: planning costs O(ranges + slots) per leaf and thread instead of
-// a walk over every range for every tile.
-constexpr int kStagedRanges = 256;
-
-__device__ __forceinline__ int plan_tile_staged(const int2* __restrict__ rng, const int* __restrict__ pre, int nr,
-                                                int T, int& cur, int (&gidx)[kSlots]) {
-  const int total = pre[nr];
-  const int cnt = min(kSrcTile, total - T);
-#pragma unroll
-  for (int m = 0; m < kSlots; ++m) {
-    const int sl = threadIdx.x + m * kThreads;
-    gidx[m] = -1;
-    if (sl < cnt) {
-      const int S = T + sl;
-      while (pre[cur + 1] <= S) ++cur;
-      gidx[m] = rng[cur].x + (S - pre[cur]);
+// Bulk copies of stream pairs [T0, T1) into a tile, one per range piece,
+// completing on bar (whose expected bytes are set by the caller).
+__device__ __forceinline__ void issue_tile(const Stream& st, int nw, int T0, int T1,
+                                           const SrcPair* __restrict__ src, uint32_t dst, uint32_t bar,
+                                           const Lim& lim) {
+  for (int r = threadIdx.x; r < nw; r += kThreads) {
+    const int pr = st.pre[r];
+    const int a = max(pr, T0), b = min(st.pre[r + 1], T1);
+    if (a < b) {
+      const int first = st.rng[r].x + (a - pr);
+#ifdef GBFMM_CHECKED
+      if (!in_range(first + (b - a) - 1, (lim.N + 1) / 2, 108, lim.rec)) continue;
+#endif
+      bulk_g2s(dst + (uint32_t)(a - T0) * (uint32_t)sizeof(SrcPair), src + first,
+               (uint32_t)(b - a) * (uint32_t)sizeof(SrcPair), bar);
     }
-  }
-  return cnt > 0 ? cnt : 0;
-}
-
-__device__ __forceinline__ void load_slots(const float4* __restrict__ bodies, const int (&gidx)[kSlots],
-                                           float4 (&v)[kSlots], const Lim& lim) {
-#pragma unroll
-  for (int m = 0; m < kSlots; ++m)
-    v[m] = gidx[m] >= 0 ? GB_LD(bodies, gidx[m], lim.N, 108) : make_float4(kFar, kFar, kFar, 0.f);
-}
-
-__device__ __forceinline__ void store_slots(SrcPair* tile, int cnt, const float4 (&v)[kSlots]) {
-  const int lim2 = (cnt + 1) & ~1;  // slots up to the even length (the pad)
-#pragma unroll
-  for (int m = 0; m < kSlots; ++m) {
-    const int sl = threadIdx.x + m * kThreads;
-    if (sl < lim2) put_body(tile, sl, v[m]);
   }
 }
 
+// After the copies of pairs [T0, T1) have landed: a half that lies outside
+// its range becomes a far-away zero charge (r^2 overflows to +inf, rsqrt
+// gives 0, and the half adds exactly zero, masked or not).
+__device__ __forceinline__ void pad_tile(const Stream& st, int nw, int T0, int T1, SrcPair* tile) {
+  for (int r = threadIdx.x; r < nw; r += kThreads) {
+    const int f = st.rng[r].y;
+    if (f == 0) continue;
+    const int a = st.pre[r], b = st.pre[r + 1] - 1;
+    if ((f & 1) && a >= T0 && a < T1) {
+      tile[a - T0].w[0] = kFar;
+      tile[a - T0].w[6] = 0.f;
+    }
+    if ((f & 2) && b >= T0 && b < T1) {
+      tile[b - T0].w[1] = kFar;
+      tile[b - T0].w[7] = 0.f;
+    }
+  }
+}
+
+// Group g of G takes pairs g, g + G, g + 2G, ... of a tile of np pairs.
 template <bool MASK>
-__device__ __forceinline__ void tile_sum2(const SrcPair* __restrict__ tile, int k0, int k1, f2 X0, f2 Y0, f2 Z0,
-                                          f2 X1, f2 Y1, f2 Z1, Acc2& a0, Acc2& a1) {
+__device__ __forceinline__ void tile_sum2(const SrcPair* __restrict__ tile, int k, int np, int G, f2 X0, f2 Y0,
+                                          f2 Z0, f2 X1, f2 Y1, f2 Z1, Acc2& a0, Acc2& a1) {
 #pragma unroll 2
-  for (int k = k0; k < k1; ++k) {
-    const ulonglong2 A = *reinterpret_cast<const ulonglong2*>(tile[k].w);
-    const ulonglong2 B = *reinterpret_cast<const ulonglong2*>(tile[k].w + 4);
-    pair2<MASK>(A.x, A.y, B.x, B.y, X0, Y0, Z0, a0);
-    pair2<MASK>(A.x, A.y, B.x, B.y, X1, Y1, Z1, a1);
+  for (; k < np; k += G) {
+    const float4 A = *reinterpret_cast<const float4*>(tile[k].w);
+    const float4 B = *reinterpret_cast<const float4*>(tile[k].w + 4);
+    const f2 XX = make_float2(A.x, A.y), YY = make_float2(A.z, A.w);
+    const f2 ZZ = make_float2(B.x, B.y), QQ = make_float2(B.z, B.w);
+    pair2<MASK>(XX, YY, ZZ, QQ, X0, Y0, Z0, a0);
+    pair2<MASK>(XX, YY, ZZ, QQ, X1, Y1, Z1, a1);
   }
 }
 
 __global__ void __launch_bounds__(kThreads) k_p2p_f2(const float4* __restrict__ bodies,
+                                                     const SrcPair* __restrict__ pairs,
                                                      const int32_t* __restrict__ leaves,
                                                      const int32_t* __restrict__ bbeg, const int32_t* __restrict__ bend,
                                                      const int32_t* __restrict__ rptr, const int2* __restrict__ ranges,
-                                                     float4* __restrict__ near, Lim lim) {
-  __shared__ SrcPair tiles[2][kPairTile];
-  __shared__ Acc<float> red[2][kThreads];
-  __shared__ int2 srng[kStagedRanges];
-  __shared__ int spre[kStagedRanges + 1];
+                                                     float4* __restrict__ near, int* __restrict__ err, Lim lim) {
+  // the group partials of the final reduction reuse the first tile
+  static_assert(sizeof(Acc<float>) * 2 * kThreads <= sizeof(SrcPair) * kTilePairs, "reduction space");
+  __shared__ SrcPair tiles[2][kTilePairs];
+  __shared__ Stream st;
+  __shared__ __align__(8) unsigned long long bar[2];
+  __shared__ int abort_flag;
+  Acc<float>(*red)[kThreads] = reinterpret_cast<Acc<float>(*)[kThreads]>(&tiles[0][0]);
   const int li = blockIdx.x;
   const int cell = GB_LD(leaves, li, lim.nleaf, 101);
   const int s = GB_LD(bbeg, cell, lim.ncell, 102), e = GB_LD(bend, cell, lim.ncell, 103);
   const int r0 = GB_LD(rptr, li, lim.nleaf + 1, 104), r1 = GB_LD(rptr, li + 1, lim.nleaf + 1, 105);
   const int tid = threadIdx.x;
-  const f2 zero = 0ull;
-  // the leaf's neighbour ranges and their prefix sums in shared memory (warp
-  // 0 scans 32 ranges at a time); larger lists take the uniform range walk
-  const int nr = r1 - r0;
-  const bool staged = nr <= kStagedRanges;
-  if (staged && tid < 32) {
-    int base = 0;
-    for (int r = tid; r - tid < nr; r += 32) {
-      int len = 0;
-      if (r < nr) {
-        const int2 rg = GB_LD(ranges, r0 + r, lim.nranges, 107);
-        srng[r] = rg;
-        len = rg.y - rg.x;
-      }
-      int incl = len;
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const int v = __shfl_up_sync(0xffffffffu, incl, o);
-        if (tid >= o) incl += v;
-      }
-      if (r < nr) spre[r] = base + incl - len;
-      base += __shfl_sync(0xffffffffu, incl, 31);
-    }
-    if (tid == 0) spre[nr] = base;
+  const f2 zero = make_float2(0.f, 0.f);
+  if (tid == 0) {
+    mbar_init(smem_u32(&bar[0]), 1);
+    mbar_init(smem_u32(&bar[1]), 1);
+    abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
   }
   __syncthreads();
+  const int nr = r1 - r0;
+  const int nwin = (nr + kWindow - 1) / kWindow;
+  int buf = 0;
+  uint32_t parity = 0;  // bit b: the phase of bar[b] to wait for next
   for (int t0 = s; t0 < e; t0 += kTgtChunk) {
     const int nt = min(kTgtChunk, e - t0);
     const int T2 = (nt + 1) >> 1;
@@ -422,12 +416,13 @@ __global__ void __launch_bounds__(kThreads) k_p2p_f2(const float4* __restrict__ 
     if (active) {
       const float4 a = GB_LD(bodies, t0 + i, lim.N, 106);
       const float4 b = has_b ? GB_LD(bodies, t0 + i + T2, lim.N, 106) : a;
-      X0 = f2_pack(a.x, a.x);
-      Y0 = f2_pack(a.y, a.y);
-      Z0 = f2_pack(a.z, a.z);
-      X1 = f2_pack(b.x, b.x);
-      Y1 = f2_pack(b.y, b.y);
-      Z1 = f2_pack(b.z, b.z);
+      // negated, duplicated target coordinates
+      X0 = f2_pack(-a.x, -a.x);
+      Y0 = f2_pack(-a.y, -a.y);
+      Z0 = f2_pack(-a.z, -a.z);
+      X1 = f2_pack(-b.x, -b.x);
+      Y1 = f2_pack(-b.y, -b.y);
+      Z1 = f2_pack(-b.z, -b.z);
     }
     // tile sums: the two parities folded, then compensated (Kahan) addition
     auto fold = [](const Acc2& a) {
@@ -444,67 +439,64 @@ __global__ void __launch_bounds__(kThreads) k_p2p_f2(const float4* __restrict__ 
       return r;
     };
     Acc<float> s0{0, 0, 0, 0}, c0{0, 0, 0, 0}, s1{0, 0, 0, 0}, c1{0, 0, 0, 0};
-    auto accumulate = [&](const Acc2& p, Acc<float>& sm, Acc<float>& cm) { kahan_add(sm, cm, fold(p)); };
-    // own leaf, masked
-    for (int c0b = s; c0b < e; c0b += kSrcTile) {
-      const int cnt = min(kSrcTile, e - c0b);
-      int gidx[kSlots];
-#pragma unroll
-      for (int m = 0; m < kSlots; ++m) {
-        const int sl = tid + m * kThreads;
-        gidx[m] = sl < cnt ? c0b + sl : -1;
+    // window -1: the leaf's own bodies (masked: self and coincident pairs
+    // add zero); then the neighbour ranges, kWindow at a time
+    for (int w = -1; w < nwin; ++w) {
+      const int nw = w < 0 ? 1 : min(kWindow, nr - w * kWindow);
+      if (tid < 32) {
+        int P;
+        if (w < 0) {
+          const int ps = s >> 1, pe = (e + 1) >> 1;
+          if (tid == 0) {
+            st.rng[0] = make_int2(ps, (s & 1) | ((e & 1) << 1));
+            st.pre[0] = 0;
+            st.pre[1] = pe - ps;
+          }
+          P = pe - ps;
+        } else {
+          P = stage_window(st, ranges, r0 + w * kWindow, nw, lim);
+        }
+        if (tid == 0 && P > 0) mbar_arrive_expect_tx(smem_u32(&bar[buf]), (uint32_t)(min(P, kTilePairs) * sizeof(SrcPair)));
       }
-      float4 v[kSlots];
-      load_slots(bodies, gidx, v, lim);
       __syncthreads();
-      store_slots(tiles[0], cnt, v);
+      const int P = st.pre[nw];
+      const int ntile = (P + kTilePairs - 1) / kTilePairs;
+      if (ntile > 0) {
+        fence_async_smem();
+        issue_tile(st, nw, 0, min(P, kTilePairs), pairs, smem_u32(tiles[buf]), smem_u32(&bar[buf]), lim);
+      }
+      for (int k = 0; k < ntile; ++k) {
+        const int T0 = k * kTilePairs, T1 = min(T0 + kTilePairs, P);
+        const bool ok = mbar_wait(smem_u32(&bar[buf]), (parity >> buf) & 1u, &abort_flag);
+        parity ^= 1u << buf;
+        if (ok) pad_tile(st, nw, T0, T1, tiles[buf]);
+        const int T2n = min(T1 + kTilePairs, P);
+        if (tid == 0 && T1 < P)
+          mbar_arrive_expect_tx(smem_u32(&bar[buf ^ 1]), (uint32_t)((T2n - T1) * sizeof(SrcPair)));
+        // the pads are visible and tiles[buf ^ 1] is no longer read
+        if (__syncthreads_or(!ok)) {
+          // a copy did not land: give up on this leaf (no copy is in flight
+          // but the one waited for)
+          if (tid == 0) atomicExch(err, 1);
+          return;
+        }
+        if (T1 < P) {
+          fence_async_smem();
+          issue_tile(st, nw, T1, T2n, pairs, smem_u32(tiles[buf ^ 1]), smem_u32(&bar[buf ^ 1]), lim);
+        }
+        if (active) {
+          Acc2 p0{zero, zero, zero, zero}, p1{zero, zero, zero, zero};
+          if (w < 0)
+            tile_sum2<true>(tiles[buf], g, T1 - T0, G, X0, Y0, Z0, X1, Y1, Z1, p0, p1);
+          else
+            tile_sum2<false>(tiles[buf], g, T1 - T0, G, X0, Y0, Z0, X1, Y1, Z1, p0, p1);
+          kahan_add(s0, c0, fold(p0));
+          kahan_add(s1, c1, fold(p1));
+        }
+        buf ^= 1;
+      }
+      // the window's ranges and tiles are no longer read
       __syncthreads();
-      if (active) {
-        const int np = (cnt + 1) >> 1;
-        const int k0 = (g * np) / G, k1 = ((g + 1) * np) / G;
-        Acc2 p0{zero, zero, zero, zero}, p1{zero, zero, zero, zero};
-        tile_sum2<true>(tiles[0], k0, k1, X0, Y0, Z0, X1, Y1, Z1, p0, p1);
-        accumulate(p0, s0, c0);
-        accumulate(p1, s1, c1);
-      }
-    }
-    // neighbour stream: the next tile is loaded into registers while the
-    // current one is summed
-    Cursor cur{r0, 0};
-    int scur = 0, T = 0;
-    auto plan = [&](int (&gi)[kSlots]) {
-      if (staged) {
-        const int c = plan_tile_staged(srng, spre, nr, T, scur, gi);
-        T += kSrcTile;
-        return c;
-      }
-      return plan_tile(ranges, cur, r1, gi, lim);
-    };
-    int gidx[kSlots];
-    float4 v[kSlots];
-    int cnt = plan(gidx);
-    load_slots(bodies, gidx, v, lim);
-    __syncthreads();
-    store_slots(tiles[0], cnt, v);
-    __syncthreads();
-    int buf = 0;
-    while (cnt > 0) {
-      const int nxt = plan(gidx);
-      if (nxt > 0) load_slots(bodies, gidx, v, lim);
-      if (active) {
-        const int np = (cnt + 1) >> 1;
-        const int k0 = (g * np) / G, k1 = ((g + 1) * np) / G;
-        Acc2 p0{zero, zero, zero, zero}, p1{zero, zero, zero, zero};
-        tile_sum2<false>(tiles[buf], k0, k1, X0, Y0, Z0, X1, Y1, Z1, p0, p1);
-        accumulate(p0, s0, c0);
-        accumulate(p1, s1, c1);
-      }
-      // tiles[buf ^ 1] was last read two iterations ago (before the barrier
-      // that ended the previous iteration)
-      if (nxt > 0) store_slots(tiles[buf ^ 1], nxt, v);
-      __syncthreads();
-      buf ^= 1;
-      cnt = nxt;
     }
     red[0][tid] = s0;
     red[1][tid] = s1;
@@ -632,8 +624,13 @@ void launch_p2p(fmm_tree* t, cudaStream_t s) {
     return;
   }
   if (std::is_same<R, float>::value) {
-    k_p2p_f2<<<t->nleaf, kThreads, 0, s>>>((const float4*)t->work, t->leaves, t->c.bbeg, t->c.bend, t->p2p_rptr,
-                                           t->p2p_ranges, (float4*)t->near, t->lim);
+    const long long npair = (t->N + 1) / 2;
+    k_pair_bodies<<<(unsigned)((npair + 255) / 256), 256, 0, s>>>((const float4*)t->work, t->N,
+                                                                  (SrcPair*)t->near_src);
+    GB_LAUNCH("k_pair_bodies");
+    k_p2p_f2<<<t->nleaf, kThreads, 0, s>>>((const float4*)t->work, (const SrcPair*)t->near_src, t->leaves,
+                                           t->c.bbeg, t->c.bend, t->p2p_rptr, t->p2p_ranges, (float4*)t->near,
+                                           t->dev_err, t->lim);
     GB_LAUNCH("k_p2p_f2");
     return;
   }
