@@ -61,6 +61,7 @@ void create_tree(fmm_tree* t, const R* xyzq) {
   mark(FMM_PH_BUILD_TREE, 1);
   mark(FMM_PH_BUILD_LISTS, 0);
   build_lists(t);
+  if (!f64) build_p2p_items(t);
   mark(FMM_PH_BUILD_LISTS, 1);
   mark(FMM_PH_BUILD_PLAN, 0);
   build_m2l_plan(t);
@@ -88,6 +89,8 @@ void create_tree(fmm_tree* t, const R* xyzq) {
   mark(FMM_PH_BUILD_OPS, 1);
   mark(FMM_PH_BUILD_TOTAL, 1);
   GB_CK(cudaStreamSynchronize(s));
+  if (t->p2p_nitem)
+    GB_CK(cudaMemcpy(&t->p2p_nitem_host, t->p2p_nitem, sizeof(long long), cudaMemcpyDeviceToHost));
   if (timing)
     for (int ph : {FMM_PH_BUILD_TOTAL, FMM_PH_BUILD_TREE, FMM_PH_BUILD_LISTS, FMM_PH_BUILD_PLAN, FMM_PH_BUILD_OPS})
       cudaEventElapsedTime(&t->ms[ph], t->ev[2 * ph], t->ev[2 * ph + 1]);

@@ -55,6 +55,8 @@ template <class R> void launch_m2m(fmm_tree* t, int level, cudaStream_t s);
 template <class R> void launch_l2l(fmm_tree* t, int level, cudaStream_t s);
 template <class R> void launch_m2l_cuda_core(fmm_tree* t, cudaStream_t s);
 template <class R> void launch_p2p(fmm_tree* t, cudaStream_t s);
+// near-field work items of the single-precision kernel (after the lists)
+void build_p2p_items(fmm_tree* t);
 // mode 0: forward (pot, force out; gradient saved); mode 1: backward
 // (a = dq, b = dx; the pass charges are the weights w).
 template <class R> void launch_l2p_finalize(fmm_tree* t, int mode, R* a, R* b, cudaStream_t s);

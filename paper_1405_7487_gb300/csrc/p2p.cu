@@ -14,6 +14,8 @@
 // two different leaves never coincide, so those tiles need no mask.
 // Within a tile each thread sums naively; tile sums are combined with
 // compensated (Kahan) addition.
+#include <algorithm>
+
 #include "kernels.cuh"
 #include "mbarrier.cuh"
 
@@ -377,10 +379,10 @@ __device__ __forceinline__ void tile_sum2(const SrcPair* __restrict__ tile, int 
 
 __global__ void __launch_bounds__(kThreads) k_p2p_f2(const float4* __restrict__ bodies,
                                                      const SrcPair* __restrict__ pairs,
-                                                     const int32_t* __restrict__ leaves,
-                                                     const int32_t* __restrict__ bbeg, const int32_t* __restrict__ bend,
-                                                     const int32_t* __restrict__ rptr, const int2* __restrict__ ranges,
-                                                     float4* __restrict__ near, int* __restrict__ err, Lim lim) {
+                                                     const int4* __restrict__ items,
+                                                     const int2* __restrict__ item_rng,
+                                                     const int2* __restrict__ ranges, float4* __restrict__ near,
+                                                     int* __restrict__ err, Lim lim) {
   // the group partials of the final reduction reuse the first tile
   static_assert(sizeof(Acc<float>) * 2 * kThreads <= sizeof(SrcPair) * kTilePairs, "reduction space");
   __shared__ SrcPair tiles[2][kTilePairs];
@@ -388,10 +390,11 @@ __global__ void __launch_bounds__(kThreads) k_p2p_f2(const float4* __restrict__ 
   __shared__ __align__(8) unsigned long long bar[2];
   __shared__ int abort_flag;
   Acc<float>(*red)[kThreads] = reinterpret_cast<Acc<float>(*)[kThreads]>(&tiles[0][0]);
-  const int li = blockIdx.x;
-  const int cell = GB_LD(leaves, li, lim.nleaf, 101);
-  const int s = GB_LD(bbeg, cell, lim.ncell, 102), e = GB_LD(bend, cell, lim.ncell, 103);
-  const int r0 = GB_LD(rptr, li, lim.nleaf + 1, 104), r1 = GB_LD(rptr, li + 1, lim.nleaf + 1, 105);
+  // the item: targets [t0, t0 + nt) of the leaf with bodies [s, e) and
+  // neighbour ranges [r0, r1)
+  const int4 item = items[blockIdx.x];
+  const int2 irng = item_rng[blockIdx.x];
+  const int t0 = item.x, nt = item.y, s = item.z, e = item.w, r0 = irng.x, r1 = irng.y;
   const int tid = threadIdx.x;
   const f2 zero = make_float2(0.f, 0.f);
   if (tid == 0) {
@@ -405,8 +408,7 @@ __global__ void __launch_bounds__(kThreads) k_p2p_f2(const float4* __restrict__ 
   const int nwin = (nr + kWindow - 1) / kWindow;
   int buf = 0;
   uint32_t parity = 0;  // bit b: the phase of bar[b] to wait for next
-  for (int t0 = s; t0 < e; t0 += kTgtChunk) {
-    const int nt = min(kTgtChunk, e - t0);
+  {
     const int T2 = (nt + 1) >> 1;
     const int G = kThreads / T2;
     const int i = tid % T2, g = tid / T2;
@@ -513,6 +515,66 @@ __global__ void __launch_bounds__(kThreads) k_p2p_f2(const float4* __restrict__ 
     }
     __syncthreads();
   }
+}
+
+// Work items of the single-precision near field: a chunk of at most
+// kItemTargets targets of one leaf, with the leaf's bodies (its own source
+// range) and its neighbour ranges.  Per leaf, ceil(n / kItemTargets) chunks.
+// Items are ordered by decreasing work (targets x sources), and block b
+// takes item b: the block scheduler starts the largest first, which keeps
+// the last wave short on workloads with a few large leaves.
+constexpr int kItemTargets = kTgtChunk;
+__global__ void k_item_count(const int32_t* __restrict__ leaves, const int32_t* __restrict__ bbeg,
+                             const int32_t* __restrict__ bend, int nleaf, int64_t* __restrict__ cnt) {
+  const int li = blockIdx.x * blockDim.x + threadIdx.x;
+  if (li > nleaf) return;
+  if (li == nleaf) {
+    cnt[li] = 0;
+    return;
+  }
+  const int c = leaves[li];
+  cnt[li] = (bend[c] - bbeg[c] + kItemTargets - 1) / kItemTargets;
+}
+
+constexpr int kWorkBits = 40;  // targets x sources < 2^40
+
+__global__ void k_item_fill(const int32_t* __restrict__ leaves, const int32_t* __restrict__ bbeg,
+                            const int32_t* __restrict__ bend, const int32_t* __restrict__ rptr,
+                            const int2* __restrict__ ranges, int nleaf, const int64_t* __restrict__ ptr,
+                            int4* __restrict__ items, int2* __restrict__ rng, uint64_t* __restrict__ key,
+                            int32_t* __restrict__ val) {
+  const int li = blockIdx.x * blockDim.x + threadIdx.x;
+  if (li >= nleaf) return;
+  const int c = leaves[li];
+  const int s = bbeg[c], e = bend[c], r0 = rptr[li], r1 = rptr[li + 1];
+  long long src = e - s;
+  for (int r = r0; r < r1; ++r) src += ranges[r].y - ranges[r].x;
+  const int64_t p0 = ptr[li];
+  for (int k = 0; s + k * kItemTargets < e; ++k) {
+    const int t0 = s + k * kItemTargets, nt = min(kItemTargets, e - t0);
+    const int64_t idx = p0 + k;
+    items[idx] = make_int4(t0, nt, s, e);
+    rng[idx] = make_int2(r0, r1);
+    const uint64_t work = (uint64_t)nt * (uint64_t)src;
+    key[idx] = ((1ull << kWorkBits) - 1) - (work < (1ull << kWorkBits) - 2 ? work : (1ull << kWorkBits) - 2);  // largest first
+    val[idx] = (int32_t)idx;
+  }
+}
+
+__global__ void k_item_pad(const int64_t* __restrict__ total, int64_t nmax, uint64_t* __restrict__ key,
+                           int32_t* __restrict__ val) {
+  const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (k >= nmax || k < *total) return;
+  key[k] = (1ull << kWorkBits) - 1;
+  val[k] = (int32_t)k;
+}
+
+__global__ void k_item_gather(const int32_t* __restrict__ order, int64_t nmax, const int4* __restrict__ items_in,
+                              const int2* __restrict__ rng_in, int4* __restrict__ items, int2* __restrict__ rng) {
+  const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (k >= nmax) return;
+  items[k] = items_in[order[k]];
+  rng[k] = rng_in[order[k]];
 }
 
 // ---------------------------------------------------------------------------
@@ -628,15 +690,52 @@ void launch_p2p(fmm_tree* t, cudaStream_t s) {
     k_pair_bodies<<<(unsigned)((npair + 255) / 256), 256, 0, s>>>((const float4*)t->work, t->N,
                                                                   (SrcPair*)t->near_src);
     GB_LAUNCH("k_pair_bodies");
-    k_p2p_f2<<<t->nleaf, kThreads, 0, s>>>((const float4*)t->work, (const SrcPair*)t->near_src, t->leaves,
-                                           t->c.bbeg, t->c.bend, t->p2p_rptr, t->p2p_ranges, (float4*)t->near,
-                                           t->dev_err, t->lim);
+    k_p2p_f2<<<(unsigned)t->p2p_nitem_host, kThreads, 0, s>>>((const float4*)t->work,
+                                                              (const SrcPair*)t->near_src, t->p2p_items,
+                                                              t->p2p_item_rng, t->p2p_ranges, (float4*)t->near,
+                                                              t->dev_err, t->lim);
     GB_LAUNCH("k_p2p_f2");
     return;
   }
   k_p2p<R, R4><<<t->nleaf, kThreads, 0, s>>>((const R4*)t->work, t->leaves, t->c.bbeg, t->c.bend, t->p2p_rptr,
                                              t->p2p_ranges, (R4*)t->near, t->lim);
   GB_LAUNCH("k_p2p");
+}
+
+// Near-field work items of the single-precision kernel, largest first (no
+// host synchronisation: the item count stays in device memory and the arrays
+// are sized by its bound nleaf + N / kItemTargets).
+void build_p2p_items(fmm_tree* t) {
+  Arena& a = t->arena;
+  cudaStream_t s = t->stream;
+  const int nleaf = (int)t->nleaf;
+  const int64_t nmax = (int64_t)nleaf + t->N / kItemTargets + 1;
+  const unsigned bl = (unsigned)((nleaf + 1 + 255) / 256), bm = (unsigned)((nmax + 255) / 256);
+  int64_t* ptr = alloc_n<int64_t>(a, nleaf + 1);
+  k_item_count<<<bl, 256, 0, s>>>(t->leaves, t->c.bbeg, t->c.bend, nleaf, ptr);
+  GB_LAUNCH("k_item_count");
+  t->p2p_nitem = alloc_n<long long>(a, 1);
+  scan_exclusive_i64_dev(a, ptr, nleaf + 1, (int64_t*)t->p2p_nitem, s);
+  int4* items = alloc_n<int4>(a, nmax);
+  int2* rng = alloc_n<int2>(a, nmax);
+  uint64_t* key = alloc_n<uint64_t>(a, nmax);
+  int32_t* val = alloc_n<int32_t>(a, nmax);
+  k_item_fill<<<bl, 256, 0, s>>>(t->leaves, t->c.bbeg, t->c.bend, t->p2p_rptr, t->p2p_ranges, nleaf, ptr, items,
+                                 rng, key, val);
+  GB_LAUNCH("k_item_fill");
+  k_item_pad<<<bm, 256, 0, s>>>((const int64_t*)t->p2p_nitem, nmax, key, val);
+  GB_LAUNCH("k_item_pad");
+  radix_sort_pairs(a, key, val, nmax, kWorkBits, s);
+  t->p2p_items = alloc_n<int4>(a, nmax);
+  t->p2p_item_rng = alloc_n<int2>(a, nmax);
+  k_item_gather<<<bm, 256, 0, s>>>(val, nmax, items, rng, t->p2p_items, t->p2p_item_rng);
+  GB_LAUNCH("k_item_gather");
+  t->p2p_nitem_max = nmax;
+  a.release(key);
+  a.release(val);
+  a.release(items);
+  a.release(rng);
+  a.release(ptr);
 }
 
 template void launch_p2p<float>(fmm_tree*, cudaStream_t);
