@@ -2,18 +2,22 @@
 // the source leaves of its P2P list (Sec. II.A; Sec. II.C: P2P only needs
 // the neighbours).
 //
-// One block of 128 threads per target leaf (targets in chunks of 256).  Each
-// thread owns two targets (i and i + T2, T2 = ceil(n/2)), so one shared-memory
-// load of a source serves two pairs.  The T2 threads of a target chunk form a
-// group; G = floor(128 / T2) groups split every staged source tile into G
-// contiguous pieces, and the G partial sums are added in a fixed order at the
-// end (results are reproducible).  Sources are streamed through shared
-// memory in tiles of 512 bodies (float4, 16-byte cp.async copies, double
-// buffered): first the leaf's own bodies (masked: self and coincident pairs
-// contribute zero), then the merged neighbour ranges back to back.  Bodies of
-// two different leaves never coincide, so those tiles need no mask.
-// Within a tile each thread sums naively; tile sums are combined with
-// compensated (Kahan) addition.
+// Double precision (k_p2p): one block of 128 threads per target leaf
+// (targets in chunks of 256).  Each thread owns two targets (i and i + T2,
+// T2 = ceil(n/2)), so one shared-memory load of a source serves two pairs.
+// The T2 threads of a target chunk form a group; G = floor(128 / T2) groups
+// split every staged source tile into G contiguous pieces, and the G partial
+// sums are added in a fixed order at the end (results are reproducible).
+// Sources are streamed through shared memory in tiles of 512 bodies (16-byte
+// cp.async copies, double buffered): first the leaf's own bodies (masked:
+// self and coincident pairs contribute zero), then the merged neighbour
+// ranges back to back.  Bodies of two different leaves never coincide, so
+// those tiles need no mask.  Within a tile each thread sums naively; tile
+// sums are combined with compensated (Kahan) addition.
+//
+// Single precision (k_p2p_f2, below): the same per-thread scheme on packed
+// FP32 pairs, one block per work item (a chunk of at most 256 targets of one
+// leaf, largest items first), with bulk-copied source tiles.
 #include <algorithm>
 
 #include "kernels.cuh"
@@ -213,8 +217,7 @@ __global__ void __launch_bounds__(kThreads) k_p2p(const R4* __restrict__ bodies,
 // ---------------------------------------------------------------------------
 // Single precision with packed FP32 pairs (the float2 add/mul/fma of sm_100
 // and later, __fadd2_rn and friends): one instruction evaluates one target
-// against two sources.
-// Sources are read from a pair-major copy of the sorted bodies (k_pair_bodies:
+// against two sources.  Sources are read from a pair-major copy of the sorted bodies (k_pair_bodies:
 // pair m = bodies 2m and 2m + 1 as {x0,x1,y0,y1} {z0,z1,q0,q1}, 32 bytes), so a
 // pair of sources is two 16-byte shared loads and a body range of the
 // neighbour stream is a contiguous run of pairs.  Each run is copied to
@@ -267,7 +270,7 @@ __device__ __forceinline__ void pair2(f2 XX, f2 YY, f2 ZZ, f2 QQ, f2 NX, f2 NY, 
   a.z = f2_fma(f, dz, a.z);
 }
 
-constexpr int kTilePairs = 512;  // source pairs per staged tile (1,024 bodies, 16 KB)
+constexpr int kTilePairs = 448;  // source pairs per staged tile (896 bodies, 14 KB; 7 blocks per SM)
 constexpr int kWindow = 256;     // neighbour ranges staged at a time
 constexpr float kFar = 1e30f;
 
@@ -366,7 +369,7 @@ __device__ __forceinline__ void pad_tile(const Stream& st, int nw, int T0, int T
 template <bool MASK>
 __device__ __forceinline__ void tile_sum2(const SrcPair* __restrict__ tile, int k, int np, int G, f2 X0, f2 Y0,
                                           f2 Z0, f2 X1, f2 Y1, f2 Z1, Acc2& a0, Acc2& a1) {
-#pragma unroll 2
+#pragma unroll 4
   for (; k < np; k += G) {
     const float4 A = *reinterpret_cast<const float4*>(tile[k].w);
     const float4 B = *reinterpret_cast<const float4*>(tile[k].w + 4);
@@ -377,7 +380,9 @@ __device__ __forceinline__ void tile_sum2(const SrcPair* __restrict__ tile, int 
   }
 }
 
-__global__ void __launch_bounds__(kThreads) k_p2p_f2(const float4* __restrict__ bodies,
+// Seven blocks per SM (at most 73 registers a thread): the pair chains are
+// latency-bound, so resident warps count for more than a few spilled values.
+__global__ void __launch_bounds__(kThreads, 7) k_p2p_f2(const float4* __restrict__ bodies,
                                                      const SrcPair* __restrict__ pairs,
                                                      const int4* __restrict__ items,
                                                      const int2* __restrict__ item_rng,
