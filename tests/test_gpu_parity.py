@@ -284,6 +284,17 @@ def test_ragged_tiles_and_deep_tree(fmm, orc):
     assert rel(ph, po) < TOL_PHI and rel(f, -go) < TOL_F
 
 
+@pytest.mark.parametrize("n, ncrit", [(4099, 7), (1201, 600), (2047, 300)])
+def test_odd_sizes_and_multi_chunk_leaves(fmm, orc, n, ncrit):
+    """Odd body counts (the last source pair has one body) and leaves of more
+    than 256 bodies (several near-field work items per leaf, one of them
+    ragged)."""
+    x = W.plummer(n, 29) if ncrit < 64 else W.cube(n, 29)
+    ph, f = evaluate(gpu_tree(fmm, x, 6, 0.5, ncrit))
+    po, go = orc.OracleTree(x, 6, 0.5, ncrit).evaluate()
+    assert rel(ph, po) < TOL_PHI and rel(f, -go) < TOL_F
+
+
 def test_argument_errors(fmm):
     L = fmm.lib()
     x = torch.from_numpy(W.cube(100, 28)).cuda()
