@@ -89,6 +89,7 @@ void create_tree(fmm_tree* t, const R* xyzq) {
   mark(FMM_PH_BUILD_OPS, 1);
   mark(FMM_PH_BUILD_TOTAL, 1);
   GB_CK(cudaStreamSynchronize(s));
+  if (scan_gave_up()) fail(FMM_ERR_CUDA, "a device scan's look-back wait gave up");
   if (t->p2p_nitem)
     GB_CK(cudaMemcpy(&t->p2p_nitem_host, t->p2p_nitem, sizeof(long long), cudaMemcpyDeviceToHost));
   if (timing)

@@ -541,7 +541,17 @@ __global__ void k_item_count(const int32_t* __restrict__ leaves, const int32_t* 
   cnt[li] = (bend[c] - bbeg[c] + kItemTargets - 1) / kItemTargets;
 }
 
-constexpr int kWorkBits = 40;  // targets x sources < 2^40
+// Sort key of an item: its work (targets x sources) in a 16-bit floating
+// form (6-bit exponent, 10-bit mantissa; monotone in the work), inverted so
+// that an ascending sort puts the largest first.  Padding slots take the
+// largest key.
+constexpr int kWorkBits = 16;
+__device__ __forceinline__ uint64_t work_key(uint64_t work) {
+  if (work == 0) return (1ull << kWorkBits) - 1;
+  const int e = 63 - __clzll((long long)work);  // work < 2^63
+  const uint64_t m = (e >= 10 ? work >> (e - 10) : work << (10 - e)) & 0x3ffull;
+  return ((1ull << kWorkBits) - 1) - ((uint64_t)(e + 1) << 10 | m);
+}
 
 __global__ void k_item_fill(const int32_t* __restrict__ leaves, const int32_t* __restrict__ bbeg,
                             const int32_t* __restrict__ bend, const int32_t* __restrict__ rptr,
@@ -561,7 +571,7 @@ __global__ void k_item_fill(const int32_t* __restrict__ leaves, const int32_t* _
     items[idx] = make_int4(t0, nt, s, e);
     rng[idx] = make_int2(r0, r1);
     const uint64_t work = (uint64_t)nt * (uint64_t)src;
-    key[idx] = ((1ull << kWorkBits) - 1) - (work < (1ull << kWorkBits) - 2 ? work : (1ull << kWorkBits) - 2);  // largest first
+    key[idx] = work_key(work);
     val[idx] = (int32_t)idx;
   }
 }

@@ -128,28 +128,9 @@ __device__ int64_t block_exclusive_scan(int64_t v, int64_t* total) {
   return r;
 }
 
-__global__ void k_block_sums(const int64_t* __restrict__ d, int64_t n, int64_t* __restrict__ sums) {
-  const int64_t base = (int64_t)blockIdx.x * kScanTile;
-  int64_t s = 0;
-  for (int i = threadIdx.x; i < kScanTile; i += kScanThreads) {
-    int64_t k = base + i;
-    if (k < n) s += d[k];
-  }
-  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-  __shared__ int64_t ws[kScanThreads / 32];
-  if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = s;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    int64_t t = 0;
-    for (int w = 0; w < kScanThreads / 32; ++w) t += ws[w];
-    sums[blockIdx.x] = t;
-  }
-}
-
-// In-place exclusive scan of one tile per block, plus the block's offset.
-__global__ void k_scan_apply(int64_t* __restrict__ d, int64_t n, const int64_t* __restrict__ offs,
-                             int64_t* __restrict__ total) {
-  const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
+// In-place exclusive scan of at most one tile (a single block).
+__global__ void k_scan_tile(int64_t* __restrict__ d, int64_t n, int64_t* __restrict__ total) {
+  const int64_t base = (int64_t)threadIdx.x * kScanItems;
   int64_t v[kScanItems];
   int64_t s = 0;
 #pragma unroll
@@ -158,8 +139,7 @@ __global__ void k_scan_apply(int64_t* __restrict__ d, int64_t n, const int64_t* 
     s += v[i];
   }
   __shared__ int64_t btotal;
-  int64_t ex = block_exclusive_scan(s, &btotal);
-  int64_t run = ex + (offs ? offs[blockIdx.x] : 0);
+  int64_t run = block_exclusive_scan(s, &btotal);
 #pragma unroll
   for (int i = 0; i < kScanItems; ++i) {
     if (base + i < n) d[base + i] = run;
@@ -168,27 +148,106 @@ __global__ void k_scan_apply(int64_t* __restrict__ d, int64_t n, const int64_t* 
   if (total && threadIdx.x == 0) *total = btotal;
 }
 
+// Single-pass scan (decoupled look-back): each block takes a ticket, scans
+// its tile, publishes the tile's sum, then adds the published values of the
+// tiles before it, walking back until one that already holds its inclusive
+// prefix, and publishes its own.  A block only waits for blocks that took
+// their tickets earlier and never wait for later ones, so every wait ends;
+// the spin is bounded all the same and a wait that gives up raises
+// g_scan_err.
+constexpr unsigned long long kStatAgg = 1ull << 62, kStatInc = 2ull << 62;
+constexpr unsigned long long kValMask = (1ull << 62) - 1;
+constexpr long long kScanSpin = 1ll << 24;
+
+__device__ int g_scan_err;
+
+__device__ __forceinline__ void st_release(unsigned long long* p, unsigned long long v) {
+  asm volatile("st.release.gpu.global.u64 [%0], %1;\n" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ unsigned long long ld_acquire(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];\n" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__global__ void k_scan_onepass(int64_t* __restrict__ d, int64_t n, int64_t* __restrict__ total,
+                               unsigned long long* __restrict__ state, unsigned* __restrict__ ticket) {
+  __shared__ int s_tile;
+  __shared__ int64_t s_prefix, btotal;
+  if (threadIdx.x == 0) s_tile = (int)atomicAdd(ticket, 1u);
+  __syncthreads();
+  const int tile = s_tile;
+  const int64_t base = (int64_t)tile * kScanTile + (int64_t)threadIdx.x * kScanItems;
+  int64_t v[kScanItems];
+  int64_t sum = 0;
+#pragma unroll
+  for (int i = 0; i < kScanItems; ++i) {
+    v[i] = (base + i < n) ? d[base + i] : 0;
+    sum += v[i];
+  }
+  const int64_t ex = block_exclusive_scan(sum, &btotal);
+  if (threadIdx.x == 0) {
+    const int64_t agg = btotal;
+    int64_t prefix = 0;
+    if (tile == 0) {
+      st_release(&state[0], kStatInc | (unsigned long long)agg);
+    } else {
+      st_release(&state[tile], kStatAgg | (unsigned long long)agg);
+      long long spin = 0;
+      for (int j = tile - 1; j >= 0;) {
+        const unsigned long long w = ld_acquire(&state[j]);
+        const unsigned long long st = w & ~kValMask;
+        if (st == 0) {
+          if (++spin > kScanSpin) {
+            g_scan_err = 1;
+            break;
+          }
+          continue;
+        }
+        prefix += (int64_t)(w & kValMask);
+        if (st == kStatInc) break;
+        --j;
+      }
+      st_release(&state[tile], kStatInc | (unsigned long long)(prefix + agg));
+    }
+    s_prefix = prefix;
+    if (total && tile == (int)gridDim.x - 1) *total = prefix + agg;
+  }
+  __syncthreads();
+  int64_t run = ex + s_prefix;
+#pragma unroll
+  for (int i = 0; i < kScanItems; ++i) {
+    if (base + i < n) d[base + i] = run;
+    run += v[i];
+  }
+}
+
 void scan_rec(Arena& a, int64_t* d, int64_t n, int64_t* total, cudaStream_t s) {
   if (n <= 0) {
     if (total) GB_CK(cudaMemsetAsync(total, 0, sizeof(int64_t), s));
     return;
   }
   if (n <= kScanTile) {
-    k_scan_apply<<<1, kScanThreads, 0, s>>>(d, n, nullptr, total);
-    GB_LAUNCH("k_scan_apply");
+    k_scan_tile<<<1, kScanThreads, 0, s>>>(d, n, total);
+    GB_LAUNCH("k_scan_tile");
     return;
   }
   const int64_t nb = (n + kScanTile - 1) / kScanTile;
-  int64_t* sums = alloc_n<int64_t>(a, nb);
-  k_block_sums<<<(unsigned)nb, kScanThreads, 0, s>>>(d, n, sums);
-  GB_LAUNCH("k_block_sums");
-  scan_rec(a, sums, nb, total, s);
-  k_scan_apply<<<(unsigned)nb, kScanThreads, 0, s>>>(d, n, sums, nullptr);
-  GB_LAUNCH("k_scan_apply");
-  a.release(sums);
+  // per-tile state words, then the ticket counter
+  unsigned long long* state = alloc_n<unsigned long long>(a, nb + 1);
+  GB_CK(cudaMemsetAsync(state, 0, sizeof(unsigned long long) * (nb + 1), s));
+  k_scan_onepass<<<(unsigned)nb, kScanThreads, 0, s>>>(d, n, total, state, reinterpret_cast<unsigned*>(state + nb));
+  GB_LAUNCH("k_scan_onepass");
+  a.release(state);
 }
 
 }  // namespace
+
+bool scan_gave_up() {
+  int h = 0;
+  GB_CK(cudaMemcpyFromSymbol(&h, g_scan_err, sizeof(int)));
+  return h != 0;
+}
 
 void scan_exclusive_i64(Arena& a, int64_t* d, int64_t n, cudaStream_t s) {
   scan_rec(a, d, n, nullptr, s);
