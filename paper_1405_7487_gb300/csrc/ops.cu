@@ -491,6 +491,120 @@ __global__ void k_m2l_geom(const int32_t* __restrict__ desc, int n, double* __re
   geom[5 * i + 4] = dl > 0 ? dl : 0;   // log2(R_B / r)
 }
 
+// Single-precision M2L operators (the same entries as k_build_ops).  FP64
+// runs at a small fraction of the FP32 rate on this GPU, so only the
+// harmonics are computed in double (one thread, as above); each is then held
+// as a pair of floats (hi + lo, about 48 bits), and the per-entry work -- the
+// sum of the +m and -m parts, the power-of-two scale and the TF32 split --
+// runs in FP32 on those pairs.  A pair's low part that underflows only drops
+// digits below 2^-126 of the operator.
+struct ff {
+  float h, l;
+};
+__device__ __forceinline__ ff ff_add(ff a, ff b) {
+  const float s = a.h + b.h;
+  const float bb = s - a.h;
+  float e = (a.h - (s - bb)) + (b.h - bb);
+  e += a.l + b.l;
+  const float h = s + e;
+  return ff{h, e - (h - s)};
+}
+__device__ __forceinline__ ff ff_neg(ff a) { return ff{-a.h, -a.l}; }
+
+__device__ __forceinline__ float tf32_rna(float x) {
+  uint32_t b;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(b) : "f"(x));
+  return __uint_as_float(b);
+}
+
+__global__ void k_build_m2l_f32(int p, int Kp, const double* __restrict__ geom, int nops, float* __restrict__ ops,
+                                float* __restrict__ ops_lo, int* __restrict__ range_bad) {
+  extern __shared__ cd X[];  // the (2p - 1)-degree triangle, then its float pairs
+  const int op = blockIdx.x;
+  if (op >= nops) return;
+  const double* g = geom + 5 * (int64_t)op;
+  const int P = 2 * p - 1;
+  const int ntri = P * (P + 1) / 2;
+  float4* Xf = reinterpret_cast<float4*>(X + ntri);  // (re hi, re lo, im hi, im lo)
+  const int eA = (int)g[3], eB = (int)g[4];
+  if (threadIdx.x == 0) irregular_tri(g[0], g[1], g[2], P, X);
+  float* o = ops + (int64_t)op * Kp * Kp;
+  float* olo = ops_lo ? ops_lo + (int64_t)op * Kp * Kp : nullptr;
+  for (int i = threadIdx.x; i < Kp * Kp; i += blockDim.x) {
+    o[i] = 0.0f;
+    if (olo) olo[i] = 0.0f;
+  }
+  __syncthreads();
+  for (int k = threadIdx.x; k < ntri; k += blockDim.x) {
+    const double re = X[k].re, im = X[k].im;
+    const float rh = (float)re, ih = (float)im;
+    Xf[k] = make_float4(rh, (float)(re - (double)rh), ih, (float)(im - (double)ih));
+  }
+  __syncthreads();
+  const int nt = p * (p + 1) / 2;
+  for (int w = threadIdx.x; w < nt * nt; w += blockDim.x) {
+    const int oi = w / nt, ii = w % nt;
+    int a = 0;
+    while ((a + 1) * (a + 2) / 2 <= oi) ++a;
+    const int b = oi - a * (a + 1) / 2;
+    int c = 0;
+    while ((c + 1) * (c + 2) / 2 <= ii) ++c;
+    const int d = ii - c * (c + 1) / 2;
+    const int n = a + c;
+    // X_n^m for -n <= m <= n (X_n^{-m} = (-1)^m conj(X_n^m))
+    auto get = [&](int m, ff& re, ff& im) {
+      const float4 v = Xf[tri(n, m < 0 ? -m : m)];
+      re = ff{v.x, v.y};
+      im = ff{v.z, v.w};
+      if (m < 0) {
+        im = ff_neg(im);
+        if ((-m) & 1) {
+          re = ff_neg(re);
+          im = ff_neg(im);
+        }
+      }
+    };
+    ff vals[4];  // (Re out, Im out) x (Re in, Im in)
+    ff pr, pi;
+    get(d + b, pr, pi);
+    if (d == 0) {
+      vals[0] = pr;
+      vals[1] = ff{0.f, 0.f};
+      vals[2] = pi;
+      vals[3] = ff{0.f, 0.f};
+    } else {
+      ff nr, ni;
+      get(b - d, nr, ni);
+      if (d & 1) {
+        nr = ff_neg(nr);
+        ni = ff_neg(ni);
+      }
+      // input M = u + i v:  cp M + cn (-1)^d conj(M)
+      vals[0] = ff_add(pr, nr);
+      vals[1] = ff_add(ff_neg(pi), ni);
+      vals[2] = ff_add(pi, ni);
+      vals[3] = ff_add(pr, ff_neg(nr));
+    }
+    // (-1)^a 2^(eB (a + 1) + eA c), exact in float
+    const float sc = ldexpf((a & 1) ? -1.0f : 1.0f, eB * (a + 1) + eA * c);
+    const int nout = b == 0 ? 1 : 2, nin = d == 0 ? 1 : 2;
+    for (int po = 0; po < nout; ++po)
+      for (int q = 0; q < nin; ++q) {
+        const ff v = vals[2 * po + q];
+        const float h = v.h * sc, l = v.l * sc;
+        if (!(fabsf(h) <= FLT_MAX)) *range_bad = 1;
+        const int64_t at = (int64_t)ridx(a, b, po) * Kp + ridx(c, d, q);
+        if (olo) {
+          const float hi = tf32_rna(h);
+          o[at] = hi;
+          olo[at] = tf32_rna((h - hi) + l);
+        } else {
+          o[at] = h + l;
+        }
+      }
+  }
+}
+
 }  // namespace
 
 void build_m2l_plan(fmm_tree* t) {
@@ -688,8 +802,8 @@ void build_operators(fmm_tree* t) {
                                                          nullptr, true, bad);
     } else {
       if (t->m2l_engine == 1) t->m2l_ops_lo = alloc_n<float>(a, (size_t)t->nclass * Kp * Kp);
-      k_build_ops<float><<<t->nclass, 256, sm_irr, s>>>(kM2L, p, Kp, geom, t->nclass, (float*)t->m2l_ops,
-                                                        t->m2l_ops_lo, true, bad);
+      const size_t sm_f = sm_irr + sizeof(float4) * (size_t)Pt * (Pt + 1) / 2;
+      k_build_m2l_f32<<<t->nclass, 256, sm_f, s>>>(p, Kp, geom, t->nclass, (float*)t->m2l_ops, t->m2l_ops_lo, bad);
     }
     GB_LAUNCH("k_build_ops m2l");
     a.release(geom);
