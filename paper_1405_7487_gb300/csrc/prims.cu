@@ -150,8 +150,8 @@ __global__ void k_scan_tile(int64_t* __restrict__ d, int64_t n, int64_t* __restr
 
 // Single-pass scan (decoupled look-back): each block takes a ticket, scans
 // its tile, publishes the tile's sum, then adds the published values of the
-// tiles before it, walking back until one that already holds its inclusive
-// prefix, and publishes its own.  A block only waits for blocks that took
+// tiles before it, walking back (32 tiles per step, one per lane of warp 0)
+// until one that already holds its inclusive prefix, and publishes its own.  A block only waits for blocks that took
 // their tickets earlier and never wait for later ones, so every wait ends;
 // the spin is bounded all the same and a wait that gives up raises
 // g_scan_err.
@@ -186,32 +186,46 @@ __global__ void k_scan_onepass(int64_t* __restrict__ d, int64_t n, int64_t* __re
     sum += v[i];
   }
   const int64_t ex = block_exclusive_scan(sum, &btotal);
-  if (threadIdx.x == 0) {
+  if (threadIdx.x < 32) {
+    // warp 0 looks back 32 tiles at a time: lane l reads tile j - l; the
+    // window is usable once every tile up to the nearest inclusive one has
+    // published (tiles before tile 0 count as an inclusive zero)
+    const int lane = threadIdx.x;
     const int64_t agg = btotal;
     int64_t prefix = 0;
     if (tile == 0) {
-      st_release(&state[0], kStatInc | (unsigned long long)agg);
+      if (lane == 0) st_release(&state[0], kStatInc | (unsigned long long)agg);
     } else {
-      st_release(&state[tile], kStatAgg | (unsigned long long)agg);
+      if (lane == 0) st_release(&state[tile], kStatAgg | (unsigned long long)agg);
       long long spin = 0;
       for (int j = tile - 1; j >= 0;) {
-        const unsigned long long w = ld_acquire(&state[j]);
+        const int k = j - lane;
+        const unsigned long long w = k >= 0 ? ld_acquire(&state[k]) : kStatInc;
         const unsigned long long st = w & ~kValMask;
-        if (st == 0) {
+        const unsigned inc = __ballot_sync(0xffffffffu, st == kStatInc);
+        const unsigned avail = __ballot_sync(0xffffffffu, st != 0);
+        const int first = inc ? __ffs(inc) - 1 : 31;
+        const unsigned need = first == 31 ? 0xffffffffu : ((2u << first) - 1u);
+        if ((avail & need) != need) {
           if (++spin > kScanSpin) {
-            g_scan_err = 1;
+            if (lane == 0) g_scan_err = 1;
             break;
           }
           continue;
         }
-        prefix += (int64_t)(w & kValMask);
-        if (st == kStatInc) break;
-        --j;
+        int64_t part = lane <= first ? (int64_t)(w & kValMask) : 0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) part += __shfl_down_sync(0xffffffffu, part, o);
+        prefix += __shfl_sync(0xffffffffu, part, 0);
+        if (inc) break;
+        j -= 32;
       }
-      st_release(&state[tile], kStatInc | (unsigned long long)(prefix + agg));
+      if (lane == 0) st_release(&state[tile], kStatInc | (unsigned long long)(prefix + agg));
     }
-    s_prefix = prefix;
-    if (total && tile == (int)gridDim.x - 1) *total = prefix + agg;
+    if (lane == 0) {
+      s_prefix = prefix;
+      if (total && tile == (int)gridDim.x - 1) *total = prefix + agg;
+    }
   }
   __syncthreads();
   int64_t run = ex + s_prefix;
