@@ -172,6 +172,7 @@ def run_gpu(args):
     stream = torch.cuda.current_stream(dev)
 
     extra = F.FMM_FLAG_MUTUAL_P2P if args.p2p == "mutual" else 0
+    extra |= {"half": 0, "circ": F.FMM_FLAG_CIRCUMSCRIBED, "tight": F.FMM_FLAG_TIGHT_MAC}[args.mac]
 
     def step(flags=F.FMM_FLAG_TIMING):
         T = F.Tree(x, p, theta, ncrit, flags | extra)
@@ -287,7 +288,8 @@ def run_gpu(args):
         "config": {"workload": args.workload, "distribution": spec["dist"], "N": N, "p": p, "theta": theta,
                    "ncrit": ncrit, "step": "fmm_build + fmm_evaluate (pot, force) + fmm_backward",
                    "l2": "flushed between timed steps (512 MiB write)", "parallelism": f"replicas x{world}",
-                   **({"p2p": "mutual"} if args.p2p == "mutual" else {})},
+                   **({"p2p": "mutual"} if args.p2p == "mutual" else {}),
+                   **({"mac": args.mac} if args.mac != "half" else {})},
         "e2e": e2e, "gpu_launches": int(launches), "roofline": roofline,
         "p2p_frac_fp32_peak": round(p2p_tf_iso / fp32_peak_tflops, 4),
         # P2P span in the timed steps, where it shares the GPU with M2L
@@ -460,6 +462,8 @@ def main():
     ap.add_argument("--sweep", default=None, choices=["precision"],
                     help="precision/scale sweep (cube16m: FP32 vs all-FP64 at p = 4..16), JSON lines")
     ap.add_argument("--sweep-max-p-f64", type=int, default=16, help="largest p of the double path in the sweep")
+    ap.add_argument("--mac", default="half", choices=["half", "circ", "tight"],
+                    help="MAC radius: half side of the cube (default), half diagonal, or particle-fitted")
     ap.add_argument("--p2p", default="one-sided", choices=["one-sided", "mutual"],
                     help="near field: one block per target leaf, or mutual interaction")
     args = ap.parse_args()

@@ -70,9 +70,14 @@ enum {
   FMM_FLAG_SERIAL_PHASES = 1u << 4, /* run the near field on the caller's stream after the
                                        far field instead of concurrently on a second stream
                                        (with FMM_FLAG_TIMING: each phase timed alone) */
-  FMM_FLAG_MUTUAL_P2P = 1u << 5     /* near field by mutual interaction: each unordered leaf
+  FMM_FLAG_MUTUAL_P2P = 1u << 5,    /* near field by mutual interaction: each unordered leaf
                                        pair visited once, both leaves updated (floating-point
                                        atomics: results are not bit-reproducible) */
+  FMM_FLAG_TIGHT_MAC = 1u << 6      /* MAC radius of a cell = the distance from its (cube)
+                                       centre to its farthest body, from the 21-bit integer
+                                       body coordinates (Sec. II.B's particle-fitted bound;
+                                       expansion centres stay the cube centres); overrides
+                                       FMM_FLAG_CIRCUMSCRIBED */
 };
 
 /* Optional stream-ordered allocator.  NULL selects the library's memory pool

@@ -93,14 +93,15 @@ class OracleTree:
     xyzq: (N, 4) array of x, y, z, q (any float dtype, widened to double).
     """
 
-    def __init__(self, xyzq, p: int, theta: float, ncrit: int, circumscribed: bool = False):
+    def __init__(self, xyzq, p: int, theta: float, ncrit: int, circumscribed: bool = False,
+                 tight: bool = False):
         L = lib()
         self.xyzq = _f64(xyzq).reshape(-1, 4)
         self.N = self.xyzq.shape[0]
         self.p = int(p)
         h = ctypes.c_void_p()
         rc = L.orc_build(_dp(self.xyzq), self.N, self.p, float(theta), int(ncrit),
-                         1 if circumscribed else 0, ctypes.byref(h))
+                         (1 if circumscribed else 0) | (2 if tight else 0), ctypes.byref(h))
         if rc != 0:
             raise ValueError(f"oracle build failed with code {rc}")
         self._h = h

@@ -240,6 +240,8 @@ struct Tree {
   double theta = 0;
   int ncrit = 0;
   int circumscribed = 0;
+  int tight = 0;                         // particle-fitted MAC radius (Sec. II.B)
+  std::vector<int64_t> r2;               // its square per cell (tight only)
   double lo[3], hi[3], ctr[3], H = 0, r0[3];
   std::vector<double> xyz, q;            // input order (3N, N)
   std::vector<uint64_t> key_sorted;      // keys in sorted order
@@ -357,12 +359,43 @@ void build_cells(Tree& t) {
 // Multipole acceptance criterion, theta * |c_A - c_B| > R_A + R_B, evaluated
 // on exact integers: centres are (2k+1) 2^(21-l) and radii 2^(21-l) in units
 // of H / 2^21 (R = half side; the circumscribed radius multiplies by sqrt 3).
+//
+// Particle-fitted variant (tight): the radius of a cell is the distance from
+// its centre to its farthest body, in the same units, each body at the centre
+// 2u + 1 of its voxel u (its 21-bit integer coordinate).  The squared radius
+// is an exact integer; the test is theta^2 D^2 > (sqrt(r2_A) + sqrt(r2_B))^2
+// in IEEE double (square roots correctly rounded, no contraction).
+void tight_radii(Tree& t) {
+  const int n = (int)t.level.size();
+  t.r2.assign(n, 0);
+  for (int c = 0; c < n; ++c) {
+    const int sh = MAXLEVEL - t.level[c];
+    const int64_t ctr[3] = {(2ll * t.ix[c] + 1) << sh, (2ll * t.iy[c] + 1) << sh, (2ll * t.iz[c] + 1) << sh};
+    int64_t best = 0;
+    for (int i = t.bbeg[c]; i < t.bend[c]; ++i) {
+      const uint64_t k = t.key_sorted[i];
+      const int64_t u[3] = {(int64_t)gather3(k >> 2), (int64_t)gather3(k >> 1), (int64_t)gather3(k)};
+      int64_t d2 = 0;
+      for (int a = 0; a < 3; ++a) {
+        const int64_t d = 2 * u[a] + 1 - ctr[a];
+        d2 += d * d;
+      }
+      best = std::max(best, d2);
+    }
+    t.r2[c] = best;
+  }
+}
+
 bool mac(const Tree& t, int A, int B) {
   const int la = t.level[A], lb = t.level[B];
   int64_t dx = ((2ll * t.ix[A] + 1) << (MAXLEVEL - la)) - ((2ll * t.ix[B] + 1) << (MAXLEVEL - lb));
   int64_t dy = ((2ll * t.iy[A] + 1) << (MAXLEVEL - la)) - ((2ll * t.iy[B] + 1) << (MAXLEVEL - lb));
   int64_t dz = ((2ll * t.iz[A] + 1) << (MAXLEVEL - la)) - ((2ll * t.iz[B] + 1) << (MAXLEVEL - lb));
   int64_t D2 = dx * dx + dy * dy + dz * dz;
+  if (t.tight) {
+    const double sr = std::sqrt((double)t.r2[A]) + std::sqrt((double)t.r2[B]);
+    return (t.theta * t.theta) * (double)D2 > sr * sr;
+  }
   int64_t rs = (1ll << (MAXLEVEL - la)) + (1ll << (MAXLEVEL - lb));
   int64_t S2 = rs * rs;
   if (t.circumscribed) S2 *= 3;
@@ -556,7 +589,8 @@ int orc_set_threads(int n) {
 }
 
 // xyzq: N x 4 doubles (x, y, z, q) in input order.
-int orc_build(const double* xyzq, int64_t N, int p, double theta, int ncrit, int circumscribed,
+// mac: bit 0 circumscribed radius, bit 1 particle-fitted (tight) radius.
+int orc_build(const double* xyzq, int64_t N, int p, double theta, int ncrit, int mac_mode,
               void** out) {
   if (!xyzq || !out || N < 1 || p < 1 || p > 30 || !(theta > 0.0) || ncrit < 1) return -1;
   if (N > 2147483647ll) return -1;
@@ -567,7 +601,8 @@ int orc_build(const double* xyzq, int64_t N, int p, double theta, int ncrit, int
   t->p = p;
   t->theta = theta;
   t->ncrit = ncrit;
-  t->circumscribed = circumscribed ? 1 : 0;
+  t->circumscribed = (mac_mode & 1) ? 1 : 0;
+  t->tight = (mac_mode & 2) ? 1 : 0;
   t->xyz.resize(3 * N);
   t->q.resize(N);
   for (int64_t i = 0; i < N; ++i) {
@@ -586,6 +621,7 @@ int orc_build(const double* xyzq, int64_t N, int p, double theta, int ncrit, int
   t->key_sorted.resize(N);
   for (int64_t i = 0; i < N; ++i) t->key_sorted[i] = key_in[t->perm[i]];
   build_cells(*t);
+  if (t->tight) tight_radii(*t);
   Traversal tr(*t);
   tr.visit(0, 0);
   const int ncell = (int)t->level.size();

@@ -14,7 +14,12 @@
 //           which case split the other; equal sizes, both split-table: every
 //           (child of A, child of B) pair.
 // The MAC is evaluated on exact integers (cube centres and radii in units of
-// H / 2^21), so the lists are reproducible bit for bit.
+// H / 2^21), so the lists are reproducible bit for bit.  With
+// FMM_FLAG_TIGHT_MAC a cell's radius is instead the distance from its centre
+// to its farthest body (the particle-fitted bound of Sec. II.B, the centre
+// kept): its square is an exact integer over the bodies' 21-bit coordinates,
+// and the test is theta^2 D^2 > (sqrt(r2_A) + sqrt(r2_B))^2 in correctly
+// rounded double operations, the same on every device.
 #include <algorithm>
 
 #include "common.cuh"
@@ -27,6 +32,7 @@ inline unsigned blocks(int64_t n) { return (unsigned)((n + kThreads - 1) / kThre
 
 struct CellView {
   const int32_t *level, *ix, *iy, *iz, *cbeg, *nch;
+  const long long* r2;  // FMM_FLAG_TIGHT_MAC: squared particle-fitted radius per cell, else null
 };
 
 __device__ __forceinline__ bool mac(const CellView& c, int A, int B, double theta2, int circ) {
@@ -35,6 +41,10 @@ __device__ __forceinline__ bool mac(const CellView& c, int A, int B, double thet
   const int64_t dy = ((2ll * c.iy[A] + 1) << (kMaxLevel - la)) - ((2ll * c.iy[B] + 1) << (kMaxLevel - lb));
   const int64_t dz = ((2ll * c.iz[A] + 1) << (kMaxLevel - la)) - ((2ll * c.iz[B] + 1) << (kMaxLevel - lb));
   const int64_t D2 = dx * dx + dy * dy + dz * dz;
+  if (c.r2) {
+    const double sr = __dadd_rn(__dsqrt_rn((double)c.r2[A]), __dsqrt_rn((double)c.r2[B]));
+    return __dmul_rn(theta2, (double)D2) > __dmul_rn(sr, sr);
+  }
   const int64_t rs = (1ll << (kMaxLevel - la)) + (1ll << (kMaxLevel - lb));
   int64_t S2 = rs * rs;
   if (circ) S2 *= 3;
@@ -234,6 +244,43 @@ __global__ void k_upair_write(const int32_t* __restrict__ tgt, const int32_t* __
   if (i < n && src[i] < tgt[i]) up[off[i]] = make_int2(src[i], tgt[i]);
 }
 
+// Squared particle-fitted radius of every cell: the largest squared distance
+// from the cell centre (2k + 1) 2^(21 - l) to a body's voxel centre 2u + 1,
+// per axis in units of H / 2^21, u the body's 21-bit coordinate (read back
+// from its sorted Morton key).  One block per cell.
+__device__ __forceinline__ int64_t compact3(uint64_t v) {
+  v &= 0x1249249249249249ull;
+  v = (v | (v >> 2)) & 0x10c30c30c30c30c3ull;
+  v = (v | (v >> 4)) & 0x100f00f00f00f00full;
+  v = (v | (v >> 8)) & 0x1f0000ff0000ffull;
+  v = (v | (v >> 16)) & 0x1f00000000ffffull;
+  v = (v | (v >> 32)) & 0x1fffffull;
+  return (int64_t)v;
+}
+
+__global__ void k_cell_r2(const uint64_t* __restrict__ keys, const int32_t* __restrict__ level,
+                          const int32_t* __restrict__ ix, const int32_t* __restrict__ iy,
+                          const int32_t* __restrict__ iz, const int32_t* __restrict__ bbeg,
+                          const int32_t* __restrict__ bend, long long* __restrict__ r2) {
+  const int c = blockIdx.x;
+  const int sh = kMaxLevel - level[c];
+  const int64_t cx = (2ll * ix[c] + 1) << sh, cy = (2ll * iy[c] + 1) << sh, cz = (2ll * iz[c] + 1) << sh;
+  long long m = 0;
+  for (int i = bbeg[c] + threadIdx.x; i < bend[c]; i += blockDim.x) {
+    const uint64_t k = keys[i];
+    const int64_t dx = 2 * compact3(k >> 2) + 1 - cx, dy = 2 * compact3(k >> 1) + 1 - cy, dz = 2 * compact3(k) + 1 - cz;
+    m = max(m, (long long)(dx * dx + dy * dy + dz * dz));
+  }
+  for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_down_sync(0xffffffffu, m, o));
+  __shared__ long long wm[32];
+  if ((threadIdx.x & 31) == 0) wm[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) m = max(m, wm[w]);
+    r2[c] = m;
+  }
+}
+
 }  // namespace
 
 // Smallest b with 2^b > v.
@@ -259,7 +306,14 @@ void sort_pairs_copy(Arena& a, const int32_t* tgt, const int32_t* src, int64_t n
 void build_lists(fmm_tree* t) {
   Arena& a = t->arena;
   cudaStream_t s = t->stream;
-  CellView cv{t->c.level, t->c.ix, t->c.iy, t->c.iz, t->c.cbeg, t->c.nch};
+  long long* r2 = nullptr;
+  if (t->flags & FMM_FLAG_TIGHT_MAC) {
+    r2 = alloc_n<long long>(a, t->ncell);
+    k_cell_r2<<<(unsigned)t->ncell, 128, 0, s>>>(t->keys, t->c.level, t->c.ix, t->c.iy, t->c.iz, t->c.bbeg,
+                                                t->c.bend, r2);
+    GB_LAUNCH("k_cell_r2");
+  }
+  CellView cv{t->c.level, t->c.ix, t->c.iy, t->c.iz, t->c.cbeg, t->c.nch, r2};
   const double theta2 = t->theta * t->theta;
   const int circ = (t->flags & FMM_FLAG_CIRCUMSCRIBED) ? 1 : 0;
 
@@ -315,6 +369,7 @@ void build_lists(fmm_tree* t) {
   }
   a.release(fr);
   a.release(d_seg);
+  if (r2) a.release(r2);
 
   // The pairs stay in traversal order (deterministic: every offset comes from
   // an exclusive scan); only the inspection call sorts a copy by (target,

@@ -52,12 +52,13 @@ CASES = {
 # ------------------------------------------------------------ structure
 
 @pytest.mark.parametrize("name", ["cube4k_p4", "plummer60k_p8", "sphere40k_p6"])
-@pytest.mark.parametrize("circ", [False, True])
-def test_tree_and_lists_bit_identical(fmm, orc, name, circ):
+@pytest.mark.parametrize("mac", ["half", "circ", "tight"])
+def test_tree_and_lists_bit_identical(fmm, orc, name, mac):
     gen, p, theta, ncrit = CASES[name]
     x = gen()
-    T = gpu_tree(fmm, x, p, theta, ncrit, fmm.FMM_FLAG_CIRCUMSCRIBED if circ else 0)
-    O = orc.OracleTree(x, p, theta, ncrit, circumscribed=circ)
+    flags = {"half": 0, "circ": fmm.FMM_FLAG_CIRCUMSCRIBED, "tight": fmm.FMM_FLAG_TIGHT_MAC}[mac]
+    T = gpu_tree(fmm, x, p, theta, ncrit, flags)
+    O = orc.OracleTree(x, p, theta, ncrit, circumscribed=mac == "circ", tight=mac == "tight")
     r_g, r_o = T.root(), O.root()
     for k in ("lo", "hi", "centre", "corner"):
         assert np.array_equal(r_g[k], r_o[k])
@@ -119,6 +120,26 @@ def test_forward_matches_oracle(fmm, orc, name):
     po, go = orc.OracleTree(x, p, theta, ncrit).evaluate()
     assert rel(ph, po) < TOL_PHI
     assert rel(f, -go) < TOL_F
+
+
+@pytest.mark.parametrize("name,f64", [("cube65k_p10", False), ("plummer60k_p8", False), ("sphere40k_p6", False),
+                                      ("cube4k_p4", True)])
+def test_tight_mac_matches_oracle(fmm, orc, name, f64):
+    """Particle-fitted MAC radius (row f3, centres kept): outputs against the
+    oracle built with the same MAC, forward and backward."""
+    gen, p, theta, ncrit = CASES[name]
+    x = gen()
+    T = gpu_tree(fmm, x, p, theta, ncrit, fmm.FMM_FLAG_TIGHT_MAC, f64=f64)
+    ph, f = evaluate(T)
+    O = orc.OracleTree(x, p, theta, ncrit, tight=True)
+    po, go = O.evaluate()
+    tp, tf = (TOL64_PHI, TOL64_F) if f64 else (TOL_PHI, TOL_F)
+    assert rel(ph, po) < tp and rel(f, -go) < tf
+    w = W.weights(x.shape[0], 31)
+    dq, dx = T.backward(torch.from_numpy(np.asarray(w, np.float64 if f64 else np.float32)).cuda())
+    torch.cuda.synchronize()
+    dqo, dxo = O.backward(np.asarray(w, np.float64))
+    assert rel(dq.double().cpu().numpy(), dqo) < tp and rel(dx.double().cpu().numpy(), dxo) < tf
 
 
 @pytest.mark.parametrize("name,f64", [("cube65k_p10", False), ("plummer60k_p8", False), ("sphere40k_p6", False),

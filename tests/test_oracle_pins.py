@@ -298,6 +298,48 @@ def test_traversal_covers_every_pair_exactly_once(orc):
         assert 0.6 * d > (1 << (21 - R[t])) + (1 << (21 - R[s]))
 
 
+def test_tight_mac_covers_every_pair_once_and_bounds_hold(orc):
+    """Particle-fitted MAC radius about the cube centre (Sec. II.B's tight
+    bound): every body pair is still covered exactly once, and every M2L pair
+    satisfies theta |c_A - c_B| > r_A + r_B, r the true distance from the
+    centre to the farthest body (up to the voxel quantisation of the radii)."""
+    x = W.plummer(1500, 52)
+    theta = 0.6
+    T = orc.OracleTree(x, 4, theta, 8, tight=True)
+    c = T.cells()
+    L = T.lists()
+    r = T.root()
+    N = x.shape[0]
+    bb, be = c["body_begin"], c["body_end"]
+    cnt = np.zeros((N, N), np.int32)
+    for t, s in zip(L["p2p_tgt"], L["p2p_src"]):
+        cnt[bb[t]:be[t], bb[s]:be[s]] += 1
+    for t, s in zip(L["m2l_tgt"], L["m2l_src"]):
+        cnt[bb[t]:be[t], bb[s]:be[s]] += 1
+    assert np.all(cnt == 1)
+    _, perm = T.keys()
+    u = (np.asarray(x, np.float64)[perm, :3] - r["corner"]) * (2.0 ** 21 / r["H"])  # units of H / 2^21
+    lev = c["level"].astype(np.int64)
+    ijk = np.stack([c["ix"], c["iy"], c["iz"]], 1).astype(np.int64)
+    ctr = ((2 * ijk + 1) << (21 - lev)[:, None]).astype(np.float64)
+    rad = np.array([np.sqrt(((u[bb[i]:be[i]] - ctr[i]) ** 2).sum(1).max()) for i in range(lev.size)])
+    assert np.all(rad <= np.sqrt(3.0) * np.ldexp(1.0, 21 - lev) + 1e-9)  # inside the cube
+    slack = 2.0 * np.sqrt(3.0)  # a body sits at most one unit per axis from its voxel centre
+    for t, s in zip(L["m2l_tgt"], L["m2l_src"]):
+        d = np.sqrt(((ctr[t] - ctr[s]) ** 2).sum())
+        assert theta * d > rad[t] + rad[s] - slack
+    # the bound is tighter than the circumscribed sphere: fewer body pairs go to P2P
+    C = orc.OracleTree(x, 4, theta, 8, circumscribed=True)
+    assert T.info()["p2p_pairs"] < C.info()["p2p_pairs"]
+
+
+def test_tight_mac_error_decreases_with_p(orc):
+    x = W.plummer(3000, 53)
+    pd, _ = orc.direct(x)
+    e = [rel(orc.OracleTree(x, p, 0.5, 16, tight=True).evaluate()[0], pd) for p in (3, 5, 7, 9)]
+    assert all(b < a for a, b in zip(e, e[1:]))
+
+
 def test_coincident_bodies_contribute_zero(orc):
     x = W.cube(300, 61)
     x[10, :3] = x[20, :3]
