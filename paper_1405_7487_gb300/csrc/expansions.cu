@@ -29,6 +29,54 @@ __device__ __forceinline__ void cell_geom(const double* __restrict__ root, int l
   c[2] = root[12] + (2.0 * iz + 1.0) * R;
 }
 
+// The root cube as float pairs (corner hi + lo per axis, H hi + lo, 1/H),
+// set up on the host from the double root box.
+struct RootF {
+  float ch[3], cl[3], hh, hl, ih;
+};
+
+// The frame of one cell for its bodies: the scaled offset (x - c) / R and
+// 1/R.  The double path works in double.  The single path uses no FP64 (it
+// runs at a small fraction of the FP32 rate): the centre c = corner +
+// (2k + 1) R, R = H 2^-level, is formed as a float pair (an exact product
+// by FMA and a compensated sum), and an offset is (x - c_hi) - c_lo in FP32
+// -- x - c_hi is exact wherever the cell is at least its own size away from
+// the origin, and small otherwise -- scaled by 1/R = 2^level / H in float.
+template <class R>
+struct Frame {
+  double c[3], inv;
+  __device__ void init(const double* __restrict__ root, const RootF&, int level, int ix, int iy, int iz) {
+    double Rc;
+    cell_geom(root, level, ix, iy, iz, c, Rc);
+    inv = 1.0 / Rc;
+  }
+  __device__ __forceinline__ R operator()(R x, int a) const { return (R)(((double)x - c[a]) * inv); }
+  __device__ __forceinline__ R inv_r() const { return (R)inv; }
+};
+template <>
+struct Frame<float> {
+  float hi[3], lo[3], inv;
+  __device__ void init(const double* __restrict__, const RootF& g, int level, int ix, int iy, int iz) {
+    const float rh = ldexpf(g.hh, -level), rl = ldexpf(g.hl, -level);
+    const int k3[3] = {ix, iy, iz};
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const float k = (float)(2 * k3[a] + 1);  // < 2^22: exact
+      const float p = k * rh;
+      const float pe = fmaf(k, rh, -p) + k * rl;  // the product's low part
+      const float s = g.ch[a] + p;
+      const float bb = s - g.ch[a];
+      const float se = (g.ch[a] - (s - bb)) + (p - bb);  // the sum's rounding error
+      const float l = se + pe + g.cl[a];
+      hi[a] = s + l;
+      lo[a] = l - (hi[a] - s);
+    }
+    inv = ldexpf(g.ih, level);
+  }
+  __device__ __forceinline__ float operator()(float x, int a) const { return ((x - hi[a]) - lo[a]) * inv; }
+  __device__ __forceinline__ float inv_r() const { return inv; }
+};
+
 template <class R, class R4>
 __global__ void k_set_charges(const R4* __restrict__ bodies, const int32_t* __restrict__ perm,
                               const R* __restrict__ q, int64_t n, R4* __restrict__ work, Lim lim) {
@@ -48,7 +96,8 @@ __global__ void k_p2m(const R4* __restrict__ work, const int32_t* __restrict__ l
                       const int32_t* __restrict__ level, const int32_t* __restrict__ ix,
                       const int32_t* __restrict__ iy, const int32_t* __restrict__ iz,
                       const int32_t* __restrict__ bbeg, const int32_t* __restrict__ bend,
-                      const double* __restrict__ root, int p, int Kp, R* __restrict__ M, Lim lim) {
+                      const double* __restrict__ root, RootF rootf, int p, int Kp, R* __restrict__ M,
+                      Lim lim) {
   const int lane = threadIdx.x & 31;
   const int li = blockIdx.x * kWarps + (threadIdx.x >> 5);
   if (li >= nleaf) return;
@@ -56,10 +105,9 @@ __global__ void k_p2m(const R4* __restrict__ work, const int32_t* __restrict__ l
 #ifdef GBFMM_CHECKED
   if (!in_range(cell, lim.ncell, 311, lim.rec)) return;
 #endif
-  double c[3], Rc;
-  cell_geom(root, level[cell], ix[cell], iy[cell], iz[cell], c, Rc);
+  Frame<R> off;
+  off.init(root, rootf, level[cell], ix[cell], iy[cell], iz[cell]);
   const int s = bbeg[cell], e = bend[cell];
-  const double inv_r = 1.0 / Rc;
   const int h = lane >> 4, m = lane & 15;
   R ar[kMaxP], ai[kMaxP], rf[kMaxP];
   // per-lane constants of column m: 1 / ((n+1+m)(n+1-m)) for n = m + k, and
@@ -75,9 +123,9 @@ __global__ void k_p2m(const R4* __restrict__ work, const int32_t* __restrict__ l
     R bx = 0, by = 0, bz = 0, bq = 0;
     if (j0 + lane < e) {
       R4 b = GB_LD(work, j0 + lane, lim.N, 312);
-      bx = (R)(((double)b.x - c[0]) * inv_r);
-      by = (R)(((double)b.y - c[1]) * inv_r);
-      bz = (R)(((double)b.z - c[2]) * inv_r);
+      bx = off(b.x, 0);
+      by = off(b.y, 1);
+      bz = off(b.z, 2);
       bq = b.w;
     }
     const int cnt = min(32, e - j0);
@@ -204,7 +252,8 @@ __global__ void k_l2p_finalize(const R4* __restrict__ work, const int32_t* __res
                                const int32_t* __restrict__ level, const int32_t* __restrict__ ix,
                                const int32_t* __restrict__ iy, const int32_t* __restrict__ iz,
                                const int32_t* __restrict__ bbeg, const int32_t* __restrict__ bend,
-                               const double* __restrict__ root, int p, int Kp, const R* __restrict__ L,
+                               const double* __restrict__ root, RootF rootf, int p, int Kp,
+                               const R* __restrict__ L,
                                const R4* __restrict__ near, const int32_t* __restrict__ perm, int mode,
                                R* __restrict__ out_a, R* __restrict__ out_b, R4* __restrict__ grad_q,
                                R* __restrict__ q_last, Lim lim) {
@@ -228,16 +277,15 @@ __global__ void k_l2p_finalize(const R4* __restrict__ work, const int32_t* __res
 #endif
   for (int i = lane; i < p * p; i += 32) Ls[i] = GB_LD(L, (int64_t)cell * Kp + i, lim.ncell * lim.Kp, 342);
   __syncwarp();
-  double c[3], Rc;
-  cell_geom(root, level[cell], ix[cell], iy[cell], iz[cell], c, Rc);
-  const double inv_rd = 1.0 / Rc;
-  const R inv_r = (R)inv_rd;
+  Frame<R> off;
+  off.init(root, rootf, level[cell], ix[cell], iy[cell], iz[cell]);
+  const R inv_r = off.inv_r();
   const int s = bbeg[cell], e = bend[cell];
   for (int i = s + lane; i < e; i += 32) {
     const R4 b = GB_LD(work, i, lim.N, 343);
-    const R x = (R)(((double)b.x - c[0]) * inv_rd);
-    const R y = (R)(((double)b.y - c[1]) * inv_rd);
-    const R z = (R)(((double)b.z - c[2]) * inv_rd);
+    const R x = off(b.x, 0);
+    const R y = off(b.y, 1);
+    const R z = off(b.z, 2);
     const R r2 = x * x + y * y + z * z;
     R ph = 0, gx = 0, gy = 0, gz = 0;
     R dr = 1, di = 0;  // Ups_m^m
@@ -317,6 +365,21 @@ inline unsigned blocks(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
 }  // namespace
 
+namespace {
+// The root cube's corner and half side as float pairs.
+RootF root_f(const fmm_tree* t) {
+  RootF g;
+  for (int a = 0; a < 3; ++a) {
+    g.ch[a] = (float)t->root.corner[a];
+    g.cl[a] = (float)(t->root.corner[a] - (double)g.ch[a]);
+  }
+  g.hh = (float)t->root.H;
+  g.hl = (float)(t->root.H - (double)g.hh);
+  g.ih = (float)(1.0 / t->root.H);
+  return g;
+}
+}  // namespace
+
 template <class R>
 void launch_set_charges(fmm_tree* t, const R* q, cudaStream_t s) {
   using R4 = typename Vec4<R>::type;
@@ -329,7 +392,7 @@ void launch_p2m(fmm_tree* t, cudaStream_t s) {
   using R4 = typename Vec4<R>::type;
   k_p2m<R, R4><<<blocks(t->nleaf, kWarps), 32 * kWarps, 0, s>>>(
       (const R4*)t->work, t->leaves, t->nleaf, t->c.level, t->c.ix, t->c.iy, t->c.iz, t->c.bbeg, t->c.bend,
-      t->d_root, t->p, t->Kp, (R*)t->M, t->lim);
+      t->d_root, root_f(t), t->p, t->Kp, (R*)t->M, t->lim);
   GB_LAUNCH("k_p2m");
 }
 
@@ -359,7 +422,7 @@ void launch_l2p_finalize(fmm_tree* t, int mode, R* a, R* b, cudaStream_t s) {
   k_l2p_finalize<R, R4><<<blocks(t->nleaf, kWarps), 32 * kWarps,
                           sizeof(R) * (kMaxP * kMaxP + kMaxP + kWarps * t->Kp), s>>>(
       (const R4*)t->work, t->leaves, t->nleaf, t->c.level, t->c.ix, t->c.iy, t->c.iz, t->c.bbeg, t->c.bend,
-      t->d_root, t->p, t->Kp, (const R*)t->L, (const R4*)t->near, t->perm, mode, a, b, (R4*)t->grad_q,
+      t->d_root, root_f(t), t->p, t->Kp, (const R*)t->L, (const R4*)t->near, t->perm, mode, a, b, (R4*)t->grad_q,
       (R*)t->q_last, t->lim);
   GB_LAUNCH("k_l2p_finalize");
 }
