@@ -87,10 +87,11 @@ __global__ void k_set_charges(const R4* __restrict__ bodies, const int32_t* __re
   work[i] = b;
 }
 
-// P2M: one warp per leaf.  The warp loads 32 bodies at a time (offsets from
-// the centre formed in double, then scaled by 1/R and rounded); lane m (of
-// each half warp) owns column m of the expansion and runs the recurrence
-// over n, the two half warps taking alternate bodies.
+// P2M: one warp per leaf.  The warp loads 32 bodies at a time (their scaled
+// offsets from the centre, see Frame); the lanes form G = floor(32 / p)
+// groups of p, lane m of a group owns column m of the expansion and runs the
+// recurrence over n, and the groups take bodies in turn (G bodies per step).
+// The groups' sums are added in group order at the end.
 template <class R, class R4>
 __global__ void k_p2m(const R4* __restrict__ work, const int32_t* __restrict__ leaves, int nleaf,
                       const int32_t* __restrict__ level, const int32_t* __restrict__ ix,
@@ -108,7 +109,9 @@ __global__ void k_p2m(const R4* __restrict__ work, const int32_t* __restrict__ l
   Frame<R> off;
   off.init(root, rootf, level[cell], ix[cell], iy[cell], iz[cell]);
   const int s = bbeg[cell], e = bend[cell];
-  const int h = lane >> 4, m = lane & 15;
+  const int G = 32 / p;  // p <= 16: at least two groups
+  const int g = lane / p, m = lane - g * p;
+  const bool grp = g < G;
   R ar[kMaxP], ai[kMaxP], rf[kMaxP];
   // per-lane constants of column m: 1 / ((n+1+m)(n+1-m)) for n = m + k, and
   // the diagonal factor 1 / (2^m m!)
@@ -130,13 +133,13 @@ __global__ void k_p2m(const R4* __restrict__ work, const int32_t* __restrict__ l
     }
     const int cnt = min(32, e - j0);
     // the trip count is warp-uniform: every lane takes part in every shuffle
-    for (int jb = 0; jb < cnt; jb += 2) {
-      const int jj = jb + h;
-      const bool ok = jj < cnt;
+    for (int jb = 0; jb < cnt; jb += G) {
+      const int jj = jb + g;
+      const bool ok = grp && jj < cnt;
       const int sl = ok ? jj : 0;
       const R x = __shfl_sync(0xffffffffu, bx, sl), y = __shfl_sync(0xffffffffu, by, sl);
       const R z = __shfl_sync(0xffffffffu, bz, sl), q = __shfl_sync(0xffffffffu, bq, sl);
-      if (!ok || m >= p) continue;
+      if (!ok) continue;
       // diagonal Ups_m^m = (-(x + i y))^m / (2^m m!)
       R ur = dfac, ui = 0;
       for (int k = 1; k <= m; ++k) {
@@ -167,12 +170,19 @@ __global__ void k_p2m(const R4* __restrict__ work, const int32_t* __restrict__ l
       }
     }
   }
+  // group 0 adds the other groups' sums in order (lane + j p < 32 for its lanes)
+  for (int j = 1; j < G; ++j) {
+    const int src = min(lane + j * p, 31);
 #pragma unroll
-  for (int k = 0; k < kMaxP; ++k) {
-    ar[k] += __shfl_xor_sync(0xffffffffu, ar[k], 16);
-    ai[k] += __shfl_xor_sync(0xffffffffu, ai[k], 16);
+    for (int k = 0; k < kMaxP; ++k) {
+      const R vr = __shfl_sync(0xffffffffu, ar[k], src), vi = __shfl_sync(0xffffffffu, ai[k], src);
+      if (g == 0) {
+        ar[k] += vr;
+        ai[k] += vi;
+      }
+    }
   }
-  if (h == 0 && m < p) {
+  if (g == 0) {
     R* out = M + (int64_t)cell * Kp;
 #pragma unroll
     for (int k = 0; k < kMaxP; ++k) {
