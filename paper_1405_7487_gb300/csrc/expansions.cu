@@ -92,8 +92,9 @@ __global__ void k_set_charges(const R4* __restrict__ bodies, const int32_t* __re
 // groups of p, lane m of a group owns column m of the expansion and runs the
 // recurrence over n, and the groups take bodies in turn (G bodies per step).
 // The groups' sums are added in group order at the end.
+// Six blocks per SM (at most 80 registers a thread, a few spilled values).
 template <class R, class R4>
-__global__ void k_p2m(const R4* __restrict__ work, const int32_t* __restrict__ leaves, int nleaf,
+__global__ void __launch_bounds__(32 * kWarps, 6) k_p2m(const R4* __restrict__ work, const int32_t* __restrict__ leaves, int nleaf,
                       const int32_t* __restrict__ level, const int32_t* __restrict__ ix,
                       const int32_t* __restrict__ iy, const int32_t* __restrict__ iz,
                       const int32_t* __restrict__ bbeg, const int32_t* __restrict__ bend,
