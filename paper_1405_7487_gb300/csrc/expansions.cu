@@ -310,36 +310,45 @@ __global__ void k_l2p_finalize(const R4* __restrict__ work, const int32_t* __res
       }
       const R wm = m == 0 ? (R)1 : (R)2;
       R ur = dr, ui = di, pr = 0, pi = 0;
+      // packed offsets of columns m, m - 1 and m + 1 within a degree (ridx),
+      // the running n^2 and 2n + 1 (the latter also as a float)
+      const int c0 = m ? 2 * m - 1 : 0, cm = m >= 2 ? 2 * m - 3 : 0, cp = 2 * m + 1;
+      int sq = m * m, c = 2 * m + 1;
+      R cf = (R)c;
       for (int n = m; n < p; ++n) {
         // Re(L conj U) = Lr Ur + Li Ui ; Im(L conj U) = Li Ur - Lr Ui
         {
-          const R lr = Ls[ridx(n, m, 0)], lim = m ? Ls[ridx(n, m, 1)] : (R)0;
+          const R lr = Ls[sq + c0], lim = m ? Ls[sq + c0 + 1] : (R)0;
           ph += wm * (lr * ur + lim * ui);
         }
+        const int sq1 = sq + c;  // (n + 1)^2
         if (n + 1 < p) {
           {
-            const R lr = Ls[ridx(n + 1, m, 0)], lim = m ? Ls[ridx(n + 1, m, 1)] : (R)0;
+            const R lr = Ls[sq1 + c0], lim = m ? Ls[sq1 + c0 + 1] : (R)0;
             gz += wm * (lr * ur + lim * ui);
           }
           if (m >= 1) {
-            const R lr = Ls[ridx(n + 1, m - 1, 0)], lim = (m - 1) ? Ls[ridx(n + 1, m - 1, 1)] : (R)0;
+            const R lr = Ls[sq1 + cm], lim = (m - 1) ? Ls[sq1 + cm + 1] : (R)0;
             gx += lr * ur + lim * ui;
             gy -= lim * ur - lr * ui;
           }
           {
-            const R lr = Ls[ridx(n + 1, m + 1, 0)], lim = Ls[ridx(n + 1, m + 1, 1)];
+            const R lr = Ls[sq1 + cp], lim = Ls[sq1 + cp + 1];
             gx -= lr * ur + lim * ui;
             gy -= lim * ur - lr * ui;
           }
         }
         const R f = rtab[m * kMaxP + n];
-        const R a = (R)(2 * n + 1) * z;
+        const R a = cf * z;
         const R nr = (a * ur - r2 * pr) * f;
         const R ni = (a * ui - r2 * pi) * f;
         pr = ur;
         pi = ui;
         ur = nr;
         ui = ni;
+        sq = sq1;
+        c += 2;
+        cf += (R)2;
       }
     }
     const R4 nf = GB_LD(near, i, lim.N, 344);
