@@ -56,7 +56,8 @@ void scan_exclusive_i64(Arena& a, int64_t* d, int64_t n, cudaStream_t s);
 // the total is left in device memory (no host synchronisation)
 void scan_exclusive_i64_dev(Arena& a, int64_t* d, int64_t n, int64_t* total_dev, cudaStream_t s);
 int64_t scan_exclusive_i64_total(Arena& a, int64_t* d, int64_t n, cudaStream_t s);
-// true once a single-pass scan's bounded look-back wait has given up
+// true if a single-pass scan's bounded look-back wait has given up since the
+// last call (the flag is cleared when read)
 bool scan_gave_up();
 
 // LSD radix sort of (key, value) pairs on bits [0, bits) of the key; stable.

@@ -260,6 +260,10 @@ void scan_rec(Arena& a, int64_t* d, int64_t n, int64_t* total, cudaStream_t s) {
 bool scan_gave_up() {
   int h = 0;
   GB_CK(cudaMemcpyFromSymbol(&h, g_scan_err, sizeof(int)));
+  if (h) {
+    const int zero = 0;
+    GB_CK(cudaMemcpyToSymbol(g_scan_err, &zero, sizeof(int)));  // reported once
+  }
   return h != 0;
 }
 
