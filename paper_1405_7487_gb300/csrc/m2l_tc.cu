@@ -556,26 +556,39 @@ __global__ void k_m2l_reduce4(const int32_t* __restrict__ tile_tgt, const int32_
   const int q = tile / kQuad, lq = tile % kQuad;
   const int c0 = quad_cptr[q], c1 = quad_cptr[q + 1];
   const int64_t cstride = (int64_t)kQuad * Kp * kTile;  // floats between chunks
-  for (int w = threadIdx.x; w < kTile * K; w += blockDim.x) {
-    const int c = w / kTile, r = w % kTile;
-    const int tgt = tile_tgt[(int64_t)tile * kTile + r];
-    if (tgt < 0) continue;
+  // thread per (coefficient, four consecutive rows): 16-byte loads of the
+  // column-major partials, four compensated sums side by side
+  for (int w = threadIdx.x; w < (kTile / 4) * K; w += blockDim.x) {
+    const int c = w / (kTile / 4), r = 4 * (w % (kTile / 4));
+    const int4 tg = *reinterpret_cast<const int4*>(tile_tgt + (int64_t)tile * kTile + r);
+    if ((tg.x & tg.y & tg.z & tg.w) < 0) continue;  // all four rows empty
     const float* pp = part + ((int64_t)lq * Kp + c) * kTile + r;
-    float sum = 0.f, comp = 0.f;
+    float4 sum = make_float4(0.f, 0.f, 0.f, 0.f), comp = sum;
+    auto kahan = [](float& sm, float& cm, float v) {
+      const float y = v - cm;
+      const float tt = sm + y;
+      cm = (tt - sm) - y;
+      sm = tt;
+    };
     for (int b = c0; b < c1; b += 8) {
-      float v[8];
+      float4 v[8];
 #pragma unroll
-      for (int k = 0; k < 8; ++k) v[k] = b + k < c1 ? __ldcs(pp + (int64_t)(b + k) * cstride) : 0.f;
+      for (int k = 0; k < 8; ++k)
+        v[k] = b + k < c1 ? __ldcs(reinterpret_cast<const float4*>(pp + (int64_t)(b + k) * cstride))
+                          : make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
       for (int k = 0; k < 8; ++k) {
         if (b + k >= c1) break;
-        const float y = v[k] - comp;
-        const float tt = sum + y;
-        comp = (tt - sum) - y;
-        sum = tt;
+        kahan(sum.x, comp.x, v[k].x);
+        kahan(sum.y, comp.y, v[k].y);
+        kahan(sum.z, comp.z, v[k].z);
+        kahan(sum.w, comp.w, v[k].w);
       }
     }
-    L[(int64_t)tgt * Kp + c] = sum;
+    if (tg.x >= 0) L[(int64_t)tg.x * Kp + c] = sum.x;
+    if (tg.y >= 0) L[(int64_t)tg.y * Kp + c] = sum.y;
+    if (tg.z >= 0) L[(int64_t)tg.z * Kp + c] = sum.z;
+    if (tg.w >= 0) L[(int64_t)tg.w * Kp + c] = sum.w;
   }
 }
 
