@@ -21,6 +21,7 @@
 // and the test is theta^2 D^2 > (sqrt(r2_A) + sqrt(r2_B))^2 in correctly
 // rounded double operations, the same on every device.
 #include <algorithm>
+#include <climits>
 
 #include "common.cuh"
 
@@ -151,45 +152,77 @@ __global__ void k_unpack_pairs(const uint64_t* __restrict__ k, int64_t n, int32_
   src[i] = (int32_t)(k[i] & 0xffffffffu);
 }
 
-// P2P source ranges per target leaf: key (leaf index, body_begin of source),
-// self pairs dropped (the kernel treats a leaf's own bodies separately).
-__global__ void k_p2p_range_keys(const int32_t* __restrict__ tgt, const int32_t* __restrict__ src,
-                                 int64_t n, const int32_t* __restrict__ leaf_of,
-                                 const int32_t* __restrict__ bbeg, int nb, uint64_t* __restrict__ key,
-                                 int32_t* __restrict__ val, unsigned long long* __restrict__ pairs,
-                                 const int32_t* __restrict__ bend) {
+// P2P source lists by target leaf: a counting sort by leaf, then each leaf's
+// sources in body order (their body ranges are disjoint, so the order is
+// unique).  Count pass: non-self pairs per leaf, and the body-pair total.
+__global__ void k_p2p_leaf_count(const int32_t* __restrict__ tgt, const int32_t* __restrict__ src, int64_t n,
+                                 const int32_t* __restrict__ leaf_of, const int32_t* __restrict__ bbeg,
+                                 const int32_t* __restrict__ bend, int64_t* __restrict__ cnt,
+                                 unsigned long long* __restrict__ pairs) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  // body-pair count: warp sums, one atomic per warp
   unsigned long long np = 0;
   if (i < n) np = (unsigned long long)(bend[tgt[i]] - bbeg[tgt[i]]) * (unsigned long long)(bend[src[i]] - bbeg[src[i]]);
   for (int o = 16; o > 0; o >>= 1) np += __shfl_down_sync(0xffffffffu, np, o);
   if ((threadIdx.x & 31) == 0 && np) atomicAdd(pairs, np);
-  if (i >= n) return;
-  const int t = tgt[i], s = src[i];
-  if (t == s) {
-    key[i] = ~0ull;  // sorts last, ignored
-    val[i] = -1;
-    return;
-  }
-  key[i] = ((uint64_t)(uint32_t)leaf_of[t] << nb) | (uint32_t)bbeg[s];
-  val[i] = s;
+  if (i < n && tgt[i] != src[i]) atomicAdd(reinterpret_cast<unsigned long long*>(&cnt[leaf_of[tgt[i]]]), 1ull);
 }
 
-// Position of the first key >= (leaf << nb) for every leaf (and the end);
-// keys are compared on their low `bits` bits (the sorted ones).
-__global__ void k_leaf_entry_ptr(const uint64_t* __restrict__ key, int64_t n, int nleaf, int nb, int bits,
-                                 int64_t* __restrict__ ptr) {
-  const int l = blockIdx.x * blockDim.x + threadIdx.x;
-  if (l > nleaf) return;
-  const uint64_t mask = bits >= 64 ? ~0ull : ((1ull << bits) - 1);
-  const uint64_t want = (uint64_t)(uint32_t)l << nb;
-  int64_t lo = 0, hi = n;
-  while (lo < hi) {
-    int64_t mid = (lo + hi) >> 1;
-    if ((key[mid] & mask) < want) lo = mid + 1;
-    else hi = mid;
+__global__ void k_p2p_leaf_scatter(const int32_t* __restrict__ tgt, const int32_t* __restrict__ src, int64_t n,
+                                   const int32_t* __restrict__ leaf_of, const int64_t* __restrict__ ptr,
+                                   int32_t* __restrict__ cursor, int32_t* __restrict__ val) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n || tgt[i] == src[i]) return;
+  const int l = leaf_of[tgt[i]];
+  val[ptr[l] + atomicAdd(&cursor[l], 1)] = src[i];
+}
+
+// One block per leaf: its sources ordered by body begin, from `in` to `out`.
+// Up to kSegSort entries a bitonic sort in shared memory; longer lists (none
+// at the workloads here) rank each entry by counting the smaller ones.
+constexpr int kSegSort = 1024;
+__global__ void k_p2p_leaf_sort(const int64_t* __restrict__ ptr, int nleaf, const int32_t* __restrict__ bbeg,
+                                const int32_t* __restrict__ in, int32_t* __restrict__ out) {
+  __shared__ int sk[kSegSort], sv[kSegSort];
+  const int l = blockIdx.x;
+  if (l >= nleaf) return;
+  const int64_t b = ptr[l];
+  const int L = (int)(ptr[l + 1] - b);
+  if (L <= kSegSort) {
+    int n2 = 1;
+    while (n2 < L) n2 <<= 1;
+    for (int i = threadIdx.x; i < n2; i += blockDim.x) {
+      const bool ok = i < L;
+      const int v = ok ? in[b + i] : -1;
+      sv[i] = v;
+      sk[i] = ok ? bbeg[v] : INT_MAX;
+    }
+    __syncthreads();
+    for (int k = 2; k <= n2; k <<= 1)
+      for (int j = k >> 1; j > 0; j >>= 1) {
+        for (int i = threadIdx.x; i < n2; i += blockDim.x) {
+          const int x = i ^ j;
+          if (x > i) {
+            const bool up = (i & k) == 0;
+            if ((sk[i] > sk[x]) == up) {
+              const int tk = sk[i], tv = sv[i];
+              sk[i] = sk[x];
+              sv[i] = sv[x];
+              sk[x] = tk;
+              sv[x] = tv;
+            }
+          }
+        }
+        __syncthreads();
+      }
+    for (int i = threadIdx.x; i < L; i += blockDim.x) out[b + i] = sv[i];
+  } else {
+    for (int i = threadIdx.x; i < L; i += blockDim.x) {
+      const int v = in[b + i], key = bbeg[v];
+      int r = 0;
+      for (int j = 0; j < L; ++j) r += bbeg[in[b + j]] < key;
+      out[b + r] = v;
+    }
   }
-  ptr[l] = lo;
 }
 
 // Merge adjacent body ranges of one target leaf; count pass (out == null)
@@ -390,21 +423,26 @@ void build_lists(fmm_tree* t) {
   a.release(p2p);
 
   // --- P2P body ranges per target leaf, merged where contiguous
-  uint64_t* rkey = alloc_n<uint64_t>(a, np);
-  int32_t* rval = alloc_n<int32_t>(a, np);
   unsigned long long* d_pairs = alloc_n<unsigned long long>(a, 1);
   GB_CK(cudaMemsetAsync(d_pairs, 0, sizeof(unsigned long long), s));
-  // key = (leaf, body_begin) in lb + nb bits; 2^lb > nleaf and 2^nb > N, so a
-  // real key is never the all-ones key of a self pair
-  const int nb = bits_for(t->N), lb = bits_for(t->nleaf);
-  k_p2p_range_keys<<<blocks(np), kThreads, 0, s>>>(t->p2p_tgt, t->p2p_src, np, t->leaf_of_cell,
-                                                   t->c.bbeg, nb, rkey, rval, d_pairs, t->c.bend);
-  GB_LAUNCH("k_p2p_range_keys");
-  radix_sort_pairs(a, rkey, rval, np, lb + nb, s);
   int64_t* eptr = alloc_n<int64_t>(a, t->nleaf + 1);
-  k_leaf_entry_ptr<<<blocks(t->nleaf + 1), kThreads, 0, s>>>(rkey, np, t->nleaf, nb, lb + nb, eptr);
-  GB_LAUNCH("k_leaf_entry_ptr");
-  // the self entries (key ~0) sort last; cap the last leaf at the non-self count
+  GB_CK(cudaMemsetAsync(eptr, 0, sizeof(int64_t) * (t->nleaf + 1), s));
+  k_p2p_leaf_count<<<blocks(np), kThreads, 0, s>>>(t->p2p_tgt, t->p2p_src, np, t->leaf_of_cell, t->c.bbeg,
+                                                   t->c.bend, eptr, d_pairs);
+  GB_LAUNCH("k_p2p_leaf_count");
+  scan_exclusive_i64(a, eptr, t->nleaf + 1, s);
+  int32_t* cursor = alloc_n<int32_t>(a, t->nleaf);
+  GB_CK(cudaMemsetAsync(cursor, 0, sizeof(int32_t) * t->nleaf, s));
+  int32_t* rtmp = alloc_n<int32_t>(a, np);
+  k_p2p_leaf_scatter<<<blocks(np), kThreads, 0, s>>>(t->p2p_tgt, t->p2p_src, np, t->leaf_of_cell, eptr, cursor,
+                                                     rtmp);
+  GB_LAUNCH("k_p2p_leaf_scatter");
+  int32_t* rval = alloc_n<int32_t>(a, np);
+  k_p2p_leaf_sort<<<(unsigned)t->nleaf, 128, 0, s>>>(eptr, (int)t->nleaf, t->c.bbeg, rtmp, rval);
+  GB_LAUNCH("k_p2p_leaf_sort");
+  a.release(cursor);
+  a.release(rtmp);
+  // per leaf: the number of merged ranges, then the ranges
   int64_t* rcount = alloc_n<int64_t>(a, t->nleaf + 1);
   GB_CK(cudaMemsetAsync(rcount, 0, sizeof(int64_t) * (t->nleaf + 1), s));
   k_merge_ranges<<<blocks(t->nleaf), kThreads, 0, s>>>(eptr, rval, t->c.bbeg, t->c.bend, t->nleaf,
@@ -423,7 +461,6 @@ void build_lists(fmm_tree* t) {
   GB_CK(cudaStreamSynchronize(s));
   t->p2p_body_pairs = (int64_t)hp - t->N;
   a.release(d_pairs);
-  a.release(rkey);
   a.release(rval);
   a.release(eptr);
   a.release(rcount);
