@@ -316,6 +316,28 @@ def test_odd_sizes_and_multi_chunk_leaves(fmm, orc, n, ncrit):
     assert rel(ph, po) < TOL_PHI and rel(f, -go) < TOL_F
 
 
+def test_long_neighbour_lists(fmm, orc):
+    """theta = 0.1 and one body per leaf: about 1,000 target leaves with more
+    than 1,024 source leaves (the long-list path of the per-leaf source sort)
+    and 345 with more than 256 merged ranges (several staged range windows in
+    the single-precision near field)."""
+    x = W.cube(4000, 33)
+    T = gpu_tree(fmm, x, 2, 0.1, 1)
+    O = orc.OracleTree(x, 2, 0.1, 1)
+    lg, lo = T.lists(), O.lists()
+    for k in lo:
+        assert np.array_equal(lg[k], lo[k]), k
+    P = T.plan()
+    rp, rg = P["p2p_rptr"], P["p2p_ranges"]
+    assert np.diff(rp).max() > 256
+    for li in range(rp.shape[0] - 1):
+        r = rg[rp[li]:rp[li + 1]]
+        assert np.all(r[1:, 0] > r[:-1, 1])  # ascending, disjoint and merged
+    ph, f = evaluate(T)
+    po, go = O.evaluate()
+    assert rel(ph, po) < TOL_PHI and rel(f, -go) < TOL_F
+
+
 def test_argument_errors(fmm):
     L = fmm.lib()
     x = torch.from_numpy(W.cube(100, 28)).cuda()
