@@ -308,7 +308,7 @@ def run_gpu(args):
         "clocks": clk,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_baseline(args.workload, steps=1)
+        out["cpu_baseline"] = cpu_baseline(args.workload, steps=1, mac=args.mac)
     if rank == 0:
         print(json.dumps(out), flush=True)
     if world > 1:
@@ -317,10 +317,10 @@ def run_gpu(args):
 
 # ---------------------------------------------------------- oracle (CPU)
 
-def cpu_baseline(workload: str, steps: int) -> dict:
+def cpu_baseline(workload: str, steps: int, mac: str = "half") -> dict:
     """The double-precision oracle, as it stands, on the host cores: a bounded
     sample (the first CPU_SAMPLE_N bodies of the same workload, same p, theta,
-    ncrit); each step = oracle build + forward + backward."""
+    ncrit and MAC radius); each step = oracle build + forward + backward."""
     import numpy as np
 
     import oracle
@@ -332,7 +332,8 @@ def cpu_baseline(workload: str, steps: int) -> dict:
     w = W.weights(x.shape[0], spec.get("wseed", 40)).astype(np.float64)
     t0 = time.perf_counter()
     for _ in range(steps):
-        T = oracle.OracleTree(x, spec["p"], spec["theta"], spec["ncrit"])
+        T = oracle.OracleTree(x, spec["p"], spec["theta"], spec["ncrit"], circumscribed=mac == "circ",
+                              tight=mac == "tight")
         T.backward(w)  # evaluates with q (forward) and with w (adjoint)
         del T
     dt = time.perf_counter() - t0
@@ -437,8 +438,8 @@ def run_reference(args):
     from paper_1405_7487_gb300 import workloads as W
     spec = W.WORKLOADS[args.workload]
     for _ in range(args.warmup):
-        cpu_baseline(args.workload, 1)
-    cb = cpu_baseline(args.workload, args.steps)
+        cpu_baseline(args.workload, 1, args.mac)
+    cb = cpu_baseline(args.workload, args.steps, args.mac)
     out = {"metric": METRIC, "value": cb["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": CPU_SAMPLE_N / cb["value"] * 1e3, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
@@ -447,6 +448,8 @@ def run_reference(args):
                       "step": "oracle build + forward + backward"},
            "cpu_baseline": cb,
            "e2e": {"value": cb["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    if args.mac != "half":
+        out["config"]["mac"] = args.mac
     print(json.dumps(out), flush=True)
 
 
