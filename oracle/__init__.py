@@ -32,42 +32,60 @@ _I32 = ctypes.POINTER(ctypes.c_int32)
 _U64 = ctypes.POINTER(ctypes.c_uint64)
 
 
+def compile_library(src: str, out: str) -> None:
+    """Compile an oracle source file into a shared library (g++, OpenMP, no FMA
+    contraction: the tree build's floating-point steps must round as written)."""
+    cmd = ["g++", "-O2", "-std=c++17", "-fopenmp", "-ffp-contract=off", "-fPIC",
+           "-shared", "-o", out, src]
+    subprocess.run(cmd, check=True)
+
+
 def build(force: bool = False) -> str:
-    """Compile the oracle shared library (g++, OpenMP, no FMA contraction)."""
+    """Compile the oracle shared library next to its source when it is stale."""
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + f".{os.getpid()}.tmp"
-        cmd = ["g++", "-O2", "-std=c++17", "-fopenmp", "-ffp-contract=off", "-fPIC",
-               "-shared", "-o", tmp, _SRC]
-        subprocess.run(cmd, check=True)
+        compile_library(_SRC, tmp)
         os.replace(tmp, _LIB)
     return _LIB
+
+
+def use_library(path: str) -> None:
+    """Make this module call another build of the oracle's source.  The
+    mutation tests plant one mistake in a copy of ``fmm_oracle.cpp``, build it
+    with :func:`compile_library` and run the pins against it through here."""
+    global _lib
+    _lib = _load(path)
 
 
 def lib():
     global _lib
     if _lib is None:
         build()
-        L = ctypes.CDLL(_LIB)
-        L.orc_set_threads.argtypes = [ctypes.c_int]
-        L.orc_build.argtypes = [_D, ctypes.c_int64, ctypes.c_int, ctypes.c_double, ctypes.c_int,
-                                ctypes.c_int, ctypes.POINTER(ctypes.c_void_p)]
-        L.orc_free.argtypes = [ctypes.c_void_p]
-        L.orc_free.restype = None
-        L.orc_info.argtypes = [ctypes.c_void_p, _I64]
-        L.orc_root.argtypes = [ctypes.c_void_p, _D]
-        L.orc_keys.argtypes = [ctypes.c_void_p, _U64, _I64]
-        L.orc_cells.argtypes = [ctypes.c_void_p, _I32]
-        L.orc_lists.argtypes = [ctypes.c_void_p, _I32, _I32, _I32, _I32]
-        L.orc_evaluate.argtypes = [ctypes.c_void_p, _D, _D, ctypes.c_int, ctypes.c_int64, _I64, _D, _D]
-        L.orc_expansions.argtypes = [ctypes.c_void_p, _D, _D]
-        L.orc_backward.argtypes = [ctypes.c_void_p, _D, _D, _D, _D]
-        L.orc_direct.argtypes = [_D, ctypes.c_int64, ctypes.c_int64, _I64, _D, _D]
-        L.orc_op_p2m.argtypes = [ctypes.c_int, _D, ctypes.c_int, _D, _D]
-        for name in ("orc_op_m2m", "orc_op_m2l", "orc_op_l2l", "orc_op_l2p", "orc_op_m2p"):
-            getattr(L, name).argtypes = [ctypes.c_int, _D, _D, _D, _D]
-        L.orc_harmonics.argtypes = [ctypes.c_int, _D, _D, _D]
-        _lib = L
+        _lib = _load(_LIB)
     return _lib
+
+
+def _load(path: str):
+    L = ctypes.CDLL(path)
+    L.orc_set_threads.argtypes = [ctypes.c_int]
+    L.orc_build.argtypes = [_D, ctypes.c_int64, ctypes.c_int, ctypes.c_double, ctypes.c_int,
+                            ctypes.c_int, ctypes.POINTER(ctypes.c_void_p)]
+    L.orc_free.argtypes = [ctypes.c_void_p]
+    L.orc_free.restype = None
+    L.orc_info.argtypes = [ctypes.c_void_p, _I64]
+    L.orc_root.argtypes = [ctypes.c_void_p, _D]
+    L.orc_keys.argtypes = [ctypes.c_void_p, _U64, _I64]
+    L.orc_cells.argtypes = [ctypes.c_void_p, _I32]
+    L.orc_lists.argtypes = [ctypes.c_void_p, _I32, _I32, _I32, _I32]
+    L.orc_evaluate.argtypes = [ctypes.c_void_p, _D, _D, ctypes.c_int, ctypes.c_int64, _I64, _D, _D]
+    L.orc_expansions.argtypes = [ctypes.c_void_p, _D, _D]
+    L.orc_backward.argtypes = [ctypes.c_void_p, _D, _D, _D, _D]
+    L.orc_direct.argtypes = [_D, ctypes.c_int64, ctypes.c_int64, _I64, _D, _D]
+    L.orc_op_p2m.argtypes = [ctypes.c_int, _D, ctypes.c_int, _D, _D]
+    for name in ("orc_op_m2m", "orc_op_m2l", "orc_op_l2l", "orc_op_l2p", "orc_op_m2p"):
+        getattr(L, name).argtypes = [ctypes.c_int, _D, _D, _D, _D]
+    L.orc_harmonics.argtypes = [ctypes.c_int, _D, _D, _D]
+    return L
 
 
 def set_threads(n: int = 0) -> int:

@@ -340,6 +340,56 @@ def test_tight_mac_error_decreases_with_p(orc):
     assert all(b < a for a, b in zip(e, e[1:]))
 
 
+def _deinterleave(keys, shift):
+    u = np.zeros(keys.shape, np.int64)
+    for b in range(21):
+        u |= ((keys >> np.uint64(3 * b + shift)) & np.uint64(1)).astype(np.int64) << b
+    return u
+
+
+@pytest.mark.parametrize("mode", ["half", "circumscribed", "tight"])
+def test_lists_follow_the_acceptance_criterion(orc, mode):
+    """Sec. II.A/C: a pair of cells goes to M2L exactly when it is far enough
+    for its sizes.  Every M2L pair passes theta |c_A - c_B| > R_A + R_B and every
+    P2P pair of two distinct leaves fails it, with the radii derived here from
+    the geometry (units of H / 2^21): the half side 2^(21-l); the distance from
+    the centre to a corner of the cube (the circumscribed sphere); the distance
+    to the farthest voxel centre 2u + 1 of the cell's bodies (particle-fitted)."""
+    x = W.plummer(2000, 54)
+    theta = 0.55
+    T = orc.OracleTree(x, 4, theta, 6, circumscribed=mode == "circumscribed", tight=mode == "tight")
+    c = T.cells()
+    L = T.lists()
+    lev = c["level"].astype(np.int64)
+    ijk = np.stack([c["ix"], c["iy"], c["iz"]], 1).astype(np.int64)
+    half = np.left_shift(np.int64(1), 21 - lev)
+    ctr = (2 * ijk + 1) * half[:, None]
+    if mode == "tight":
+        keys, _ = T.keys()
+        u = np.stack([_deinterleave(keys, 2), _deinterleave(keys, 1), _deinterleave(keys, 0)], 1)
+        vox = 2 * u + 1
+        bb, be = c["body_begin"], c["body_end"]
+        r2 = np.array([int(((vox[bb[i]:be[i]] - ctr[i]) ** 2).sum(1).max()) for i in range(lev.size)])
+        rad = [math.sqrt(float(v)) for v in r2]
+    # a corner of the cube, (h, h, h) from its centre, is sqrt(3) h away
+    k2 = 3 if mode == "circumscribed" else 1
+
+    def accepted(a, b):
+        d = ctr[a] - ctr[b]
+        D2 = int(d @ d)
+        if mode == "tight":
+            s = rad[a] + rad[b]
+            return (theta * theta) * float(D2) > s * s
+        # (R_A + R_B)^2 = k^2 (h_A + h_B)^2, exact in integers
+        return (theta * theta) * float(D2) > float(k2 * (int(half[a]) + int(half[b])) ** 2)
+
+    assert len(L["m2l_tgt"]) > 0
+    assert all(accepted(t, s) for t, s in zip(L["m2l_tgt"], L["m2l_src"]))
+    far_p2p = [(t, s) for t, s in zip(L["p2p_tgt"], L["p2p_src"]) if t != s]
+    assert len(far_p2p) > 0
+    assert not any(accepted(t, s) for t, s in far_p2p)
+
+
 def test_coincident_bodies_contribute_zero(orc):
     x = W.cube(300, 61)
     x[10, :3] = x[20, :3]
