@@ -338,6 +338,7 @@ def cpu_baseline(workload: str, steps: int, mac: str = "half") -> dict:
         del T
     dt = time.perf_counter() - t0
     return {"value": x.shape[0] * steps / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "bodies": int(x.shape[0]),
             "sample": f"first {x.shape[0]} bodies of {workload}, same p/theta/ncrit; "
                       f"build + forward + backward, {steps} step(s), {dt:.2f} s"}
 
@@ -441,9 +442,9 @@ def run_reference(args):
         cpu_baseline(args.workload, 1, args.mac)
     cb = cpu_baseline(args.workload, args.steps, args.mac)
     out = {"metric": METRIC, "value": cb["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
-           "warmup": args.warmup, "ms_per_step": CPU_SAMPLE_N / cb["value"] * 1e3, "higher_is_better": True,
+           "warmup": args.warmup, "ms_per_step": cb["bodies"] / cb["value"] * 1e3, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-           "config": {"workload": args.workload, "distribution": spec["dist"], "N": CPU_SAMPLE_N,
+           "config": {"workload": args.workload, "distribution": spec["dist"], "N": cb["bodies"],
                       "p": spec["p"], "theta": spec["theta"], "ncrit": spec["ncrit"],
                       "step": "oracle build + forward + backward"},
            "cpu_baseline": cb,

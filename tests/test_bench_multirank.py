@@ -66,3 +66,32 @@ def test_reference_arm_other_ranks_exit_without_work(monkeypatch, capsys):
 
     bench.run_reference(A())
     assert capsys.readouterr().out == ""
+
+
+@pytest.mark.parametrize("mac", ["half", "tight"])
+def test_reference_arm_line_on_rank0(monkeypatch, capsys, mac):
+    # rank 0 times the oracle on the host and prints one JSON line of the
+    # benchmark's schema, with the e2e block of a host-only program
+    import json
+    monkeypatch.setenv("RANK", "0")
+    monkeypatch.setenv("WORLD_SIZE", "1")
+
+    class A:
+        workload, steps, warmup = "cube4k_p4", 2, 1
+
+    A.mac = mac
+    bench.run_reference(A())
+    lines = [ln for ln in capsys.readouterr().out.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+              "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert k in d
+    assert d["impl"] == "reference" and d["value"] > 0 and d["steps"] == 2 and d["warmup"] == 1
+    assert d["config"]["workload"] == "cube4k_p4" and d["config"]["N"] == 4096
+    assert d["config"].get("mac", "half") == mac
+    assert d["ms_per_step"] == pytest.approx(4096 / d["value"] * 1e3)
+    cb = d["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"]
+    assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": 0}
