@@ -136,7 +136,7 @@ typedef struct {
  *   theta  opening angle of the MAC  theta * |c_A - c_B| > R_A + R_B,
  *          0 < theta < 1.
  *   ncrit  a cell with more than ncrit bodies is split (up to level 21).
- *   flags  FMM_FLAG_* bits.
+ *   flags  FMM_FLAG_* bits; any other bit is FMM_ERR_ARG.
  *   alloc  NULL or a stream-ordered allocator (used for all workspace).
  *   stream the stream all work is ordered on; the call synchronises it.
  *   out    host; receives the new tree handle (NULL on failure).

@@ -97,12 +97,16 @@ void create_tree(fmm_tree* t, const R* xyzq) {
       cudaEventElapsedTime(&t->ms[ph], t->ev[2 * ph], t->ev[2 * ph + 1]);
 }
 
+constexpr uint32_t kKnownFlags = FMM_FLAG_CIRCUMSCRIBED | FMM_FLAG_TIMING | FMM_FLAG_M2L_CUDA_CORE |
+                                 FMM_FLAG_SORTED_PLAN | FMM_FLAG_SERIAL_PHASES | FMM_FLAG_MUTUAL_P2P |
+                                 FMM_FLAG_TIGHT_MAC;
+
 template <class R>
 int build_common(const R* xyzq, int64_t n, int p, double theta, int ncrit, uint32_t flags,
                  const fmm_allocator* alloc, fmm_stream stream, fmm_tree** out) {
   if (out) *out = nullptr;
   if (!xyzq || !out || n < 1 || n > 0x7fffffffll || p < 1 || p > kMaxP || !(theta > 0.0) ||
-      !(theta < 1.0) || ncrit < 1)
+      !(theta < 1.0) || ncrit < 1 || (flags & ~kKnownFlags))
     return FMM_ERR_ARG;
   if (alloc && (!alloc->alloc || !alloc->free)) return FMM_ERR_ARG;
   fmm_tree* t = new (std::nothrow) fmm_tree();

@@ -63,3 +63,35 @@ def test_product_does_not_import_the_oracle():
             if f.endswith((".py", ".cu", ".cuh", ".h")):
                 txt = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in txt and "from oracle" not in txt and "fmm_oracle" not in txt, f
+
+
+def test_build_arguments_checked_before_any_gpu_work(libpath):
+    # every rejected argument returns FMM_ERR_ARG (-1) before a CUDA call, so
+    # this runs without a GPU; the position pointer is never dereferenced
+    L = ctypes.CDLL(libpath)
+    dummy = ctypes.c_void_p(16)
+    h = ctypes.c_void_p(1)
+    ok = dict(n=1000, p=4, theta=0.4, ncrit=8, flags=0)
+    bad = [dict(n=0), dict(n=1 << 31), dict(p=0), dict(p=17), dict(theta=0.0), dict(theta=1.0),
+           dict(theta=float("nan")), dict(theta=-0.5), dict(ncrit=0), dict(flags=1 << 7),
+           dict(flags=1 << 31)]
+    for b in bad:
+        a = dict(ok, **b)
+        for build in (L.fmm_build, L.fmm_build_f64):
+            h.value = 1
+            rc = build(dummy, ctypes.c_int64(a["n"]), a["p"], ctypes.c_double(a["theta"]), a["ncrit"],
+                       ctypes.c_uint32(a["flags"]), None, None, ctypes.byref(h))
+            assert rc == -1, b
+            assert not h.value  # the handle is cleared on failure
+
+    class Alloc(ctypes.Structure):
+        _fields_ = [("alloc", ctypes.c_void_p), ("free", ctypes.c_void_p), ("ctx", ctypes.c_void_p)]
+
+    half = Alloc(ctypes.c_void_p(16), None, None)  # an allocator without a free function
+    assert L.fmm_build(dummy, ctypes.c_int64(1000), 4, ctypes.c_double(0.4), 8, ctypes.c_uint32(0),
+                       ctypes.byref(half), None, ctypes.byref(h)) == -1
+    # null handles and outputs
+    assert L.fmm_evaluate(None, None, dummy, None, None) == -1
+    assert L.fmm_backward(None, dummy, dummy, dummy, None) == -1
+    assert L.fmm_solve_host(None, None, ctypes.c_int64(10), 4, ctypes.c_double(0.4), 8, ctypes.c_uint32(0),
+                            dummy, None, None, None, None) == -1
