@@ -42,6 +42,11 @@
 //     -n <= m <= n (p*p entries); no m >= 0 symmetry is used here.
 //   * Output: phi_i (no 1/(4 pi), no softening), grad_i = grad phi(x_i);
 //     self and coincident pairs contribute zero.
+//   * Range: the harmonics are unscaled (r^n and 1/r^(n+1) up to degree
+//     2p - 2), so the far field needs those powers of the cell sizes and
+//     distances inside the double range: at p = 16 a root cube between about
+//     1e-9 and 1e9 across.  The tree, the lists and the near field have no
+//     such limit.
 //
 // Build:  g++ -O2 -std=c++17 -fopenmp -ffp-contract=off -fPIC -shared
 

@@ -1,0 +1,123 @@
+"""Property tests of the oracle's tree and traversal on small generated body
+sets, including degenerate geometry: bodies on a line or a plane, repeated
+points, clusters far apart, and coordinates of very large or very small
+magnitude.  For every set, every (target, source) body pair is covered exactly
+once by P2P or by one M2L, the lists are symmetric, every cell's bodies lie in
+its cube, and with the MAC switched off (theta tiny) the result is the direct
+sum.  With the circumscribed radius, every body's potential error stays under
+the sum, over the M2L pairs that reach it, of the double-truncation bound
+Q_A rho^p / (d - r_A - r_B), rho = (r_A + r_B) / d: M2M and L2L are exact
+within the degree < p truncation, so the M2L truncations are the only error.
+"""
+
+import numpy as np
+import pytest
+
+hyp = pytest.importorskip("hypothesis")
+from hypothesis import HealthCheck, given, settings  # noqa: E402
+from hypothesis import strategies as st  # noqa: E402
+
+
+# The expansions use unscaled solid harmonics (r^n and 1/r^(n+1) up to degree
+# 2p - 2), so the far field needs cell sizes whose powers stay inside the double
+# range; the tree, the lists and the near field have no such limit.
+ALL_SCALES = (1e-30, 1e-6, 1.0, 1e6, 1e30)
+FAR_FIELD_SCALES = (1e-12, 1e-6, 1.0, 1e6, 1e12)
+
+
+@st.composite
+def body_sets(draw, scales=ALL_SCALES):
+    n = draw(st.integers(1, 160))
+    seed = draw(st.integers(0, 2 ** 31 - 1))
+    shape = draw(st.sampled_from(["cube", "line", "plane", "repeats", "clusters"]))
+    scale = draw(st.sampled_from(scales))
+    rng = np.random.default_rng(seed)
+    x = rng.uniform(-1, 1, (n, 3))
+    if shape == "line":
+        x = np.outer(rng.uniform(-1, 1, n), rng.normal(size=3))
+    elif shape == "plane":
+        x[:, draw(st.integers(0, 2))] = 0.25
+    elif shape == "repeats":
+        x = x[rng.integers(0, max(1, n // 4), n)]
+    elif shape == "clusters":
+        x = 1e-3 * x + np.where(rng.random((n, 1)) < 0.5, -1.0, 1.0) * np.array([1.0, 0.5, 0.25])
+    q = rng.uniform(-1, 1, n)
+    return np.concatenate([scale * x, q[:, None]], axis=1)
+
+
+def _covered_once(T, n):
+    c = T.cells()
+    L = T.lists()
+    bb, be = c["body_begin"], c["body_end"]
+    cnt = np.zeros((n, n), np.int32)
+    for t, s in zip(L["p2p_tgt"], L["p2p_src"]):
+        cnt[bb[t]:be[t], bb[s]:be[s]] += 1
+    for t, s in zip(L["m2l_tgt"], L["m2l_src"]):
+        cnt[bb[t]:be[t], bb[s]:be[s]] += 1
+    assert np.all(cnt == 1)
+    for a, b in (("p2p_tgt", "p2p_src"), ("m2l_tgt", "m2l_src")):
+        pairs = set(zip(L[a].tolist(), L[b].tolist()))
+        assert all((s, t) in pairs for t, s in pairs)
+
+
+def _bodies_in_cells(T, x):
+    c = T.cells()
+    r = T.root()
+    _, perm = T.keys()
+    xs = x[perm, :3]
+    for i in range(c["level"].size):
+        R = np.ldexp(r["H"], -int(c["level"][i]))
+        lo = r["corner"] + 2 * R * np.array([c["ix"][i], c["iy"][i], c["iz"][i]], np.float64)
+        b = xs[c["body_begin"][i]:c["body_end"][i]]
+        tol = 1e-12 * r["H"]
+        assert np.all(b >= lo - tol) and np.all(b <= lo + 2 * R + tol)
+
+
+@settings(max_examples=300, deadline=None, derandomize=True, suppress_health_check=[HealthCheck.too_slow])
+@given(x=body_sets(), ncrit=st.integers(1, 12), theta=st.sampled_from([0.3, 0.5, 0.7, 0.95]),
+       mode=st.sampled_from(["half", "circumscribed", "tight"]))
+def test_traversal_covers_every_pair_once(orc, x, ncrit, theta, mode):
+    T = orc.OracleTree(x, 3, theta, ncrit, circumscribed=mode == "circumscribed", tight=mode == "tight")
+    _covered_once(T, x.shape[0])
+    _bodies_in_cells(T, x)
+
+
+@settings(max_examples=200, deadline=None, derandomize=True, suppress_health_check=[HealthCheck.too_slow])
+@given(x=body_sets(), ncrit=st.integers(1, 12))
+def test_no_acceptance_gives_the_direct_sum(orc, x, ncrit):
+    T = orc.OracleTree(x, 2, 1e-9, ncrit)
+    assert T.info()["n_m2l"] == 0
+    ph, g = T.evaluate()
+    pd, gd = orc.direct(x)
+    np.testing.assert_allclose(ph, pd, rtol=1e-12, atol=1e-12 * np.abs(pd).max(initial=0))
+    np.testing.assert_allclose(g, gd, rtol=1e-12, atol=1e-12 * np.abs(gd).max(initial=0))
+
+
+@settings(max_examples=200, deadline=None, derandomize=True, suppress_health_check=[HealthCheck.too_slow])
+@given(x=body_sets(FAR_FIELD_SCALES), ncrit=st.integers(1, 12), theta=st.sampled_from([0.3, 0.5, 0.7]),
+       p=st.integers(1, 7))
+def test_potential_error_within_the_truncation_bound(orc, x, ncrit, theta, p):
+    T = orc.OracleTree(x, p, theta, ncrit, circumscribed=True)
+    c = T.cells()
+    L = T.lists()
+    r = T.root()
+    _, perm = T.keys()
+    bb, be = c["body_begin"], c["body_end"]
+    R = np.ldexp(r["H"], -c["level"].astype(np.int64))
+    ctr = r["corner"] + R[:, None] * (2.0 * np.stack([c["ix"], c["iy"], c["iz"]], 1) + 1.0)
+    rad = np.sqrt(3.0) * R
+    qa = np.abs(x[perm, 3])
+    Q = np.array([qa[bb[i]:be[i]].sum() for i in range(R.size)])
+    bound = np.zeros(x.shape[0])
+    for t, s in zip(L["m2l_tgt"], L["m2l_src"]):
+        d = np.linalg.norm(ctr[t] - ctr[s])
+        rho = (rad[t] + rad[s]) / d
+        assert rho < theta * (1 + 1e-12)
+        bound[bb[t]:be[t]] += Q[s] * rho ** p / (d - rad[t] - rad[s])
+    ph, _ = T.evaluate()
+    pd, _ = orc.direct(x)
+    absq = x.copy()
+    absq[:, 3] = np.abs(absq[:, 3])
+    scale, _ = orc.direct(absq)  # sum_j |q_j| / r_ij: the size of the rounding errors
+    err = np.abs(ph - pd)[perm]
+    assert np.all(err <= bound * (1 + 1e-9) + 1e-12 * scale[perm])
