@@ -201,8 +201,12 @@ int fmm_solve_host(const float* xyzq_h, const float* w_h, int64_t n, int p, doub
  * n bodies (coincident bodies skipped) and force_i = -grad phi(x_i).
  * Used to report the FMM's error (accuracy, not a fast path: O(n) per target).
  *   xyzq     device, n x 4 float (the same input the tree was built from).
- *   targets  device, nt int32 input indices in [0, n).
+ *   targets  device, nt int32 input indices in [0, n); an index outside that
+ *            range is not read through and gives NaN for that target.
+ *   nt       0 <= nt <= 2^31 - 1.
  *   pot      device, nt double;  force  device, nt x 3 double, or NULL.
+ * Errors: FMM_ERR_ARG (null pointers, n < 1, nt out of range, xyzq not
+ * 16-byte aligned), FMM_ERR_CUDA.
  */
 int fmm_direct_f64(const float* xyzq, int64_t n, const int32_t* targets, int64_t nt, double* pot,
                    double* force, fmm_stream stream);

@@ -14,7 +14,16 @@ __global__ void k_direct(const float4* __restrict__ xyzq, int64_t n, const int32
                          int64_t nt, double* __restrict__ pot, double* __restrict__ force) {
   const int64_t k = blockIdx.x;
   if (k >= nt) return;
-  const float4 ti = xyzq[tg[k]];
+  const int32_t i = tg[k];
+  if (i < 0 || i >= n) {  // the whole block leaves: the target is not a body
+    if (threadIdx.x == 0) {
+      const double qnan = __longlong_as_double(0x7ff8000000000000ll);
+      pot[k] = qnan;
+      if (force) force[3 * k] = force[3 * k + 1] = force[3 * k + 2] = qnan;
+    }
+    return;
+  }
+  const float4 ti = xyzq[i];
   const double xi = ti.x, yi = ti.y, zi = ti.z;
   double s0 = 0, s1 = 0, s2 = 0, s3 = 0;
   for (int64_t j = threadIdx.x; j < n; j += kThreads) {
@@ -57,7 +66,7 @@ __global__ void k_direct(const float4* __restrict__ xyzq, int64_t n, const int32
 
 extern "C" int fmm_direct_f64(const float* xyzq, int64_t n, const int32_t* targets, int64_t nt, double* pot,
                               double* force, fmm_stream stream) {
-  if (!xyzq || !targets || !pot || n < 1 || nt < 0) return FMM_ERR_ARG;
+  if (!xyzq || !targets || !pot || n < 1 || nt < 0 || nt > 0x7fffffffll) return FMM_ERR_ARG;
   if (nt == 0) return FMM_OK;
   if (((uintptr_t)xyzq & 15) != 0) return FMM_ERR_ARG;
   try {

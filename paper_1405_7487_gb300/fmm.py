@@ -276,6 +276,8 @@ def direct_f64(xyzq: torch.Tensor, targets: torch.Tensor, force: bool = True):
     """Double-precision direct sum at the target input indices
     (fmm_direct_f64): (pot (nt,), force (nt, 3)) as float64 CUDA tensors."""
     x = _dev_tensor(xyzq, torch.float32, (xyzq.shape[0], 4), "xyzq")
+    if targets.dim() != 1:
+        raise ValueError("targets must be one-dimensional")
     tg = targets.to(device=x.device, dtype=torch.int32).contiguous()
     nt = tg.shape[0]
     pot = torch.empty(nt, dtype=torch.float64, device=x.device)
@@ -291,7 +293,11 @@ def solve_host(xyzq: np.ndarray, w: Optional[np.ndarray], p: int, theta: float, 
     """One whole step through host buffers (fmm_solve_host): build, evaluate
     and, when w is given, the backward pass, copies included."""
     x = np.ascontiguousarray(xyzq, dtype=np.float32)
+    if x.ndim != 2 or x.shape[1] != 4 or x.shape[0] < 1:
+        raise ValueError(f"xyzq must have shape (N, 4) with N >= 1, got {x.shape}")
     N = x.shape[0]
+    if w is not None and np.shape(w) != (N,):
+        raise ValueError(f"w must have shape ({N},), got {np.shape(w)}")
     pot = np.empty(N, np.float32)
     frc = np.empty((N, 3), np.float32) if force else None
     ww = None if w is None else np.ascontiguousarray(w, dtype=np.float32)

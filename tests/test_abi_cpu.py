@@ -95,3 +95,21 @@ def test_build_arguments_checked_before_any_gpu_work(libpath):
     assert L.fmm_backward(None, dummy, dummy, dummy, None) == -1
     assert L.fmm_solve_host(None, None, ctypes.c_int64(10), 4, ctypes.c_double(0.4), 8, ctypes.c_uint32(0),
                             dummy, None, None, None, None) == -1
+
+
+def test_binding_rejects_bad_shapes_before_the_library(libpath):
+    # checked in Python before any library call, so no GPU is needed
+    import numpy as np
+    import torch
+
+    from paper_1405_7487_gb300 import fmm
+    with pytest.raises(ValueError):
+        fmm.Tree(torch.zeros(10, 4), 4, 0.4, 8)  # a host tensor
+    with pytest.raises(ValueError):
+        fmm.solve_host(np.zeros((10, 3), np.float32), None, 4, 0.4, 8)
+    with pytest.raises(ValueError):
+        fmm.solve_host(np.zeros((0, 4), np.float32), None, 4, 0.4, 8)
+    with pytest.raises(ValueError):
+        fmm.solve_host(np.zeros((10, 4), np.float32), np.zeros(9, np.float32), 4, 0.4, 8)
+    with pytest.raises(TypeError):
+        fmm.direct_f64(torch.zeros(10, 4), torch.zeros(3, dtype=torch.int64))
