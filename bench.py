@@ -339,7 +339,8 @@ def cpu_baseline(workload: str, steps: int, mac: str = "half") -> dict:
     dt = time.perf_counter() - t0
     return {"value": x.shape[0] * steps / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
             "bodies": int(x.shape[0]),
-            "sample": f"first {x.shape[0]} bodies of {workload}, same p/theta/ncrit; "
+            "sample": f"first {x.shape[0]} bodies of {workload}, same p/theta/ncrit"
+                      f"{'' if mac == 'half' else ', ' + mac + ' MAC radius'}; "
                       f"build + forward + backward, {steps} step(s), {dt:.2f} s"}
 
 
