@@ -55,6 +55,10 @@ MUTANTS = [
     ("leaf_size_rule", "void build_cells(", "if (e - s <= t.ncrit) continue;",
      "if (e - s < t.ncrit) continue;"),
     ("tight_radius_not_max", "void tight_radii(", "best = std::max(best, d2);", "best = d2;"),
+    ("tight_voxel_corner", "void tight_radii(", "const int64_t d = 2 * u[a] + 1 - ctr[a];",
+     "const int64_t d = 2 * u[a] - ctr[a];"),
+    ("mac_accepts_ties", "bool mac(", "return (t.theta * t.theta) * (double)D2 > (double)S2;",
+     "return (t.theta * t.theta) * (double)D2 >= (double)S2;"),
     ("mac_theta_not_squared", "bool mac(",
      "return (t.theta * t.theta) * (double)D2 > (double)S2;",
      "return t.theta * (double)D2 > (double)S2;"),

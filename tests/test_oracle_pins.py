@@ -347,16 +347,18 @@ def _deinterleave(keys, shift):
     return u
 
 
+@pytest.mark.parametrize("theta", [0.5, 0.55])
 @pytest.mark.parametrize("mode", ["half", "circumscribed", "tight"])
-def test_lists_follow_the_acceptance_criterion(orc, mode):
+def test_lists_follow_the_acceptance_criterion(orc, mode, theta):
     """Sec. II.A/C: a pair of cells goes to M2L exactly when it is far enough
     for its sizes.  Every M2L pair passes theta |c_A - c_B| > R_A + R_B and every
     P2P pair of two distinct leaves fails it, with the radii derived here from
     the geometry (units of H / 2^21): the half side 2^(21-l); the distance from
     the centre to a corner of the cube (the circumscribed sphere); the distance
-    to the farthest voxel centre 2u + 1 of the cell's bodies (particle-fitted)."""
+    to the farthest voxel centre 2u + 1 of the cell's bodies (particle-fitted).
+    At theta = 0.5 with the half side, cells two widths apart along an axis meet
+    the criterion with equality; the strict inequality sends them to P2P."""
     x = W.plummer(2000, 54)
-    theta = 0.55
     T = orc.OracleTree(x, 4, theta, 6, circumscribed=mode == "circumscribed", tight=mode == "tight")
     c = T.cells()
     L = T.lists()
@@ -388,6 +390,11 @@ def test_lists_follow_the_acceptance_criterion(orc, mode):
     far_p2p = [(t, s) for t, s in zip(L["p2p_tgt"], L["p2p_src"]) if t != s]
     assert len(far_p2p) > 0
     assert not any(accepted(t, s) for t, s in far_p2p)
+    if mode == "half" and theta == 0.5:
+        def tie(a, b):
+            d = ctr[a] - ctr[b]
+            return (theta * theta) * float(int(d @ d)) == float((int(half[a]) + int(half[b])) ** 2)
+        assert any(tie(t, s) for t, s in far_p2p)
 
 
 def test_coincident_bodies_contribute_zero(orc):
