@@ -113,3 +113,42 @@ def test_binding_rejects_bad_shapes_before_the_library(libpath):
         fmm.solve_host(np.zeros((10, 4), np.float32), np.zeros(9, np.float32), 4, 0.4, 8)
     with pytest.raises(TypeError):
         fmm.direct_f64(torch.zeros(10, 4), torch.zeros(3, dtype=torch.int64))
+
+
+C_CLIENT = r"""
+#include <stdio.h>
+#include <string.h>
+#include "gbfmm.h"
+
+int main(void) {
+  fmm_tree* t = (fmm_tree*)1;
+  int rc = fmm_build(NULL, 10, 4, 0.4, 8, 0u, NULL, NULL, &t);
+  if (rc != FMM_ERR_ARG || t != NULL) return 1;
+  if (strcmp(fmm_strerror(FMM_ERR_ARG), fmm_strerror(FMM_OK)) == 0) return 2;
+  if (fmm_destroy(NULL) != FMM_OK) return 3;
+  if (fmm_launch_count() != 0) return 4;
+  printf("%s\n", fmm_strerror(rc));
+  return 0;
+}
+"""
+
+
+def test_plain_c_client_compiles_links_and_runs(libpath, tmp_path):
+    # the boundary is a C ABI: a C99 program includes the header, links the
+    # library and calls it (argument checks only, so no GPU is needed)
+    import shutil
+    import subprocess
+    if shutil.which("gcc") is None:
+        pytest.skip("needs gcc")
+    src = tmp_path / "client.c"
+    src.write_text(C_CLIENT)
+    exe = tmp_path / "client"
+    libdir = os.path.dirname(libpath)
+    name = os.path.basename(libpath)
+    assert name.startswith("lib") and name.endswith(".so")
+    subprocess.run(["gcc", "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror", "-I", os.path.join(ROOT, "include"),
+                    str(src), "-o", str(exe), "-L", libdir, "-l" + name[3:-3], "-Wl,-rpath," + libdir],
+                   check=True)
+    r = subprocess.run([str(exe)], capture_output=True, text=True, timeout=60)
+    assert r.returncode == 0, (r.returncode, r.stdout, r.stderr)
+    assert r.stdout.strip() == "invalid argument"
