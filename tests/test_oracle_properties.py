@@ -4,7 +4,8 @@ points, clusters far apart, and coordinates of very large or very small
 magnitude.  For every set, every (target, source) body pair is covered exactly
 once by P2P or by one M2L, the lists are symmetric, every cell's bodies lie in
 its cube, and with the MAC switched off (theta tiny) the result is the direct
-sum.  With the circumscribed radius, every body's potential error stays under
+sum, and the operator is symmetric.  With the circumscribed radius, every
+body's potential error stays under
 the sum, over the M2L pairs that reach it, of the double-truncation bound
 Q_A rho^p / (d - r_A - r_B), rho = (r_A + r_B) / d: M2M and L2L are exact
 within the degree < p truncation, so the M2L truncations are the only error.
@@ -121,3 +122,23 @@ def test_potential_error_within_the_truncation_bound(orc, x, ncrit, theta, p):
     scale, _ = orc.direct(absq)  # sum_j |q_j| / r_ij: the size of the rounding errors
     err = np.abs(ph - pd)[perm]
     assert np.all(err <= bound * (1 + 1e-9) + 1e-12 * scale[perm])
+
+
+@settings(max_examples=150, deadline=None, derandomize=True, suppress_health_check=[HealthCheck.too_slow])
+@given(x=body_sets(FAR_FIELD_SCALES), ncrit=st.integers(1, 12), theta=st.sampled_from([0.3, 0.5, 0.7]),
+       p=st.integers(1, 7), mode=st.sampled_from(["half", "circumscribed", "tight"]),
+       wseed=st.integers(0, 2 ** 31 - 1))
+def test_operator_is_symmetric(orc, x, ncrit, theta, p, mode, wseed):
+    """The truncated kernel of an M2L pair is a polynomial of degree < p in each
+    of the two offsets with the coefficients of the even 1/r, and the lists are
+    symmetric, so the FMM operator is symmetric: w . FMM(q) = q . FMM(w)."""
+    T = orc.OracleTree(x, p, theta, ncrit, circumscribed=mode == "circumscribed", tight=mode == "tight")
+    q = x[:, 3]
+    w = np.random.default_rng(wseed).uniform(-1, 1, x.shape[0])
+    pq, _ = T.evaluate(q)
+    pw, _ = T.evaluate(w)
+    absx = x.copy()
+    absx[:, 3] = 1.0
+    s, _ = orc.direct(absx)  # sum_j 1 / r_ij: the size of the terms
+    size = float(np.abs(w) @ (s * np.abs(q).max())) + float(np.abs(q) @ (s * np.abs(w).max()))
+    assert abs(float(w @ pq) - float(q @ pw)) <= 1e-11 * size + 1e-300
