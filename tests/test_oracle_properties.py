@@ -1,14 +1,14 @@
-"""Property tests of the oracle's tree and traversal on small generated body
-sets, including degenerate geometry: bodies on a line or a plane, repeated
-points, clusters far apart, and coordinates of very large or very small
-magnitude.  For every set, every (target, source) body pair is covered exactly
-once by P2P or by one M2L, the lists are symmetric, every cell's bodies lie in
-its cube, and with the MAC switched off (theta tiny) the result is the direct
-sum, and the operator is symmetric.  With the circumscribed radius, every
-body's potential error stays under
-the sum, over the M2L pairs that reach it, of the double-truncation bound
-Q_A rho^p / (d - r_A - r_B), rho = (r_A + r_B) / d: M2M and L2L are exact
-within the degree < p truncation, so the M2L truncations are the only error.
+"""Property tests of the oracle on small generated body sets, including
+degenerate geometry: bodies on a line or a plane, repeated points, clusters
+far apart, and coordinates of very large or very small magnitude.  For every
+set: every (target, source) body pair is covered exactly once by P2P or by one
+M2L, the lists are symmetric, every cell's bodies lie in its cube, with the MAC
+switched off (theta tiny) the result is the direct sum, and the operator is
+symmetric.  With the circumscribed radius, every body's potential error stays
+under the sum, over the M2L pairs that reach it, of the double-truncation
+bound Q_A rho^p / (d - r_A - r_B), rho = (r_A + r_B) / d: M2M and L2L are
+exact within the degree < p truncation, so the M2L truncations are the only
+error.
 """
 
 import numpy as np
