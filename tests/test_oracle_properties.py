@@ -3,8 +3,8 @@ degenerate geometry: bodies on a line or a plane, repeated points, clusters
 far apart, and coordinates of very large or very small magnitude.  For every
 set: every (target, source) body pair is covered exactly once by P2P or by one
 M2L, the lists are symmetric, every cell's bodies lie in its cube, with the MAC
-switched off (theta tiny) the result is the direct sum, and the operator is
-symmetric.  With the circumscribed radius, every body's potential error stays
+switched off (theta tiny) the result is the direct sum, the operator is
+symmetric, and the result equals the independent Cartesian Taylor checker.  With the circumscribed radius, every body's potential error stays
 under the sum, over the M2L pairs that reach it, of the double-truncation
 bound Q_A rho^p / (d - r_A - r_B), rho = (r_A + r_B) / d: M2M and L2L are
 exact within the degree < p truncation, so the M2L truncations are the only
@@ -142,3 +142,24 @@ def test_operator_is_symmetric(orc, x, ncrit, theta, p, mode, wseed):
     s, _ = orc.direct(absx)  # sum_j 1 / r_ij: the size of the terms
     size = float(np.abs(w) @ (s * np.abs(q).max())) + float(np.abs(q) @ (s * np.abs(w).max()))
     assert abs(float(w @ pq) - float(q @ pw)) <= 1e-11 * size + 1e-300
+
+
+@settings(max_examples=60, deadline=None, derandomize=True, suppress_health_check=[HealthCheck.too_slow])
+@given(x=body_sets((1e-3, 1.0, 1e3)), ncrit=st.integers(1, 8), theta=st.sampled_from([0.5, 0.7]),
+       p=st.integers(1, 4), mode=st.sampled_from(["half", "circumscribed", "tight"]))
+def test_matches_the_cartesian_checker(orc, x, ncrit, theta, p, mode):
+    """The whole oracle equals the basis-free double Taylor closed form of the
+    same lists (an independent Cartesian evaluation with no M2M or L2L)."""
+    from tests import taylor_checker
+    x = x[:60]
+    T = orc.OracleTree(x, p, theta, ncrit, circumscribed=mode == "circumscribed", tight=mode == "tight")
+    ph, g = T.evaluate()
+    ph2, g2 = taylor_checker.evaluate(x, p, T.cells(), T.lists(), T.keys(), T.root())
+    # sizes of the summed terms, sum_j |q_j| / r_ij and sum_j |q_j| / r_ij^2,
+    # set the rounding tolerance
+    d = np.linalg.norm(x[:, None, :3] - x[None, :, :3], axis=2)
+    inv = np.divide(1.0, d, out=np.zeros_like(d), where=d > 0)
+    s1 = inv @ np.abs(x[:, 3])
+    s2 = (inv * inv) @ np.abs(x[:, 3])
+    assert np.all(np.abs(ph - ph2) <= 1e-11 * s1)
+    assert np.all(np.abs(g - g2).max(1) <= 1e-10 * s2)
