@@ -4,8 +4,9 @@ Each case plants one plausible mistake in a copy of ``oracle/fmm_oracle.cpp``:
 a dropped term, a wrong sign, a wrong index or a swapped operand, in every stage
 of the path (harmonics, P2M, M2M, M2L, L2L, L2P, P2P, keys, tree, MAC,
 traversal, adjoint, direct sum).  The copy is built with the oracle's own
-compiler flags and the pins of ``test_oracle_pins.py`` run against it in a
-child process; at least one pin must fail.  The unmutated copy goes through the
+compiler flags, and the pins of ``test_oracle_pins.py`` and the properties of
+``test_oracle_properties.py`` run against it in a child process; at least one
+must fail.  The unmutated copy goes through the
 same harness and must pass, so that a broken harness cannot pass as a catch.
 """
 
@@ -86,7 +87,7 @@ RUNNER = (
     "import sys, oracle, pytest\n"
     "oracle.use_library(sys.argv[1])\n"
     "sys.exit(pytest.main(['-x', '-q', '-p', 'no:cacheprovider', '-m', 'not gpu',\n"
-    "                      'tests/test_oracle_pins.py']))\n"
+    "                      'tests/test_oracle_pins.py', 'tests/test_oracle_properties.py']))\n"
 )
 
 

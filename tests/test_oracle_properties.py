@@ -1,10 +1,12 @@
 """Property tests of the oracle on small generated body sets, including
 degenerate geometry: bodies on a line or a plane, repeated points, clusters
-far apart, and coordinates of very large or very small magnitude.  For every
-set: every (target, source) body pair is covered exactly once by P2P or by one
-M2L, the lists are symmetric, every cell's bodies lie in its cube, with the MAC
-switched off (theta tiny) the result is the direct sum, the operator is
-symmetric, and the result equals the independent Cartesian Taylor checker.  With the circumscribed radius, every body's potential error stays
+far apart, and coordinates of very large or very small magnitude. For every
+set: the root cube, keys, order and cells equal their definitions written out
+with plain integers, every (target, source) body pair is covered exactly once
+by P2P or by one M2L, the lists are symmetric, every cell's bodies lie in its
+cube, with the MAC switched off (theta tiny) the result is the direct sum, the
+operator is symmetric, and the result equals the independent Cartesian Taylor
+checker. With the circumscribed radius, every body's potential error stays
 under the sum, over the M2L pairs that reach it, of the double-truncation
 bound Q_A rho^p / (d - r_A - r_B), rho = (r_A + r_B) / d: M2M and L2L are
 exact within the degree < p truncation, so the M2L truncations are the only
@@ -163,3 +165,75 @@ def test_matches_the_cartesian_checker(orc, x, ncrit, theta, p, mode):
     s2 = (inv * inv) @ np.abs(x[:, 3])
     assert np.all(np.abs(ph - ph2) <= 1e-11 * s1)
     assert np.all(np.abs(g - g2).max(1) <= 1e-10 * s2)
+
+
+def _brute_tree(x, ncrit):
+    """Root cube, keys, order and cells written out from their definitions
+    (Sec. II.B/II.C, Sec. III.A's N_crit) with plain Python integers."""
+    lo, hi = x[:, :3].min(0), x[:, :3].max(0)
+    ctr = (lo + hi) * 0.5
+    H = max(float(v) for v in (hi - lo) * 0.5) * (1.0 + 2.0 ** -20)
+    H = 0.5 if H == 0.0 else H
+    corner = ctr - H
+    k = np.floor(((x[:, :3] - corner) / (2.0 * H)) * 2.0 ** 21)
+    k = np.clip(k, 0, 2 ** 21 - 1).astype(np.int64)
+    keys = []
+    for kx, ky, kz in k.tolist():
+        key = 0
+        for b in range(21):  # x is the most significant bit of each triple
+            key |= (((kx >> b) & 1) << (3 * b + 2)) | (((ky >> b) & 1) << (3 * b + 1)) | (((kz >> b) & 1) << (3 * b))
+        keys.append(key)
+    perm = sorted(range(len(keys)), key=lambda i: (keys[i], i))
+    ks = [keys[i] for i in perm]
+    # breadth-first cells: (level, prefix, begin, end, parent)
+    cells = [(0, 0, 0, len(ks), -1)]
+    child_begin, child_count = [], []
+    i = 0
+    while i < len(cells):
+        lev, pre, b, e, _ = cells[i]
+        if e - b > ncrit and lev < 21:
+            first = len(cells)
+            shift = 3 * (21 - lev - 1)
+            j = b
+            while j < e:
+                pc = ks[j] >> shift
+                m = j
+                while m < e and ks[m] >> shift == pc:
+                    m += 1
+                cells.append((lev + 1, pc, j, m, i))
+                j = m
+            child_begin.append(first)
+            child_count.append(len(cells) - first)
+        else:
+            child_begin.append(-1)
+            child_count.append(0)
+        i += 1
+
+    def coord(pre, lev, axis_bit):
+        v = 0
+        for b in range(lev):
+            v |= ((pre >> (3 * b + axis_bit)) & 1) << b
+        return v
+
+    out = {"level": [c[0] for c in cells],
+           "ix": [coord(c[1], c[0], 2) for c in cells], "iy": [coord(c[1], c[0], 1) for c in cells],
+           "iz": [coord(c[1], c[0], 0) for c in cells],
+           "body_begin": [c[2] for c in cells], "body_end": [c[3] for c in cells],
+           "child_begin": child_begin, "child_count": child_count, "parent": [c[4] for c in cells]}
+    return {"lo": lo, "hi": hi, "centre": ctr, "H": H, "corner": corner}, ks, perm, out
+
+
+@settings(max_examples=200, deadline=None, derandomize=True, suppress_health_check=[HealthCheck.too_slow])
+@given(x=body_sets(), ncrit=st.integers(1, 12))
+def test_tree_equals_its_definition(orc, x, ncrit):
+    T = orc.OracleTree(x, 2, 0.5, ncrit)
+    root, ks, perm, cells = _brute_tree(x.astype(np.float64), ncrit)
+    r = T.root()
+    for name in ("lo", "hi", "centre", "corner"):
+        assert np.array_equal(r[name], root[name]), name
+    assert r["H"] == root["H"]
+    keys, operm = T.keys()
+    assert keys.tolist() == ks and operm.tolist() == perm
+    c = T.cells()
+    for name, v in cells.items():
+        assert c[name].tolist() == v, name
