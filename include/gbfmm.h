@@ -120,8 +120,12 @@ typedef struct {
                                 per CTA, 2 four tiles per CTA sharing each operator */
   int64_t workspace_bytes;   /* device bytes held by the tree */
   int32_t evaluations;       /* fmm_evaluate calls on this tree */
-  int32_t device_errors;     /* nonzero if a kernel's bounded wait gave up (the
-                                results of that pass are not valid) */
+  int32_t device_errors;     /* bits of the tree's device error word, sticky for
+                                the tree's life: 1 a bounded wait of an evaluate
+                                or backward kernel gave up (that pass's outputs
+                                are not valid); 4 a kernel block ended with a
+                                copy or tensor-core operation it issued not seen
+                                to complete (treat every output as invalid) */
   float ms[FMM_PH_COUNT];    /* last evaluate/build phase times (FMM_FLAG_TIMING) */
 } fmm_stats;
 
@@ -141,7 +145,10 @@ typedef struct {
  *   stream the stream all work is ordered on; the call synchronises it.
  *   out    host; receives the new tree handle (NULL on failure).
  * Errors: FMM_ERR_ARG, FMM_ERR_NONFINITE, FMM_ERR_OOM, FMM_ERR_CUDA,
- * FMM_ERR_RANGE.  On failure nothing is leaked.
+ * FMM_ERR_RANGE, FMM_ERR_TIMEOUT (a device scan of the build waited past
+ * its limit for another block: the build's blocks are not making progress
+ * as they must).  On failure every byte taken from the allocator is given
+ * back to it (through its free callback) before the call returns.
  */
 int fmm_build(const float* xyzq, int64_t n, int p, double theta, int ncrit, uint32_t flags,
               const fmm_allocator* alloc, fmm_stream stream, fmm_tree** out);
@@ -189,7 +196,8 @@ int fmm_backward_f64(fmm_tree* t, const double* w, double* dq, double* dx, fmm_s
  *   pot_h   host, N float.  force_h  host, N x 3 float, or NULL.
  *   dq_h, dx_h  host, N and N x 3 float; required when w_h is given.
  * Synchronous (returns when the host outputs are written).  Pinned host
- * memory makes the copies faster but is not required.
+ * memory makes the copies faster but is not required.  Returns
+ * FMM_ERR_TIMEOUT (outputs not valid) when fmm_check would.
  */
 int fmm_solve_host(const float* xyzq_h, const float* w_h, int64_t n, int p, double theta,
                    int ncrit, uint32_t flags, float* pot_h, float* force_h, float* dq_h,
@@ -214,8 +222,17 @@ int fmm_direct_f64(const float* xyzq, int64_t n, const int32_t* targets, int64_t
 /* host: number of CUDA kernels this library has launched in this process. */
 int64_t fmm_launch_count(void);
 
-/* host: statistics of the tree and of its last build/evaluate. */
+/* host: statistics of the tree and of its last build/evaluate.  Waits for
+ * the tree's last evaluate / backward.  Fills *out in every case and returns
+ * FMM_ERR_TIMEOUT when out->device_errors is nonzero. */
 int fmm_get_stats(const fmm_tree* t, fmm_stats* out);
+
+/* host: waits for the tree's last evaluate / backward and returns
+ * FMM_ERR_TIMEOUT if a bounded device wait of any pass on this tree gave up
+ * (the outputs of that pass, and of any backward that uses it, are not
+ * valid), else FMM_OK.  Every kernel wait is bounded so that a device fault
+ * surfaces here instead of hanging the caller. */
+int fmm_check(const fmm_tree* t);
 
 /* Releases the tree and its workspace (stream-ordered on the build stream).
  * NULL is accepted. */
@@ -291,6 +308,13 @@ int fmm_get_plan(const fmm_tree* t, int32_t* tile_tgt, int32_t* tile_eptr, int32
  */
 int fmm_root_keys_noalloc(const float* xyzq, int64_t n, double* root, uint64_t* keys, int32_t* nonfinite,
                           fmm_stream stream);
+
+/* host, test only: on != 0 makes the first tile of every multi-tile device
+ * scan publish its sum 10 ms late while the look-back's time limit drops to
+ * 1 ms, so that the waiting blocks run past their limit (the scan's result
+ * stays correct: they keep waiting).  fmm_build then fails with
+ * FMM_ERR_TIMEOUT.  Process-wide; returns the previous setting. */
+int fmm_debug_scan_fault(int on);
 
 /* host out[4]: record of the self-checking build (compiled with
  * -DGBFMM_CHECKED): site code and index of the first out-of-range access the

@@ -70,6 +70,7 @@ def _load(path: str):
     L.orc_set_threads.argtypes = [ctypes.c_int]
     L.orc_build.argtypes = [_D, ctypes.c_int64, ctypes.c_int, ctypes.c_double, ctypes.c_int,
                             ctypes.c_int, ctypes.POINTER(ctypes.c_void_p)]
+    L.orc_set_order.argtypes = [ctypes.c_void_p, ctypes.c_int]
     L.orc_free.argtypes = [ctypes.c_void_p]
     L.orc_free.restype = None
     L.orc_info.argtypes = [ctypes.c_void_p, _I64]
@@ -129,6 +130,12 @@ class OracleTree:
         if h is not None and h.value:
             lib().orc_free(h)
             self._h = None
+
+    def set_order(self, p: int) -> None:
+        """Evaluate with p terms from now on (same tree and lists)."""
+        if lib().orc_set_order(self._h, int(p)) != 0:
+            raise ValueError(f"bad order {p}")
+        self.p = int(p)
 
     def info(self) -> dict:
         out = np.zeros(6, np.int64)

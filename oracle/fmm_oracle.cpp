@@ -638,6 +638,18 @@ int orc_build(const double* xyzq, int64_t N, int p, double theta, int ncrit, int
 
 void orc_free(void* t) { delete (Tree*)t; }
 
+// Expansion order of later evaluations.  The tree and the lists do not
+// depend on it (Sec. III.A: P only sets the number of terms), so one build
+// serves several orders.
+int orc_set_order(void* tp, int p) {
+  if (!tp || p < 1 || p > 30) return -1;
+  Tree& t = *(Tree*)tp;
+  t.p = p;
+  t.M.clear();
+  t.L.clear();
+  return 0;
+}
+
 // info: ncell, nleaf, nlevel, n_p2p, n_m2l, p2p body pairs (excl. self)
 int orc_info(void* tp, int64_t* info) {
   Tree& t = *(Tree*)tp;

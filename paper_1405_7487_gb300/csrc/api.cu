@@ -22,7 +22,7 @@ void release_tree(fmm_tree* t) {
       cudaStreamSynchronize(st);
       cudaStreamDestroy(st);
     }
-  for (cudaEvent_t e : {t->fork, t->join, t->fork_near, t->join_far})
+  for (cudaEvent_t e : {t->fork, t->join, t->fork_near, t->join_far, t->pass_done})
     if (e) cudaEventDestroy(e);
   for (auto& e : t->ev)
     if (e) cudaEventDestroy(e);
@@ -45,12 +45,17 @@ void create_tree(fmm_tree* t, const R* xyzq) {
     GB_CK(cudaStreamCreateWithPriority(&t->side, cudaStreamNonBlocking, lo));
     GB_CK(cudaStreamCreateWithPriority(&t->far, cudaStreamNonBlocking, hi));
   }
-  for (cudaEvent_t* e : {&t->fork, &t->join, &t->fork_near, &t->join_far})
+  for (cudaEvent_t* e : {&t->fork, &t->join, &t->fork_near, &t->join_far, &t->pass_done})
     GB_CK(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
   if (t->flags & FMM_FLAG_TIMING)
     for (auto& e : t->ev) GB_CK(cudaEventCreate(&e));
   Arena& a = t->arena;
   cudaStream_t s = t->stream;
+  // the tree's device error word comes first: every device scan of the
+  // build reports a wait past its limit there
+  t->dev_err = alloc_n<int>(a, 1);
+  GB_CK(cudaMemsetAsync(t->dev_err, 0, sizeof(int), s));
+  a.err = t->dev_err;
   const bool timing = (t->flags & FMM_FLAG_TIMING) != 0;
   auto mark = [&](int ph, int end) {
     if (timing) GB_CK(cudaEventRecord(t->ev[2 * ph + end], s));
@@ -81,15 +86,12 @@ void create_tree(fmm_tree* t, const R* xyzq) {
     if (const char* env = getenv("GBFMM_M2L_CHUNK")) per = std::max(1, atoi(env));  // tuning knob
     build_m2l_chunks(t, per);
   }
-  t->dev_err = alloc_n<int>(a, 1);
-  GB_CK(cudaMemsetAsync(t->dev_err, 0, sizeof(int), s));
   t->check_rec = alloc_n<unsigned long long>(a, 4);
   GB_CK(cudaMemsetAsync(t->check_rec, 0, 4 * sizeof(unsigned long long), s));
   t->lim = Lim{t->N, t->ncell, t->nleaf, t->Kp, t->ntile, t->nentry, t->nclass, t->n_p2p_ranges, t->check_rec};
   mark(FMM_PH_BUILD_OPS, 1);
   mark(FMM_PH_BUILD_TOTAL, 1);
-  GB_CK(cudaStreamSynchronize(s));
-  if (scan_gave_up()) fail(FMM_ERR_CUDA, "a device scan's look-back wait gave up");
+  check_scan_error(a, s);  // synchronises
   if (t->p2p_nitem)
     GB_CK(cudaMemcpy(&t->p2p_nitem_host, t->p2p_nitem, sizeof(long long), cudaMemcpyDeviceToHost));
   if (timing)
@@ -214,6 +216,7 @@ int evaluate_common(fmm_tree* t, const R* q, R* pot, R* force, fmm_stream stream
     if (q) launch_set_charges<R>(t, q, s);
     else GB_CK(cudaMemcpyAsync(t->work, t->bodies, sizeof(R) * 4 * (size_t)t->N, cudaMemcpyDeviceToDevice, s));
     run_pass<R>(t, s, 0, pot, force);
+    GB_CK(cudaEventRecord(t->pass_done, s));
     t->evaluations++;
   } catch (const Error& e) {
     return to_code(e);
@@ -230,10 +233,27 @@ int backward_common(fmm_tree* t, const R* w, R* dq, R* dx, fmm_stream stream) {
   try {
     launch_set_charges<R>(t, w, s);
     run_pass<R>(t, s, 1, dq, dx);
+    GB_CK(cudaEventRecord(t->pass_done, s));
   } catch (const Error& e) {
     return to_code(e);
   }
   return FMM_OK;
+}
+
+// host: waits for the tree's last evaluate / backward and reads its device
+// error word; -1 if the wait or the copy failed
+int read_device_errors(const fmm_tree* t) {
+  if (!t->dev_err) return 0;
+  if (t->pass_done && cudaEventSynchronize(t->pass_done) != cudaSuccess) {
+    cudaGetLastError();
+    return -1;
+  }
+  int h = 0;
+  if (cudaMemcpy(&h, t->dev_err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) {
+    cudaGetLastError();
+    return -1;
+  }
+  return h;
 }
 
 }  // namespace
@@ -303,6 +323,7 @@ int fmm_solve_host(const float* xyzq_h, const float* w_h, int64_t n, int p, doub
   if (rc == FMM_OK) rc = fmm_build(d_x, n, p, theta, ncrit, flags, nullptr, stream, &t);
   if (rc == FMM_OK) rc = fmm_evaluate(t, nullptr, d_pot, d_force, stream);
   if (rc == FMM_OK && w_h) rc = fmm_backward(t, d_w, d_dq, d_dx, stream);
+  if (rc == FMM_OK) rc = fmm_check(t);
   auto back = [&](float* h, const float* d, size_t count) {
     if (rc == FMM_OK && h && cudaMemcpyAsync(h, d, sizeof(float) * count, cudaMemcpyDeviceToHost, s) != cudaSuccess)
       rc = FMM_ERR_CUDA;
@@ -346,14 +367,9 @@ int fmm_get_stats(const fmm_tree* tc, fmm_stats* o) {
   o->m2l_engine = t->m2l_engine == 1 && t->m2l_quad ? 2 : t->m2l_engine;
   o->workspace_bytes = (int64_t)t->arena.bytes;
   o->evaluations = t->evaluations;
-  if (t->dev_err) {
-    int h = 0;
-    if (cudaMemcpy(&h, t->dev_err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) {
-      cudaGetLastError();
-      return FMM_ERR_CUDA;
-    }
-    o->device_errors = h;
-  }
+  const int derr = read_device_errors(t);
+  if (derr < 0) return FMM_ERR_CUDA;
+  o->device_errors = derr;
   if ((t->flags & FMM_FLAG_TIMING) && t->evaluations > 0) {
     if (cudaEventSynchronize(t->ev[2 * FMM_PH_EVAL_TOTAL + 1]) != cudaSuccess) {
       cudaGetLastError();
@@ -367,8 +383,16 @@ int fmm_get_stats(const fmm_tree* tc, fmm_stats* o) {
     }
   }
   for (int ph = 0; ph < FMM_PH_COUNT; ++ph) o->ms[ph] = t->ms[ph];
-  return FMM_OK;
+  return derr ? FMM_ERR_TIMEOUT : FMM_OK;
 }
+
+int fmm_check(const fmm_tree* t) {
+  if (!t) return FMM_ERR_ARG;
+  const int derr = read_device_errors(t);
+  if (derr < 0) return FMM_ERR_CUDA;
+  return derr ? FMM_ERR_TIMEOUT : FMM_OK;
+}
+
 
 int fmm_destroy(fmm_tree* t) {
   if (!t) return FMM_OK;

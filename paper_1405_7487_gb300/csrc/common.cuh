@@ -17,6 +17,12 @@ constexpr int kMaxP = 16;       // expansion terms supported (K = p*p <= 256)
 constexpr int kTile = 128;      // targets per M2L tile (rows of one MMA / one CTA)
 constexpr int kM2LChunk = 16;   // entries accumulated per TMEM partial (tensor-core M2L)
 
+// Bits of a tree's device error word (fmm_tree::dev_err), set by kernels
+// whose bounded waits gave up; the word is sticky for the tree's life.
+constexpr int kErrWait = 1;   // an evaluation kernel gave up on a copy or MMA: that pass is invalid
+constexpr int kErrScan = 2;   // a device scan's look-back gave up: the build is invalid
+constexpr int kErrDrain = 4;  // a block ended while a copy or MMA it issued had not been seen to complete
+
 struct Error {
   int code;
   std::string what;
@@ -37,6 +43,7 @@ struct Arena {
   fmm_allocator user{};
   bool has_user = false;
   cudaStream_t stream = nullptr;
+  int* err = nullptr;  // the owning tree's device error word (kErr* bits), set before any scan
   std::vector<void*> live;
   void* alloc(size_t bytes);
   void release(void* p);
@@ -50,15 +57,19 @@ T* alloc_n(Arena& a, size_t n) {
 }
 
 // ---------------------------------------------------------------- device prims
-// Exclusive scan of n int64 values in place; returns the total (synchronises
-// the stream to read it back when `total` is requested).
+// Exclusive scans of n nonnegative int64 values in place.  A scan whose
+// bounded look-back wait gave up sets kErrScan in *a.err; kernels that
+// consume a scan's offsets before the host has looked at that word skip
+// their work once it is set (they take the error word as an argument).
 void scan_exclusive_i64(Arena& a, int64_t* d, int64_t n, cudaStream_t s);
 // the total is left in device memory (no host synchronisation)
 void scan_exclusive_i64_dev(Arena& a, int64_t* d, int64_t n, int64_t* total_dev, cudaStream_t s);
+// returns the total: synchronises the stream, reads the total and the error
+// word, and fails with FMM_ERR_TIMEOUT if kErrScan is set
 int64_t scan_exclusive_i64_total(Arena& a, int64_t* d, int64_t n, cudaStream_t s);
-// true if a single-pass scan's bounded look-back wait has given up since the
-// last call (the flag is cleared when read)
-bool scan_gave_up();
+// host: fails with FMM_ERR_TIMEOUT if kErrScan is set in the error word
+// (synchronises the stream first)
+void check_scan_error(Arena& a, cudaStream_t s);
 
 // LSD radix sort of (key, value) pairs on bits [0, bits) of the key; stable.
 // keys/vals are replaced by the sorted arrays (ping-pong buffers from the arena).
@@ -157,7 +168,8 @@ struct fmm_tree {
   int evaluations = 0;
 
   unsigned long long* check_rec = nullptr;  // self-check record (checked build)
-  int* dev_err = nullptr;  // set by a kernel whose bounded wait gave up
+  int* dev_err = nullptr;  // kErr* bits set by kernels whose bounded waits gave up (sticky)
+  cudaEvent_t pass_done = nullptr;  // recorded at the end of every evaluate / backward
   gbfmm::Lim lim{};
   cudaStream_t side = nullptr;  // P2P runs here (lowest priority), concurrently with the far field
   cudaStream_t far = nullptr;   // the far field runs here (highest priority)

@@ -215,11 +215,9 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
     // no copy may still be in flight when the CTA ends: the thread's own
     // cp.async copies, and (thread 0, after an abort) the last operator load
     cp_async_wait<0>();
-    if (r == 0 && tma_issued > 0) {
-      volatile int dummy = 0;
-      const int last = tma_issued - 1;
-      mbar_wait(smem_u32(&bar_opfull[last % nstage]), (last / nstage) & 1, &dummy);
-    }
+    if (r == 0)  // every operator load that may still be in flight
+      for (int i = max(0, tma_issued - nstage); i < tma_issued; ++i)
+        if (!mbar_drain(smem_u32(&bar_opfull[i % nstage]), (i / nstage) & 1)) atomicOr(err, kErrDrain);
     // ------------------------------------------------------------ epilogue
     const bool ok = nit > 0 && mbar_wait(smem_u32(&bar_done), 0, &abort_flag);
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
@@ -283,12 +281,14 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
   // drain: the last commits must land before the TMEM is released
   asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
   __syncthreads();
-  if (abort_flag && tid == 0) atomicExch(err, 1);
+  if (abort_flag && tid == 0) atomicOr(err, kErrWait);
   if (warp == 4) {
     if (abort_flag && nit > 0) {
-      // wait (bounded) for the MMAs that were issued, then release
-      volatile int dummy = 0;
-      mbar_wait(smem_u32(&bar_done), 0, &dummy);
+      // wait (bounded) for the MMAs that were issued before the TMEM is
+      // released; if they are not seen to finish, the release still happens
+      // (an unreleased allocation would block every later block on this SM)
+      // and the error word says so
+      if (!mbar_drain(smem_u32(&bar_done), 0) && lane == 0) atomicOr(err, kErrDrain);
     }
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(tmem_cols) : "memory");
@@ -450,11 +450,9 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
     }
     // no copy may still be in flight when the CTA ends
     cp_async_wait<0>();
-    if (r == 0 && tma_issued > 0) {
-      volatile int dummy = 0;
-      const int last = tma_issued - 1;
-      mbar_wait(smem_u32(&bar_bfull[last & 1]), (last >> 1) & 1, &dummy);
-    }
+    if (r == 0)  // both operator stages may still be in flight
+      for (int i = max(0, tma_issued - 2); i < tma_issued; ++i)
+        if (!mbar_drain(smem_u32(&bar_bfull[i & 1]), (i >> 1) & 1)) atomicOr(err, kErrDrain);
     // ------------------------------------------------------------ epilogue
     const bool ok = j1 > j0 && mbar_wait(smem_u32(&bar_done), 0, &abort_flag);
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
@@ -536,11 +534,10 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
   }
   asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
   __syncthreads();
-  if (abort_flag && tid == 0) atomicExch(err, 1);
+  if (abort_flag && tid == 0) atomicOr(err, kErrWait);
   if (warp == 4) {
     if (abort_flag && j1 > j0) {
-      volatile int dummy = 0;
-      mbar_wait(smem_u32(&bar_done), 0, &dummy);
+      if (!mbar_drain(smem_u32(&bar_done), 0) && lane == 0) atomicOr(err, kErrDrain);
     }
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(512) : "memory");

@@ -8,6 +8,11 @@ namespace gbfmm {
 
 // Polls of a bounded mbarrier wait before it gives up.
 constexpr long long kSpinLimit = 1ll << 20;
+// Polls of the wait that drains a copy or tensor-core operation still in
+// flight after a block gave up, before the block ends or frees its tensor
+// memory (a block must not end while a copy into its shared memory can still
+// land).
+constexpr long long kDrainSpinLimit = 1ll << 24;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -25,8 +30,9 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, uint32_t byt
 
 // Bounded wait for the phase with the given parity; false if it gave up (it
 // then sets *abort_flag) or another thread raised *abort_flag.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag) {
-  for (long long it = 0; it < kSpinLimit; ++it) {
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag,
+                                          long long limit = kSpinLimit) {
+  for (long long it = 0; it < limit; ++it) {
     uint32_t done;
     asm volatile(
         "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
@@ -38,6 +44,13 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatil
   }
   *abort_flag = 1;
   return false;
+}
+
+// Drain after a give-up: waits (bounded, kDrainSpinLimit polls, no abort) for
+// the phase with the given parity; false if that also gave up.
+__device__ __forceinline__ bool mbar_drain(uint32_t bar, uint32_t parity) {
+  volatile int none = 0;
+  return mbar_wait(bar, parity, &none, kDrainSpinLimit);
 }
 
 // Orders this thread's (and, after a barrier, the block's) generic-proxy

@@ -474,7 +474,8 @@ __global__ void __launch_bounds__(kThreads, 7) k_p2p_f2(const float4* __restrict
       }
       for (int k = 0; k < ntile; ++k) {
         const int T0 = k * kTilePairs, T1 = min(T0 + kTilePairs, P);
-        const bool ok = mbar_wait(smem_u32(&bar[buf]), (parity >> buf) & 1u, &abort_flag);
+        const uint32_t phase = (parity >> buf) & 1u;
+        const bool ok = mbar_wait(smem_u32(&bar[buf]), phase, &abort_flag);
         parity ^= 1u << buf;
         if (ok) pad_tile(st, nw, T0, T1, tiles[buf]);
         const int T2n = min(T1 + kTilePairs, P);
@@ -482,9 +483,15 @@ __global__ void __launch_bounds__(kThreads, 7) k_p2p_f2(const float4* __restrict
           mbar_arrive_expect_tx(smem_u32(&bar[buf ^ 1]), (uint32_t)((T2n - T1) * sizeof(SrcPair)));
         // the pads are visible and tiles[buf ^ 1] is no longer read
         if (__syncthreads_or(!ok)) {
-          // a copy did not land: give up on this leaf (no copy is in flight
-          // but the one waited for)
-          if (tid == 0) atomicExch(err, 1);
+          // a copy did not land in time: give up on this item.  The copies
+          // of the tile waited for are the only ones in flight (the next
+          // tile's are issued after this point); the block must not end
+          // before they land in its shared memory, so thread 0 drains them
+          // with a longer bounded wait.
+          if (tid == 0) {
+            atomicOr(err, kErrWait);
+            if (!mbar_drain(smem_u32(&bar[buf]), phase)) atomicOr(err, kErrDrain);
+          }
           return;
         }
         if (T1 < P) {

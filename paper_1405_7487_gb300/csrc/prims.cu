@@ -151,15 +151,26 @@ __global__ void k_scan_tile(int64_t* __restrict__ d, int64_t n, int64_t* __restr
 // Single-pass scan (decoupled look-back): each block takes a ticket, scans
 // its tile, publishes the tile's sum, then adds the published values of the
 // tiles before it, walking back (32 tiles per step, one per lane of warp 0)
-// until one that already holds its inclusive prefix, and publishes its own.  A block only waits for blocks that took
-// their tickets earlier and never wait for later ones, so every wait ends;
-// the spin is bounded all the same and a wait that gives up raises
-// g_scan_err.
+// until one that already holds its inclusive prefix, and publishes its own.
+// A block only waits for blocks that took their tickets earlier and never
+// for later ones, so every wait ends.  The wait is bounded all the same, by
+// the device clock (%globaltimer, ns): past soft_ns it sets kErrScan in *err
+// (the host then fails the call with FMM_ERR_TIMEOUT) and keeps waiting, so
+// that the offsets every later kernel uses stay correct; past kScanHardNs it
+// gives up for good and the scan's result is not valid.  No copy is in
+// flight in this kernel, so giving up is safe for the kernel itself.
+//
+// late_first_ns (test switch, fmm_debug_scan_fault): tile 0 publishes only
+// after that delay, so the look-back of the tiles after it runs past a soft
+// limit shorter than the delay.
 constexpr unsigned long long kStatAgg = 1ull << 62, kStatInc = 2ull << 62;
 constexpr unsigned long long kValMask = (1ull << 62) - 1;
-constexpr long long kScanSpin = 1ll << 24;
+constexpr long long kScanSoftNs = 50000000ll;        // 50 ms: report
+constexpr long long kScanHardNs = 2000000000ll;      // 2 s: give up
+constexpr long long kScanFaultSoftNs = 1000000ll;    // test switch: 1 ms soft limit,
+constexpr long long kScanFaultDelayNs = 10000000ll;  //   tile 0 publishes after 10 ms
 
-__device__ int g_scan_err;
+std::atomic<int> g_scan_fault{0};
 
 __device__ __forceinline__ void st_release(unsigned long long* p, unsigned long long v) {
   asm volatile("st.release.gpu.global.u64 [%0], %1;\n" ::"l"(p), "l"(v) : "memory");
@@ -169,9 +180,15 @@ __device__ __forceinline__ unsigned long long ld_acquire(const unsigned long lon
   asm volatile("ld.acquire.gpu.global.u64 %0, [%1];\n" : "=l"(v) : "l"(p) : "memory");
   return v;
 }
+__device__ __forceinline__ long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return (long long)t;
+}
 
 __global__ void k_scan_onepass(int64_t* __restrict__ d, int64_t n, int64_t* __restrict__ total,
-                               unsigned long long* __restrict__ state, unsigned* __restrict__ ticket) {
+                               unsigned long long* __restrict__ state, unsigned* __restrict__ ticket,
+                               int* __restrict__ err, long long soft_ns, long long late_first_ns) {
   __shared__ int s_tile;
   __shared__ int64_t s_prefix, btotal;
   if (threadIdx.x == 0) s_tile = (int)atomicAdd(ticket, 1u);
@@ -194,10 +211,17 @@ __global__ void k_scan_onepass(int64_t* __restrict__ d, int64_t n, int64_t* __re
     const int64_t agg = btotal;
     int64_t prefix = 0;
     if (tile == 0) {
-      if (lane == 0) st_release(&state[0], kStatInc | (unsigned long long)agg);
+      if (lane == 0) {
+        if (late_first_ns > 0) {  // test switch only; bounded by the clock
+          const long long t0 = global_ns();
+          while (global_ns() - t0 < late_first_ns) __nanosleep(10000);
+        }
+        st_release(&state[0], kStatInc | (unsigned long long)agg);
+      }
     } else {
       if (lane == 0) st_release(&state[tile], kStatAgg | (unsigned long long)agg);
-      long long spin = 0;
+      const long long t0 = global_ns();
+      bool reported = false;
       for (int j = tile - 1; j >= 0;) {
         const int k = j - lane;
         const unsigned long long w = k >= 0 ? ld_acquire(&state[k]) : kStatInc;
@@ -207,10 +231,12 @@ __global__ void k_scan_onepass(int64_t* __restrict__ d, int64_t n, int64_t* __re
         const int first = inc ? __ffs(inc) - 1 : 31;
         const unsigned need = first == 31 ? 0xffffffffu : ((2u << first) - 1u);
         if ((avail & need) != need) {
-          if (++spin > kScanSpin) {
-            if (lane == 0) g_scan_err = 1;
-            break;
+          const long long waited = __shfl_sync(0xffffffffu, global_ns() - t0, 0);
+          if (waited > soft_ns && !reported) {
+            if (lane == 0) atomicOr(err, kErrScan);
+            reported = true;
           }
+          if (waited > kScanHardNs) break;  // the scan's result is not valid
           continue;
         }
         int64_t part = lane <= first ? (int64_t)(w & kValMask) : 0;
@@ -237,6 +263,7 @@ __global__ void k_scan_onepass(int64_t* __restrict__ d, int64_t n, int64_t* __re
 }
 
 void scan_rec(Arena& a, int64_t* d, int64_t n, int64_t* total, cudaStream_t s) {
+  if (!a.err) fail(FMM_ERR_CUDA, "internal: device scan without an error word");
   if (n <= 0) {
     if (total) GB_CK(cudaMemsetAsync(total, 0, sizeof(int64_t), s));
     return;
@@ -250,21 +277,21 @@ void scan_rec(Arena& a, int64_t* d, int64_t n, int64_t* total, cudaStream_t s) {
   // per-tile state words, then the ticket counter
   unsigned long long* state = alloc_n<unsigned long long>(a, nb + 1);
   GB_CK(cudaMemsetAsync(state, 0, sizeof(unsigned long long) * (nb + 1), s));
-  k_scan_onepass<<<(unsigned)nb, kScanThreads, 0, s>>>(d, n, total, state, reinterpret_cast<unsigned*>(state + nb));
+  const bool fault = g_scan_fault.load() != 0;
+  k_scan_onepass<<<(unsigned)nb, kScanThreads, 0, s>>>(d, n, total, state, reinterpret_cast<unsigned*>(state + nb),
+                                                       a.err, fault ? kScanFaultSoftNs : kScanSoftNs,
+                                                       fault ? kScanFaultDelayNs : 0ll);
   GB_LAUNCH("k_scan_onepass");
   a.release(state);
 }
 
 }  // namespace
 
-bool scan_gave_up() {
+void check_scan_error(Arena& a, cudaStream_t s) {
   int h = 0;
-  GB_CK(cudaMemcpyFromSymbol(&h, g_scan_err, sizeof(int)));
-  if (h) {
-    const int zero = 0;
-    GB_CK(cudaMemcpyToSymbol(g_scan_err, &zero, sizeof(int)));  // reported once
-  }
-  return h != 0;
+  GB_CK(cudaMemcpyAsync(&h, a.err, sizeof(int), cudaMemcpyDeviceToHost, s));
+  GB_CK(cudaStreamSynchronize(s));
+  if (h & kErrScan) fail(FMM_ERR_TIMEOUT, "a device scan's bounded look-back wait gave up");
 }
 
 void scan_exclusive_i64(Arena& a, int64_t* d, int64_t n, cudaStream_t s) {
@@ -280,8 +307,8 @@ int64_t scan_exclusive_i64_total(Arena& a, int64_t* d, int64_t n, cudaStream_t s
   scan_rec(a, d, n, tot, s);
   int64_t h = 0;
   GB_CK(cudaMemcpyAsync(&h, tot, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-  GB_CK(cudaStreamSynchronize(s));
   a.release(tot);
+  check_scan_error(a, s);  // synchronises; nothing has used the result yet
   return h;
 }
 
@@ -390,5 +417,7 @@ void radix_sort_keys(Arena& a, uint64_t*& keys, int64_t n, int bits, cudaStream_
 }  // namespace gbfmm
 
 extern "C" int64_t fmm_launch_count(void) { return (int64_t)gbfmm::g_launches.load(); }
+
+extern "C" int fmm_debug_scan_fault(int on) { return gbfmm::g_scan_fault.exchange(on ? 1 : 0); }
 
 extern "C" const char* fmm_last_error(void) { return gbfmm::g_last_error.c_str(); }

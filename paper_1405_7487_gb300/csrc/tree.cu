@@ -6,6 +6,8 @@
 #include <cmath>
 #include <mutex>
 #include <string>
+#include <utility>
+#include <vector>
 
 #include "common.cuh"
 
@@ -134,7 +136,8 @@ __device__ __forceinline__ uint64_t spread_bits(uint64_t v) {
 }
 
 // Integer coordinate k = min(floor((x - corner) / (2H) * 2^21), 2^21 - 1) per
-// axis, interleaved x-major into a 63-bit key.
+// axis, interleaved x-major into a 63-bit key; idx (the identity permutation
+// the sort starts from) is written when it is not null.
 template <class R>
 __global__ void k_keys(const R* __restrict__ xyzq, int64_t n, const double* __restrict__ root,
                        uint64_t* __restrict__ keys, int32_t* __restrict__ idx) {
@@ -152,7 +155,7 @@ __global__ void k_keys(const R* __restrict__ xyzq, int64_t n, const double* __re
     key |= spread_bits((uint64_t)k) << (2 - a);
   }
   keys[i] = key;
-  idx[i] = (int32_t)i;
+  if (idx) idx[i] = (int32_t)i;
 }
 
 template <class R>
@@ -474,27 +477,31 @@ constexpr int kNoAllocBodies = 0x7fffffff;
 // (about 57 KB); every call overwrites it.
 static __device__ __align__(256) double g_noalloc_scratch[kNoAllocBlocks * 7 + 32];
 
-// Keys only (the allocating path also writes the identity permutation).
-__global__ void k_keys_noalloc(const float* __restrict__ xyzq, int64_t n, const double* __restrict__ root,
-                               uint64_t* __restrict__ keys) {
-  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  const double side = __dadd_rn(root[9], root[9]);
-  uint64_t key = 0;
-#pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    double d = __dsub_rn((double)xyzq[4 * i + a], root[10 + a]);
-    double s = __dmul_rn(__ddiv_rn(d, side), 2097152.0);
-    double f = floor(s);
-    int64_t k = (int64_t)f;
-    k = k < 0 ? 0 : (k > 2097151 ? 2097151 : k);
-    key |= spread_bits((uint64_t)k) << (2 - a);
-  }
-  keys[i] = key;
-}
-
+// The scratch array's device address per CUDA context (the address belongs
+// to the context the module was loaded in).  The runtime uses the primary
+// context of the current device unless the caller made another current.
 std::mutex g_noalloc_mu;
-double* g_noalloc_ptr[64] = {};
+std::vector<std::pair<CUcontext, double*>> g_noalloc_ptr;
+
+typedef CUresult (*CtxGetCurrentFn)(CUcontext*);
+
+// cuCtxGetCurrent from the driver, found through the runtime (the library
+// does not link libcuda); null if unavailable
+CUcontext current_context() {
+  static CtxGetCurrentFn fn = [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess) {
+      cudaGetLastError();
+      p = nullptr;
+    }
+    return reinterpret_cast<CtxGetCurrentFn>(p);
+  }();
+  CUcontext c = nullptr;
+  if (!fn || fn(&c) != CUDA_SUCCESS) return nullptr;
+  return c;
+}
 
 }  // namespace
 }  // namespace gbfmm
@@ -507,17 +514,17 @@ extern "C" int fmm_root_keys_noalloc(const float* xyzq, int64_t n, double* root,
     g_last_error = "fmm_root_keys_noalloc: n exceeds the maximum of 2^31 - 1 bodies";
     return FMM_ERR_ARG;
   }
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
-    cudaGetLastError();
-    return FMM_ERR_CUDA;
-  }
   double* scratch = nullptr;
   {
-    // once per device, with that device current: the device address of the
-    // scratch array (the host-side symbol is only a stand-in for it)
+    // once per device (per CUDA context), with that device current: the
+    // device address of the scratch array (the host-side symbol is only a
+    // stand-in for it).  The lookup also makes the context current if the
+    // runtime had not yet done so.
     std::lock_guard<std::mutex> lock(g_noalloc_mu);
-    if (!g_noalloc_ptr[dev]) {
+    CUcontext ctx = current_context();
+    for (auto& e : g_noalloc_ptr)
+      if (ctx && e.first == ctx) scratch = e.second;
+    if (!scratch) {
       void* p = nullptr;
       cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
       if (e != cudaSuccess || !p) {
@@ -525,16 +532,17 @@ extern "C" int fmm_root_keys_noalloc(const float* xyzq, int64_t n, double* root,
         g_last_error = "fmm_root_keys_noalloc: cudaGetSymbolAddress failed";
         return FMM_ERR_CUDA;
       }
-      g_noalloc_ptr[dev] = static_cast<double*>(p);
+      scratch = static_cast<double*>(p);
+      ctx = current_context();
+      if (ctx) g_noalloc_ptr.emplace_back(ctx, scratch);
     }
-    scratch = g_noalloc_ptr[dev];
   }
   cudaStream_t s = (cudaStream_t)stream;
   const int nb = (int)std::min<int64_t>(kNoAllocBlocks, (n + kThreads - 1) / kThreads);
   int* flag = nonfinite ? nonfinite : reinterpret_cast<int*>(scratch + kNoAllocBlocks * 7);
   k_bbox_partial<float><<<nb, kThreads, 0, s>>>(xyzq, n, scratch);
   k_bbox_final<<<1, kThreads, 0, s>>>(scratch, nb, root, flag);
-  if (keys) k_keys_noalloc<<<(unsigned)((n + kThreads - 1) / kThreads), kThreads, 0, s>>>(xyzq, n, root, keys);
+  if (keys) k_keys<float><<<(unsigned)((n + kThreads - 1) / kThreads), kThreads, 0, s>>>(xyzq, n, root, keys, nullptr);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) {
     g_last_error = std::string("fmm_root_keys_noalloc: ") + cudaGetErrorName(e);

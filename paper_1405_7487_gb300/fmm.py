@@ -59,6 +59,16 @@ class Stats(ctypes.Structure):
 _V = ctypes.c_void_p
 _I64 = ctypes.c_int64
 
+# fmm_allocator: stream-ordered alloc / free callbacks and their context
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p)
+
+
+class Allocator(ctypes.Structure):
+    """The C ABI's fmm_allocator.  Keep the callback objects alive for as long
+    as a tree built with it exists."""
+    _fields_ = [("alloc", ALLOC_FN), ("free", FREE_FN), ("ctx", ctypes.c_void_p)]
+
 
 def lib():
     """Load libgbfmm.so (raises if it has not been built)."""
@@ -89,6 +99,8 @@ def lib():
             "fmm_direct_f64": [_V, _I64, _V, _I64, _V, _V, _V],
             "fmm_get_plan": [_V, _V, _V, _V, _V, _V, _V, _V],
             "fmm_debug_checks": [_V, _V],
+            "fmm_check": [_V],
+            "fmm_debug_scan_fault": [ctypes.c_int],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -134,7 +146,8 @@ class Tree:
     precision path, float64 the double precision one.
     """
 
-    def __init__(self, xyzq: torch.Tensor, p: int, theta: float, ncrit: int, flags: int = 0):
+    def __init__(self, xyzq: torch.Tensor, p: int, theta: float, ncrit: int, flags: int = 0,
+                 allocator: Optional[Allocator] = None):
         L = lib()
         if not (isinstance(xyzq, torch.Tensor) and xyzq.is_cuda and xyzq.dim() == 2 and xyzq.shape[1] == 4):
             raise ValueError("xyzq must be a CUDA tensor of shape (N, 4)")
@@ -148,10 +161,12 @@ class Tree:
         h = ctypes.c_void_p()
         build = L.fmm_build if self.dtype == torch.float32 else L.fmm_build_f64
         with torch.cuda.device(self.device):
-            rc = build(_ptr(x), self.N, self.p, float(theta), int(ncrit), int(flags), None,
-                       _stream(self.device), ctypes.byref(h))
+            rc = build(_ptr(x), self.N, self.p, float(theta), int(ncrit), int(flags),
+                       None if allocator is None else ctypes.byref(allocator), _stream(self.device),
+                       ctypes.byref(h))
         _check(rc, "fmm_build")
         self._h = h
+        self._allocator = allocator  # the callbacks must outlive the tree
 
     def close(self):
         h = getattr(self, "_h", None)
@@ -190,6 +205,11 @@ class Tree:
         with torch.cuda.device(self.device):
             _check(fn(self._h, _ptr(ww), _ptr(dq), _ptr(dx), _stream(self.device)), "fmm_backward")
         return dq, dx
+
+    def check(self):
+        """Raises FMMError (FMM_ERR_TIMEOUT) if a bounded device wait of any
+        pass on this tree gave up (fmm_check); waits for the last pass."""
+        _check(lib().fmm_check(self._h), "fmm_check")
 
     def stats(self) -> dict:
         s = Stats()

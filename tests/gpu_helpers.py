@@ -39,3 +39,29 @@ def scale_oracle(Mo: np.ndarray, Lo: np.ndarray, R: np.ndarray, p: int):
     Ms = Mo / R[:, None] ** deg[None, :]
     Ls = Lo * R[:, None] ** (deg[None, :] + 1)
     return Ms, Ls
+
+
+# Per-body bound next to the relative L2 tolerance: the largest error of one
+# body (the vector error for forces) relative to the largest reference value.
+# It catches a few bad bodies that a norm over a million would hide.
+TOL_BODY_PHI, TOL_BODY_F = 1e-4, 1e-3
+
+
+def max_body_err(a, b):
+    """max_i |a_i - b_i| / max_i |b_i|; rows are compared as vectors."""
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    if a.ndim == 2:
+        d, r = np.linalg.norm(a - b, axis=1), np.linalg.norm(b, axis=1)
+    else:
+        d, r = np.abs(a - b), np.abs(b)
+    return float(d.max() / r.max())
+
+
+def assert_match(phi, phi_ref, f, f_ref, tol_phi, tol_f, body_phi=TOL_BODY_PHI, body_f=TOL_BODY_F):
+    """Relative L2 within the tolerances, and every body within the
+    per-body bounds."""
+    e = (rel(phi, phi_ref), rel(f, f_ref), max_body_err(phi, phi_ref), max_body_err(f, f_ref))
+    assert e[0] < tol_phi and e[1] < tol_f, e
+    assert e[2] < body_phi and e[3] < body_f, e
+    return e

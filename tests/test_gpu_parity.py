@@ -11,7 +11,7 @@ import pytest
 import torch
 
 from paper_1405_7487_gb300 import workloads as W
-from tests.gpu_helpers import rel, scale_oracle, unpack
+from tests.gpu_helpers import assert_match, rel, scale_oracle, unpack
 
 pytestmark = pytest.mark.gpu
 
@@ -118,8 +118,7 @@ def test_forward_matches_oracle(fmm, orc, name):
     T = gpu_tree(fmm, x, p, theta, ncrit)
     ph, f = evaluate(T)
     po, go = orc.OracleTree(x, p, theta, ncrit).evaluate()
-    assert rel(ph, po) < TOL_PHI
-    assert rel(f, -go) < TOL_F
+    assert_match(ph, po, f, -go, TOL_PHI, TOL_F)
 
 
 @pytest.mark.parametrize("name,f64", [("cube65k_p10", False), ("plummer60k_p8", False), ("sphere40k_p6", False),
@@ -199,8 +198,7 @@ def test_full_size_sampled_parity(fmm, orc, wl):
     idx = W.sample_targets(x.shape[0], 4096)
     O = orc.OracleTree(x, spec["p"], spec["theta"], spec["ncrit"])
     po, go = O.evaluate(targets=idx)
-    assert rel(ph[idx], po) < TOL_PHI
-    assert rel(f[idx], -go) < TOL_F
+    assert_match(ph[idx], po, f[idx], -go, TOL_PHI, TOL_F)
     pd, gd = orc.direct(x, targets=idx)
     err_phi, err_f = rel(ph[idx], pd), rel(f[idx], -gd)
     eo_phi = rel(po, pd)
@@ -219,8 +217,7 @@ def test_backward_matches_oracle(fmm, orc):
     torch.cuda.synchronize()
     O = orc.OracleTree(x, 8, 0.4, 64)
     dqo, dxo = O.backward(w.astype(np.float64))
-    assert rel(dq.double().cpu().numpy(), dqo) < TOL_PHI
-    assert rel(dx.double().cpu().numpy(), dxo) < TOL_F
+    assert_match(dq.double().cpu().numpy(), dqo, dx.double().cpu().numpy(), dxo, TOL_PHI, TOL_F)
 
 
 def test_backward_before_evaluate_is_state_error(fmm):
@@ -263,13 +260,11 @@ def test_double_precision_path(fmm, orc, name):
     ph, f = evaluate(T)
     O = orc.OracleTree(x, p, theta, ncrit)
     po, go = O.evaluate()
-    assert rel(ph, po) < TOL64_PHI
-    assert rel(f, -go) < TOL64_F
+    assert_match(ph, po, f, -go, TOL64_PHI, TOL64_F, 1e-9, 1e-8)
     w = W.weights(x.shape[0], 25).astype(np.float64)
     dq, dx = T.backward(torch.from_numpy(w).cuda())
     dqo, dxo = O.backward(w)
-    assert rel(dq.cpu().numpy(), dqo) < TOL64_PHI
-    assert rel(dx.cpu().numpy(), dxo) < TOL64_F
+    assert_match(dq.cpu().numpy(), dqo, dx.cpu().numpy(), dxo, TOL64_PHI, TOL64_F, 1e-9, 1e-8)
 
 
 # ------------------------------------------------------------ edge cases

@@ -7,7 +7,10 @@ cudaMalloc/cudaFree can cause.  fmm_root_keys_noalloc serves them: it
 computes the root cube and Morton keys of fmm_build's first step with its
 scratch in a fixed device array.  This test checks it against the existing
 path (fmm_build, then fmm_get_root and fmm_get_keys) bit for bit, on two
-calls in a row.  The file name keeps it last in collection order.
+calls in a row, checks that repeated calls leave the device's free memory
+unchanged, and covers the case where the caller passes no flag word (the
+flag then goes to the scratch array).  The file name keeps it last in
+collection order.
 """
 
 import ctypes
@@ -79,3 +82,42 @@ def test_noalloc_flags_and_limits(F):
                                         ctypes.c_void_p(root.data_ptr()), None, None, s)
     assert big == -1
     assert b"maximum" in F.lib().fmm_last_error()
+
+
+def test_noalloc_allocates_nothing(F):
+    """After a first call (which looks up the scratch array), further calls
+    leave the device's free memory exactly as it was."""
+    x = torch.from_numpy(W.cube(400000, 94)).cuda()
+    n = x.shape[0]
+    root = torch.empty(13, dtype=torch.float64, device="cuda")
+    keys = torch.empty(n, dtype=torch.int64, device="cuda")
+    flag = torch.zeros(1, dtype=torch.int32, device="cuda")
+    assert _call(F, x, root, keys, flag) == 0
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    for _ in range(5):
+        assert _call(F, x, root, keys, flag) == 0
+        assert _call(F, x, root, keys, None) == 0
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
+
+
+def test_noalloc_keys_without_flag(F):
+    """keys requested, no flag word: the keys are still fmm_build's."""
+    x_h = W.plummer(150000, 95)
+    x = torch.from_numpy(x_h).cuda()
+    n = x.shape[0]
+    T = F.Tree(x, 4, 0.5, 32)
+    ks, perm = T.keys()
+    ref_keys = np.empty(n, np.uint64)
+    ref_keys[perm] = ks
+    ref = T.root()
+    root = torch.empty(13, dtype=torch.float64, device="cuda")
+    keys = torch.full((n,), -1, dtype=torch.int64, device="cuda")
+    for _ in range(2):
+        assert _call(F, x, root, keys, None) == 0
+        torch.cuda.synchronize()
+        assert np.array_equal(keys.cpu().numpy().view(np.uint64), ref_keys)
+        r = root.cpu().numpy()
+        assert r[9] == ref["H"] and np.array_equal(r[10:13], ref["corner"])
+    T.close()
