@@ -316,6 +316,17 @@ int fmm_root_keys_noalloc(const float* xyzq, int64_t n, double* root, uint64_t* 
  * FMM_ERR_TIMEOUT.  Process-wide; returns the previous setting. */
 int fmm_debug_scan_fault(int on);
 
+/* host out[16]: cycle counters of the tensor-core M2L (four-tile engine) in
+ * the trace build (compiled with -DGBFMM_M2L_TRACE), summed over blocks
+ * since the last read, then cleared: 0 producers waiting for a free source
+ * stage, 1 producers waiting for a free operator stage, 2 the MMA thread
+ * from the block's start to its loop, 3 the MMA thread from its last commit
+ * to the block's end, 5 MMA waiting for an
+ * operator stage, 6 MMA waiting for a source stage, 7 MMA issuing, 11 whole
+ * blocks, 12 block count, 13 producers waiting for the last MMA, 14 epilogue
+ * (other slots zero).  Returns 1 in a trace build, 0 (and zeros) otherwise. */
+int fmm_debug_m2l_trace(int64_t* out);
+
 /* host out[4]: record of the self-checking build (compiled with
  * -DGBFMM_CHECKED): site code and index of the first out-of-range access the
  * evaluation kernels skipped, the bound it broke, and the number of such

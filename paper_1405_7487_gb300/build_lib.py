@@ -21,6 +21,7 @@ INCLUDE = os.path.join(ROOT, "include")
 OUT = os.path.join(PKG, "libgbfmm.so")
 BUILD = os.path.join(PKG, "_build")
 CHECKED_OUT = os.path.join(PKG, "libgbfmm_checked.so")
+TRACED_OUT = os.path.join(PKG, "libgbfmm_traced.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
@@ -44,17 +45,22 @@ def _deps_mtime() -> float:
     return max(os.path.getmtime(f) for f in files)
 
 
-def build(force: bool = False, verbose: bool = False, extra=(), checked: bool = False) -> str:
+def build(force: bool = False, verbose: bool = False, extra=(), checked: bool = False,
+          traced: bool = False) -> str:
     """Build (if stale) and return the path of libgbfmm.so.
 
     checked=True builds libgbfmm_checked.so instead: the evaluation kernels
-    bounds-check their data-dependent accesses (see fmm_debug_checks)."""
-    out_path = CHECKED_OUT if checked else OUT
+    bounds-check their data-dependent accesses (see fmm_debug_checks).
+    traced=True builds libgbfmm_traced.so: the tensor-core M2L counts the
+    cycles of each role's waits and work (see fmm_debug_m2l_trace)."""
+    out_path = CHECKED_OUT if checked else (TRACED_OUT if traced else OUT)
     if checked:
         extra = tuple(extra) + ("-DGBFMM_CHECKED",)
+    if traced:
+        extra = tuple(extra) + ("-DGBFMM_M2L_TRACE",)
     if not force and os.path.exists(out_path) and os.path.getmtime(out_path) >= _deps_mtime():
         return out_path
-    bdir = BUILD + ("_checked" if checked else "")
+    bdir = BUILD + ("_checked" if checked else ("_traced" if traced else ""))
     os.makedirs(bdir, exist_ok=True)
     cc = nvcc()
 
@@ -80,4 +86,5 @@ def build(force: bool = False, verbose: bool = False, extra=(), checked: bool = 
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose=True, checked="--checked" in sys.argv))
+    print(build(force="--force" in sys.argv, verbose=True, checked="--checked" in sys.argv,
+                traced="--traced" in sys.argv))

@@ -42,6 +42,28 @@
 #include "mbarrier.cuh"
 
 namespace gbfmm {
+
+// Trace build (-DGBFMM_M2L_TRACE, libgbfmm_traced.so): the quad engine adds
+// the clock64 cycles its roles spend waiting and working to g_m2l_trace
+// (fmm_debug_m2l_trace reads and clears them).  Slots:
+//   0 producers: wait for a free source stage (thread 0)
+//   1 producers: wait for a free operator stage (thread 0)
+//   2 MMA thread: block start to its first wait
+//   3 MMA thread: its last commit to the end of the block
+//   5 MMA: wait for an operator stage     6 MMA: wait for a source stage
+//   7 MMA: issue + commit                11 whole block     12 blocks
+//  13 producers: wait for the last MMA   14 epilogue
+// (sums over all blocks).
+#ifdef GBFMM_M2L_TRACE
+__device__ unsigned long long g_m2l_trace[16];
+#define M2L_T0(v) const long long v = clock64()
+#define M2L_ADD(slot, t0, cond) \
+  if (cond) atomicAdd(&g_m2l_trace[slot], (unsigned long long)(clock64() - (t0)))
+#else
+#define M2L_T0(v)
+#define M2L_ADD(slot, t0, cond)
+#endif
+
 namespace {
 
 constexpr int kProducers = 128;
@@ -78,6 +100,16 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map
       "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
       "[%4];\n" ::"r"(dst),
       "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
+      : "memory");
+}
+
+// The same with an L2 cache policy (createpolicy) for the loaded lines.
+__device__ __forceinline__ void tma_load_2d_hint(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t bar,
+                                                 uint64_t policy) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1, "
+      "{%2, %3}], [%4], %5;\n" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar), "l"(policy)
       : "memory");
 }
 
@@ -339,6 +371,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
   const uint32_t abase = base + 4 * stageB;  // nastage source stages of 2 * kStageA
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  M2L_T0(t_block);
   const int4 ch = chunks[blockIdx.x];
   const int j0 = ch.y, j1 = ch.z;
   // the inputs span Kin = K rounded up to the 8-element k-step (columns
@@ -392,6 +425,10 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
     int bi = 0, ai = 0;
     int tma_issued = 0;  // thread 0: operator stages issued
     bool stop = false;
+    // operator k-blocks stay in L2 (evict-last): every tile group that has
+    // the class reads them again
+    uint64_t policy = 0;
+    if (r == 0) asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;\n" : "=l"(policy));
     if (j1 > j0) fetch(j0);
     for (int j = j0; j < j1 && !stop; ++j) {
       const int cls = ncls;
@@ -408,17 +445,19 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
         const int k0 = kb * kKB;
         if (r == 0) {
           const int bs = bi & 1, bround = bi >> 1;
+          M2L_T0(t1);
           if (bround > 0 && !mbar_wait(smem_u32(&bar_bempty[bs]), (bround - 1) & 1, &abort_flag)) {
             stop = true;
             break;
           }
+          M2L_ADD(1, t1, true);
           // the box is 32 columns wide; columns past Kp (last k-block) read
           // as zeros and are not used by the MMAs
           const uint32_t fb = smem_u32(&bar_bfull[bs]);
           const uint32_t sb = bbase + bs * 2 * stageB;
           mbar_arrive_expect_tx(fb, 2u * (uint32_t)stageB);
-          tma_load_2d(sb, &tm_ops_hi, k0, cls * Kp, fb);
-          tma_load_2d(sb + stageB, &tm_ops_lo, k0, cls * Kp, fb);
+          tma_load_2d_hint(sb, &tm_ops_hi, k0, cls * Kp, fb, policy);
+          tma_load_2d_hint(sb + stageB, &tm_ops_lo, k0, cls * Kp, fb, policy);
           tma_issued = bi + 1;
         }
         const int nch = min(kKB, Kin - k0) / 4;  // 16-byte chunks in this k-block
@@ -426,10 +465,12 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
         for (int q = 0; q < kQuad; ++q) {
           if (ev[q] < 0) continue;
           const int as = ai % nastage, around = ai / nastage;
+          M2L_T0(t0);
           if (around > 0 && !mbar_wait(smem_u32(&bar_aempty[as]), (around - 1) & 1, &abort_flag)) {
             stop = true;
             break;
           }
+          M2L_ADD(0, t0, r == 0);
           const uint32_t sa = abase + as * 2 * kStageA;
           if (c8 < nch) {
 #pragma unroll
@@ -454,7 +495,10 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
       for (int i = max(0, tma_issued - 2); i < tma_issued; ++i)
         if (!mbar_drain(smem_u32(&bar_bfull[i & 1]), (i >> 1) & 1)) atomicOr(err, kErrDrain);
     // ------------------------------------------------------------ epilogue
+    M2L_T0(t13);
     const bool ok = j1 > j0 && mbar_wait(smem_u32(&bar_done), 0, &abort_flag);
+    M2L_ADD(13, t13, r == 0);
+    M2L_T0(t14);
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
     if (ok) {
       for (int q = 0; q < kQuad; ++q) {
@@ -482,8 +526,10 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
         }
       }
     }
+    M2L_ADD(14, t14, r == 0);
   } else if (lane == 0) {
     // ---------------------------------------------------------------- MMA
+    M2L_ADD(2, t_block, true);
     const uint32_t idesc = idesc_tf32(Kp);
     bool ok = true;
     bool first[kQuad] = {true, true, true, true};
@@ -493,20 +539,25 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
       const int ev[kQuad] = {e4.x, e4.y, e4.z, e4.w};
       for (int kb = 0; kb < nkb && ok; ++kb, ++bi) {
         const int bs = bi & 1, bround = bi >> 1;
+        M2L_T0(t5);
         if (!mbar_wait(smem_u32(&bar_bfull[bs]), bround & 1, &abort_flag)) {
           ok = false;
           break;
         }
+        M2L_ADD(5, t5, true);
         const uint32_t sb = bbase + bs * 2 * stageB;
         const int nks = min(kKB, Kin - kb * kKB) / 8;  // tf32 k-steps of 8 elements
 #pragma unroll
         for (int q = 0; q < kQuad; ++q) {
           if (ev[q] < 0) continue;
           const int as = ai % nastage, around = ai / nastage;
+          M2L_T0(t6);
           if (!mbar_wait(smem_u32(&bar_afull[as]), around & 1, &abort_flag)) {
             ok = false;
             break;
           }
+          M2L_ADD(6, t6, true);
+          M2L_T0(t7);
           // the source rows were written through the generic proxy (cp.async)
           fence_async_smem();
           asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
@@ -523,6 +574,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
           }
           mma_commit(smem_u32(&bar_aempty[as]));
           ++ai;
+          M2L_ADD(7, t7, true);
         }
         // the operator stage is free once the MMAs that read it are done
         mma_commit(smem_u32(&bar_bempty[bs]));
@@ -532,9 +584,15 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
     if (j1 > j0) mma_commit(smem_u32(&bar_done));
     if (!ok) abort_flag = 1;
   }
+  M2L_T0(t_tail);
   asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
   __syncthreads();
+  M2L_ADD(3, t_tail, warp == 4 && lane == 0);
   if (abort_flag && tid == 0) atomicOr(err, kErrWait);
+  M2L_ADD(11, t_block, tid == 0);
+#ifdef GBFMM_M2L_TRACE
+  if (tid == 0) atomicAdd(&g_m2l_trace[12], 1ull);
+#endif
   if (warp == 4) {
     if (abort_flag && j1 > j0) {
       if (!mbar_drain(smem_u32(&bar_done), 0) && lane == 0) atomicOr(err, kErrDrain);
@@ -902,3 +960,23 @@ void build_m2l_chunks(fmm_tree* t, int per) {
 }
 
 }  // namespace gbfmm
+
+// host out[16]: the quad engine's trace counters (see g_m2l_trace), read and
+// cleared.  Returns 1 in a trace build, 0 (and zeros) otherwise.
+extern "C" int fmm_debug_m2l_trace(int64_t* out) {
+  if (!out) return FMM_ERR_ARG;
+  for (int k = 0; k < 16; ++k) out[k] = 0;
+#ifdef GBFMM_M2L_TRACE
+  unsigned long long h[16] = {0};
+  if (cudaMemcpyFromSymbol(h, gbfmm::g_m2l_trace, sizeof(h)) != cudaSuccess) {
+    cudaGetLastError();
+    return FMM_ERR_CUDA;
+  }
+  const unsigned long long z[16] = {0};
+  cudaMemcpyToSymbol(gbfmm::g_m2l_trace, z, sizeof(z));
+  for (int k = 0; k < 16; ++k) out[k] = (int64_t)h[k];
+  return 1;
+#else
+  return FMM_OK;
+#endif
+}

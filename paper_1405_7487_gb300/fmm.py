@@ -17,7 +17,7 @@ import torch
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libgbfmm_checked.so" if os.environ.get("GBFMM_CHECKED") == "1"
-                        else "libgbfmm.so")
+                        else ("libgbfmm_traced.so" if os.environ.get("GBFMM_TRACE") == "1" else "libgbfmm.so"))
 _lib = None
 
 FMM_FLAG_CIRCUMSCRIBED = 1
@@ -100,6 +100,7 @@ def lib():
             "fmm_get_plan": [_V, _V, _V, _V, _V, _V, _V, _V],
             "fmm_debug_checks": [_V, _V],
             "fmm_check": [_V],
+            "fmm_debug_m2l_trace": [_V],
             "fmm_debug_scan_fault": [ctypes.c_int],
         }
         for name, args in sig.items():
