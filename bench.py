@@ -16,9 +16,10 @@ not sharded across GPUs); the time is the maximum over ranks.
 The timed steps run as a user runs them: the near field (P2P) on a second,
 lower-priority stream concurrently with the far field, with per-phase CUDA
 events on the stream each phase runs on (the roofline's kernel time is the
-M2L span measured that way).  One further untimed step runs the phases one
-at a time ("isolated"): per-kernel times without sharing the GPU, from
-which the P2P fraction of the FP32 peak is reported.
+M2L span measured that way).  Five further steps run the phases one at a
+time ("isolated"), each after an L2 flush: per-kernel times without sharing
+the GPU, averaged over the five, from which the P2P fraction of the FP32
+peak is reported.
 """
 
 from __future__ import annotations
@@ -44,6 +45,7 @@ L2_FLUSH_BYTES = 512 << 20  # > 129 MB L2
 # Entries are dropped when the kernel changes.
 DRAM_TRAFFIC = {("cube1m_p10", 1048576, "k_m2l_tc4"): 419_200_000 + 600_150_000}
 CPU_SAMPLE_N = 65536
+ISO_STEPS = 5  # serial-phase steps behind the per-kernel ("isolated") figures
 
 
 # ------------------------------------------------------------------ helpers
@@ -213,10 +215,15 @@ def run_gpu(args):
     max_s = reduce_max(total_s, dev)
     value = aggregate(N, args.steps, world, max_s)
 
-    # the same step with the phases run one at a time (untimed): per-kernel
-    # times without the near field sharing the GPU
-    flush.zero_()
-    iso, _, _ = step(F.FMM_FLAG_TIMING | F.FMM_FLAG_SERIAL_PHASES)
+    # the same step with the phases run one at a time (ISO_STEPS steps, after
+    # the timed region, each after an L2 flush): per-kernel times without the
+    # near field sharing the GPU, averaged over the steps
+    iso_ms = []
+    for _ in range(ISO_STEPS):
+        flush.zero_()
+        st_iso, _, _ = step(F.FMM_FLAG_TIMING | F.FMM_FLAG_SERIAL_PHASES)
+        iso_ms.append(st_iso["ms"])
+    iso = {"ms": {k: statistics.mean(m[k] for m in iso_ms) for k in iso_ms[0]}}
 
     # accuracy against the double direct sum on 4096 sampled targets
     idx = torch.from_numpy(W.sample_targets(N, 4096)).to(dev)
@@ -295,7 +302,7 @@ def run_gpu(args):
         # P2P span in the timed steps, where it shares the GPU with M2L
         "p2p_frac_fp32_peak_in_step": round(p2p_tf / fp32_peak_tflops, 4),
         "m2l_tflops": round(m2l_tf, 3), "p2p_tflops": round(p2p_tf, 3),
-        "isolated": {"m2l_tflops": round(m2l_tf_iso, 3), "p2p_tflops": round(p2p_tf_iso, 3),
+        "isolated": {"steps": ISO_STEPS, "m2l_tflops": round(m2l_tf_iso, 3), "p2p_tflops": round(p2p_tf_iso, 3),
                      "m2l_frac": round(m2l_tf_iso / dom["peak"], 4) if dom["bound"] == "tensor" else None,
                      "phase_ms": {k: round(v, 4) for k, v in iso["ms"].items()}},
         "m2l_issued_tflops": round(m2l_exec_flops / (m2l_avg * 1e-3) / 1e12, 3),

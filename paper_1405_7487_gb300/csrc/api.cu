@@ -92,8 +92,12 @@ void create_tree(fmm_tree* t, const R* xyzq) {
   mark(FMM_PH_BUILD_OPS, 1);
   mark(FMM_PH_BUILD_TOTAL, 1);
   check_scan_error(a, s);  // synchronises
-  if (t->p2p_nitem)
-    GB_CK(cudaMemcpy(&t->p2p_nitem_host, t->p2p_nitem, sizeof(long long), cudaMemcpyDeviceToHost));
+  if (t->p2p_nitem) {
+    long long h[2] = {0, 0};
+    GB_CK(cudaMemcpy(h, t->p2p_nitem, sizeof(h), cudaMemcpyDeviceToHost));
+    t->p2p_nitem_host = h[0];
+    t->p2p_nbig_host = h[1];
+  }
   if (timing)
     for (int ph : {FMM_PH_BUILD_TOTAL, FMM_PH_BUILD_TREE, FMM_PH_BUILD_LISTS, FMM_PH_BUILD_PLAN, FMM_PH_BUILD_OPS})
       cudaEventElapsedTime(&t->ms[ph], t->ev[2 * ph], t->ev[2 * ph + 1]);

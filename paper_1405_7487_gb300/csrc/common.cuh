@@ -159,7 +159,8 @@ struct fmm_tree {
   void* near = nullptr;   // N x 4 (phi, grad) sorted, P2P part
   int4* p2p_items = nullptr;       // single precision: near-field work items (t0, nt, s, e), largest first
   int2* p2p_item_rng = nullptr;    //   and their neighbour ranges [r0, r1)
-  long long* p2p_nitem = nullptr;  //   item count (device)
+  long long* p2p_nitem = nullptr;  //   item count, then the count of per-block items (device)
+  int64_t p2p_nbig_host = 0;       //   items of the per-block kernel (the first ones), read back
   int64_t p2p_nitem_max = 0;       //   bound on it (array size)
   int64_t p2p_nitem_host = 0;      //   item count, read back at the end of the build
   void* near_src = nullptr;  // single precision: the P2P sources, bodies 2m and 2m + 1 in 32-byte pair m

@@ -19,6 +19,7 @@
 // FP32 pairs, one block per work item (a chunk of at most 256 targets of one
 // leaf, largest items first), with bulk-copied source tiles.
 #include <algorithm>
+#include <cstdlib>
 
 #include "kernels.cuh"
 #include "mbarrier.cuh"
@@ -380,25 +381,30 @@ __device__ __forceinline__ void tile_sum2(const SrcPair* __restrict__ tile, int 
   }
 }
 
-// Seven blocks per SM (at most 73 registers a thread): the pair chains are
-// latency-bound, so resident warps count for more than a few spilled values.
-__global__ void __launch_bounds__(kThreads, 7) k_p2p_f2(const float4* __restrict__ bodies,
-                                                     const SrcPair* __restrict__ pairs,
-                                                     const int4* __restrict__ items,
-                                                     const int2* __restrict__ item_rng,
-                                                     const int2* __restrict__ ranges, float4* __restrict__ near,
-                                                     int* __restrict__ err, Lim lim) {
+// Shared memory of one block of the per-block kernel.
+struct BlockSmem {
+  SrcPair tiles[2][kTilePairs];
+  Stream st;
+  unsigned long long bar[2];
+  int abort_flag;
+};
+
+// One work item per block (the block-wide body of k_p2p_mix).
+__device__ __forceinline__ void p2p_block_item(BlockSmem& sm, long long item_index, const float4* __restrict__ bodies,
+                                               const SrcPair* __restrict__ pairs, const int4* __restrict__ items,
+                                               const int2* __restrict__ item_rng, const int2* __restrict__ ranges,
+                                               float4* __restrict__ near, int* __restrict__ err, const Lim& lim) {
   // the group partials of the final reduction reuse the first tile
   static_assert(sizeof(Acc<float>) * 2 * kThreads <= sizeof(SrcPair) * kTilePairs, "reduction space");
-  __shared__ SrcPair tiles[2][kTilePairs];
-  __shared__ Stream st;
-  __shared__ __align__(8) unsigned long long bar[2];
-  __shared__ int abort_flag;
+  SrcPair(*tiles)[kTilePairs] = sm.tiles;
+  Stream& st = sm.st;
+  unsigned long long* bar = sm.bar;
+  int& abort_flag = sm.abort_flag;
   Acc<float>(*red)[kThreads] = reinterpret_cast<Acc<float>(*)[kThreads]>(&tiles[0][0]);
   // the item: targets [t0, t0 + nt) of the leaf with bodies [s, e) and
   // neighbour ranges [r0, r1)
-  const int4 item = items[blockIdx.x];
-  const int2 irng = item_rng[blockIdx.x];
+  const int4 item = items[item_index];
+  const int2 irng = item_rng[item_index];
   const int t0 = item.x, nt = item.y, s = item.z, e = item.w, r0 = irng.x, r1 = irng.y;
   const int tid = threadIdx.x;
   const f2 zero = make_float2(0.f, 0.f);
@@ -529,6 +535,262 @@ __global__ void __launch_bounds__(kThreads, 7) k_p2p_f2(const float4* __restrict
   }
 }
 
+// ---------------------------------------------------------------------------
+// Per-warp variant: each warp of a block owns one work item (a chunk of at
+// most kWarpTargets targets of one leaf) and streams its sources through its
+// own two shared-memory tiles, filled by bulk copies that complete on the
+// warp's own mbarriers.  No block-wide barrier is needed: a warp waits only
+// for its own copies, and its G groups (T2 targets each, two per lane) add
+// their partial sums with shuffles at the end.
+constexpr int kWarpTargets = 64;       // the per-warp code's limit (two targets per lane)
+constexpr int kWarpSmallTargets = 16;  // items routed to it (measured: larger ones run faster per block)
+constexpr int kWarpTile = 112;   // source pairs per warp tile (3.5 KB)
+constexpr int kWarpWindow = 64;  // neighbour ranges staged at a time per warp
+constexpr int kWarpsP2P = 4;
+
+struct WStream {
+  int2 rng[kWarpWindow];
+  int pre[kWarpWindow + 1];
+};
+
+// Lane-strided forms of the block helpers above, for one warp.
+__device__ __forceinline__ int stage_window_w(WStream& st, const int2* __restrict__ ranges, int r0, int nw,
+                                              const Lim& lim, int lane) {
+  int base = 0;
+  for (int r = lane; r - lane < nw; r += 32) {
+    int len = 0;
+    if (r < nw) {
+      const int2 rg = GB_LD(ranges, r0 + r, lim.nranges, 107);
+      const int ps = rg.x >> 1, pe = (rg.y + 1) >> 1;
+      st.rng[r] = make_int2(ps, (rg.x & 1) | ((rg.y & 1) << 1));
+      len = pe - ps;
+    }
+    int incl = len;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int v = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += v;
+    }
+    if (r < nw) st.pre[r] = base + incl - len;
+    base += __shfl_sync(0xffffffffu, incl, 31);
+  }
+  if (lane == 0) st.pre[nw] = base;
+  return base;
+}
+__device__ __forceinline__ void issue_tile_w(const WStream& st, int nw, int T0, int T1,
+                                             const SrcPair* __restrict__ src, uint32_t dst, uint32_t bar,
+                                             const Lim& lim, int lane) {
+  for (int r = lane; r < nw; r += 32) {
+    const int pr = st.pre[r];
+    const int a = max(pr, T0), b = min(st.pre[r + 1], T1);
+    if (a < b) {
+      const int first = st.rng[r].x + (a - pr);
+#ifdef GBFMM_CHECKED
+      if (!in_range(first + (b - a) - 1, (lim.N + 1) / 2, 108, lim.rec)) continue;
+#endif
+      bulk_g2s(dst + (uint32_t)(a - T0) * (uint32_t)sizeof(SrcPair), src + first,
+               (uint32_t)(b - a) * (uint32_t)sizeof(SrcPair), bar);
+    }
+  }
+}
+__device__ __forceinline__ void pad_tile_w(const WStream& st, int nw, int T0, int T1, SrcPair* tile, int lane) {
+  for (int r = lane; r < nw; r += 32) {
+    const int f = st.rng[r].y;
+    if (f == 0) continue;
+    const int a = st.pre[r], b = st.pre[r + 1] - 1;
+    if ((f & 1) && a >= T0 && a < T1) {
+      tile[a - T0].w[0] = kFar;
+      tile[a - T0].w[6] = 0.f;
+    }
+    if ((f & 2) && b >= T0 && b < T1) {
+      tile[b - T0].w[1] = kFar;
+      tile[b - T0].w[7] = 0.f;
+    }
+  }
+}
+
+// Shared memory of one block of the per-warp kernel.
+struct WarpSmem {
+  SrcPair tiles[kWarpsP2P][2][kWarpTile];
+  WStream st[kWarpsP2P];
+  unsigned long long bar[kWarpsP2P][2];
+  int abort_w[kWarpsP2P];
+};
+
+// One work item per warp (the per-warp body of k_p2p_mix): items
+// 4 wb .. 4 wb + 3 of `items` (nitem of them).
+__device__ __forceinline__ void p2p_warp_items(WarpSmem& sm, long long wb, const float4* __restrict__ bodies,
+                                               const SrcPair* __restrict__ pairs, const int4* __restrict__ items,
+                                               const int2* __restrict__ item_rng, long long nitem,
+                                               const int2* __restrict__ ranges, float4* __restrict__ near,
+                                               int* __restrict__ err, const Lim& lim) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const long long it = wb * kWarpsP2P + warp;
+  if (it >= nitem) return;  // the warp has no item (no block barrier follows)
+  WStream& st = sm.st[warp];
+  SrcPair(*tw)[kWarpTile] = sm.tiles[warp];
+  const uint32_t bar0 = smem_u32(&sm.bar[warp][0]), bar1 = smem_u32(&sm.bar[warp][1]);
+  volatile int* abort_flag = &sm.abort_w[warp];
+  // the item: targets [t0, t0 + nt) of the leaf with bodies [s, e) and
+  // neighbour ranges [r0, r1)
+  const int4 item = items[it];
+  const int2 irng = item_rng[it];
+  const int t0 = item.x, nt = item.y, s = item.z, e = item.w, r0 = irng.x, r1 = irng.y;
+  const f2 zero = make_float2(0.f, 0.f);
+  if (lane == 0) {
+    mbar_init(bar0, 1);
+    mbar_init(bar1, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  __syncwarp();
+  const int nr = r1 - r0;
+  const int nwin = (nr + kWarpWindow - 1) / kWarpWindow;
+  int buf = 0;
+  uint32_t parity = 0;  // bit b: the phase of bar[b] to wait for next
+  const int T2 = (nt + 1) >> 1;
+  const int G = 32 / T2;
+  const int i = lane % T2, g = lane / T2;
+  const bool active = g < G;
+  const bool has_b = i + T2 < nt;
+  f2 X0 = zero, Y0 = zero, Z0 = zero, X1 = zero, Y1 = zero, Z1 = zero;
+  if (active) {
+    const float4 a = GB_LD(bodies, t0 + i, lim.N, 106);
+    const float4 b = has_b ? GB_LD(bodies, t0 + i + T2, lim.N, 106) : a;
+    // negated, duplicated target coordinates
+    X0 = f2_pack(-a.x, -a.x);
+    Y0 = f2_pack(-a.y, -a.y);
+    Z0 = f2_pack(-a.z, -a.z);
+    X1 = f2_pack(-b.x, -b.x);
+    Y1 = f2_pack(-b.y, -b.y);
+    Z1 = f2_pack(-b.z, -b.z);
+  }
+  auto fold = [](const Acc2& a) {
+    Acc<float> r;
+    float l, h;
+    f2_unpack(a.p, l, h);
+    r.p = l + h;
+    f2_unpack(a.x, l, h);
+    r.x = l + h;
+    f2_unpack(a.y, l, h);
+    r.y = l + h;
+    f2_unpack(a.z, l, h);
+    r.z = l + h;
+    return r;
+  };
+  Acc<float> s0{0, 0, 0, 0}, c0{0, 0, 0, 0}, s1{0, 0, 0, 0}, c1{0, 0, 0, 0};
+  bool failed = false;
+  // window -1: the leaf's own bodies (masked: self and coincident pairs add
+  // zero); then the neighbour ranges, kWarpWindow at a time
+  for (int w = -1; w < nwin && !failed; ++w) {
+    const int nw = w < 0 ? 1 : min(kWarpWindow, nr - w * kWarpWindow);
+    int P;
+    if (w < 0) {
+      const int ps = s >> 1, pe = (e + 1) >> 1;
+      if (lane == 0) {
+        st.rng[0] = make_int2(ps, (s & 1) | ((e & 1) << 1));
+        st.pre[0] = 0;
+        st.pre[1] = pe - ps;
+      }
+      P = pe - ps;
+    } else {
+      P = stage_window_w(st, ranges, r0 + w * kWarpWindow, nw, lim, lane);
+    }
+    const int ntile = (P + kWarpTile - 1) / kWarpTile;
+    if (lane == 0 && P > 0)
+      mbar_arrive_expect_tx(buf ? bar1 : bar0, (uint32_t)(min(P, kWarpTile) * sizeof(SrcPair)));
+    __syncwarp();  // the window's ranges are visible to the warp
+    if (ntile > 0) {
+      fence_async_smem();
+      issue_tile_w(st, nw, 0, min(P, kWarpTile), pairs, smem_u32(tw[buf]), buf ? bar1 : bar0, lim, lane);
+    }
+    for (int k = 0; k < ntile; ++k) {
+      const int T0 = k * kWarpTile, T1 = min(T0 + kWarpTile, P);
+      const uint32_t phase = (parity >> buf) & 1u;
+      const uint32_t mb = buf ? bar1 : bar0;
+      const bool ok = __all_sync(0xffffffffu, mbar_wait(mb, phase, abort_flag));
+      parity ^= 1u << buf;
+      if (!ok) {
+        // a copy did not land in time: give up on this item after draining
+        // the copies of the tile waited for (the only ones in flight)
+        if (lane == 0) {
+          atomicOr(err, kErrWait);
+          if (!mbar_drain(mb, phase)) atomicOr(err, kErrDrain);
+        }
+        failed = true;
+        break;
+      }
+      pad_tile_w(st, nw, T0, T1, tw[buf], lane);
+      const int T2n = min(T1 + kWarpTile, P);
+      if (lane == 0 && T1 < P)
+        mbar_arrive_expect_tx(buf ? bar0 : bar1, (uint32_t)((T2n - T1) * sizeof(SrcPair)));
+      __syncwarp();  // the pads are visible and tw[buf ^ 1] is no longer read
+      if (T1 < P) {
+        fence_async_smem();
+        issue_tile_w(st, nw, T1, T2n, pairs, smem_u32(tw[buf ^ 1]), buf ? bar0 : bar1, lim, lane);
+      }
+      if (active) {
+        Acc2 p0{zero, zero, zero, zero}, p1{zero, zero, zero, zero};
+        if (w < 0)
+          tile_sum2<true>(tw[buf], g, T1 - T0, G, X0, Y0, Z0, X1, Y1, Z1, p0, p1);
+        else
+          tile_sum2<false>(tw[buf], g, T1 - T0, G, X0, Y0, Z0, X1, Y1, Z1, p0, p1);
+        kahan_add(s0, c0, fold(p0));
+        kahan_add(s1, c1, fold(p1));
+      }
+      buf ^= 1;
+    }
+    __syncwarp();  // the window's ranges and tiles are no longer read
+  }
+  if (failed) return;
+  // the G groups' partial sums, added in group order (reproducible)
+  Acc<float> ta = s0, tb = s1;
+  for (int gg = 1; gg < G; ++gg) {
+    const int src_lane = gg * T2 + i;
+    Acc<float> va, vb;
+    va.p = __shfl_sync(0xffffffffu, s0.p, src_lane);
+    va.x = __shfl_sync(0xffffffffu, s0.x, src_lane);
+    va.y = __shfl_sync(0xffffffffu, s0.y, src_lane);
+    va.z = __shfl_sync(0xffffffffu, s0.z, src_lane);
+    vb.p = __shfl_sync(0xffffffffu, s1.p, src_lane);
+    vb.x = __shfl_sync(0xffffffffu, s1.x, src_lane);
+    vb.y = __shfl_sync(0xffffffffu, s1.y, src_lane);
+    vb.z = __shfl_sync(0xffffffffu, s1.z, src_lane);
+    ta.p += va.p; ta.x += va.x; ta.y += va.y; ta.z += va.z;
+    tb.p += vb.p; tb.x += vb.x; tb.y += vb.y; tb.z += vb.z;
+  }
+  if (g == 0 && active) {
+    GB_ST(near, t0 + i, lim.N, 109, make_float4(ta.p, ta.x, ta.y, ta.z));
+    if (has_b) GB_ST(near, t0 + i + T2, lim.N, 109, make_float4(tb.p, tb.x, tb.y, tb.z));
+  }
+}
+
+// The single-precision near field in one launch: blocks 0 .. nbig - 1 take one
+// item each (items with many targets or sources), the blocks after them four
+// items each, one per warp (items[nbig ..]).  Both parts share the block's
+// shared memory; lower block indices are dispatched first, so the many short
+// per-warp items fill the end of the per-block items.  Seven blocks per SM
+// (at most 73 registers a thread): the pair chains are latency-bound, so
+// resident warps count for more than a few spilled values.
+union P2PSmem {
+  BlockSmem b;
+  WarpSmem w;
+};
+
+__global__ void __launch_bounds__(kThreads, 7) k_p2p_mix(const float4* __restrict__ bodies,
+                                                      const SrcPair* __restrict__ pairs,
+                                                      const int4* __restrict__ items,
+                                                      const int2* __restrict__ item_rng, long long nbig,
+                                                      long long nsmall, const int2* __restrict__ ranges,
+                                                      float4* __restrict__ near, int* __restrict__ err, Lim lim) {
+  __shared__ __align__(16) P2PSmem sm;
+  if ((long long)blockIdx.x < nbig)
+    p2p_block_item(sm.b, blockIdx.x, bodies, pairs, items, item_rng, ranges, near, err, lim);
+  else
+    p2p_warp_items(sm.w, (long long)blockIdx.x - nbig, bodies, pairs, items + nbig, item_rng + nbig, nsmall,
+                   ranges, near, err, lim);
+}
+
 // Work items of the single-precision near field: a chunk of at most
 // kItemTargets targets of one leaf, with the leaf's bodies (its own source
 // range) and its neighbour ranges.  Per leaf, ceil(n / kItemTargets) chunks.
@@ -537,7 +799,7 @@ __global__ void __launch_bounds__(kThreads, 7) k_p2p_f2(const float4* __restrict
 // the last wave short on workloads with a few large leaves.
 constexpr int kItemTargets = kTgtChunk;
 __global__ void k_item_count(const int32_t* __restrict__ leaves, const int32_t* __restrict__ bbeg,
-                             const int32_t* __restrict__ bend, int nleaf, int64_t* __restrict__ cnt) {
+                             const int32_t* __restrict__ bend, int nleaf, int per, int64_t* __restrict__ cnt) {
   const int li = blockIdx.x * blockDim.x + threadIdx.x;
   if (li > nleaf) return;
   if (li == nleaf) {
@@ -545,16 +807,18 @@ __global__ void k_item_count(const int32_t* __restrict__ leaves, const int32_t* 
     return;
   }
   const int c = leaves[li];
-  cnt[li] = (bend[c] - bbeg[c] + kItemTargets - 1) / kItemTargets;
+  cnt[li] = (bend[c] - bbeg[c] + per - 1) / per;
 }
 
 // Sort key of an item: its work (targets x sources) in a 16-bit floating
 // form (6-bit exponent, 10-bit mantissa; monotone in the work), inverted so
-// that an ascending sort puts the largest first.  Padding slots take the
-// largest key.
+// that an ascending sort puts the largest first; bit 16 marks an item small
+// enough for the per-warp kernel, so that the items of the per-block kernel
+// come first.  Padding slots take the largest key.
 constexpr int kWorkBits = 16;
+constexpr int kKeyBits = kWorkBits + 1;
 __device__ __forceinline__ uint64_t work_key(uint64_t work) {
-  if (work == 0) return (1ull << kWorkBits) - 1;
+  if (work == 0) return (1ull << kWorkBits) - 1;  // (an item always has targets and sources)
   const int e = 63 - __clzll((long long)work);  // work < 2^63
   const uint64_t m = (e >= 10 ? work >> (e - 10) : work << (10 - e)) & 0x3ffull;
   return ((1ull << kWorkBits) - 1) - ((uint64_t)(e + 1) << 10 | m);
@@ -562,9 +826,10 @@ __device__ __forceinline__ uint64_t work_key(uint64_t work) {
 
 __global__ void k_item_fill(const int32_t* __restrict__ leaves, const int32_t* __restrict__ bbeg,
                             const int32_t* __restrict__ bend, const int32_t* __restrict__ rptr,
-                            const int2* __restrict__ ranges, int nleaf, const int64_t* __restrict__ ptr,
-                            int4* __restrict__ items, int2* __restrict__ rng, uint64_t* __restrict__ key,
-                            int32_t* __restrict__ val) {
+                            const int2* __restrict__ ranges, int nleaf, int per, int warp_src,
+                            const int64_t* __restrict__ ptr, int4* __restrict__ items, int2* __restrict__ rng,
+                            uint64_t* __restrict__ key, int32_t* __restrict__ val,
+                            unsigned long long* __restrict__ nbig) {
   const int li = blockIdx.x * blockDim.x + threadIdx.x;
   if (li >= nleaf) return;
   const int c = leaves[li];
@@ -572,14 +837,21 @@ __global__ void k_item_fill(const int32_t* __restrict__ leaves, const int32_t* _
   long long src = e - s;
   for (int r = r0; r < r1; ++r) src += ranges[r].y - ranges[r].x;
   const int64_t p0 = ptr[li];
-  for (int k = 0; s + k * kItemTargets < e; ++k) {
-    const int t0 = s + k * kItemTargets, nt = min(kItemTargets, e - t0);
+  for (int k = 0; s + k * per < e; ++k) {
+    const int t0 = s + k * per, nt = min(per, e - t0);
     const int64_t idx = p0 + k;
     items[idx] = make_int4(t0, nt, s, e);
     rng[idx] = make_int2(r0, r1);
     const uint64_t work = (uint64_t)nt * (uint64_t)src;
-    key[idx] = work_key(work);
+    // the per-block code splits every tile among 128 / ceil(nt / 2) thread
+    // groups, so on items with few targets and few sources its fixed costs
+    // (block barriers per tile, the groups' reduction) outweigh the pairs:
+    // those go to one warp each, whose smaller tiles cost more on long
+    // source lists
+    const bool small = nt <= kWarpSmallTargets && src <= warp_src;
+    key[idx] = work_key(work) | (small ? 1ull << kWorkBits : 0ull);
     val[idx] = (int32_t)idx;
+    if (!small) atomicAdd(nbig, 1ull);
   }
 }
 
@@ -587,7 +859,7 @@ __global__ void k_item_pad(const int64_t* __restrict__ total, int64_t nmax, uint
                            int32_t* __restrict__ val) {
   const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (k >= nmax || k < *total) return;
-  key[k] = (1ull << kWorkBits) - 1;
+  key[k] = (1ull << kKeyBits) - 1;
   val[k] = (int32_t)k;
 }
 
@@ -694,6 +966,18 @@ __global__ void __launch_bounds__(kThreads) k_p2p_mutual(const R4* __restrict__ 
   }
 }
 
+// Work items of at most kWarpSmallTargets targets and this many sources (the
+// leaf's own bodies included) go to the per-warp code, the others to the
+// per-block code (GBFMM_P2P_WARP_SRC: a tuning knob).
+int p2p_warp_src() {
+  static const int v = [] {
+    const char* env = getenv("GBFMM_P2P_WARP_SRC");
+    const int x = env ? atoi(env) : 2048;
+    return x < 0 ? 0 : x;
+  }();
+  return v;
+}
+
 }  // namespace
 
 template <class R>
@@ -712,11 +996,16 @@ void launch_p2p(fmm_tree* t, cudaStream_t s) {
     k_pair_bodies<<<(unsigned)((npair + 255) / 256), 256, 0, s>>>((const float4*)t->work, t->N,
                                                                   (SrcPair*)t->near_src);
     GB_LAUNCH("k_pair_bodies");
-    k_p2p_f2<<<(unsigned)t->p2p_nitem_host, kThreads, 0, s>>>((const float4*)t->work,
-                                                              (const SrcPair*)t->near_src, t->p2p_items,
-                                                              t->p2p_item_rng, t->p2p_ranges, (float4*)t->near,
-                                                              t->dev_err, t->lim);
-    GB_LAUNCH("k_p2p_f2");
+    // items of more than the warp kernel's target limit: one per block;
+    // the rest (after them in the list): one per warp
+    const long long nbig = t->p2p_nbig_host, nsmall = t->p2p_nitem_host - nbig;
+    const long long nblk = nbig + (nsmall + kWarpsP2P - 1) / kWarpsP2P;
+    if (nblk > 0) {
+      k_p2p_mix<<<(unsigned)nblk, kThreads, 0, s>>>((const float4*)t->work, (const SrcPair*)t->near_src,
+                                                    t->p2p_items, t->p2p_item_rng, nbig, nsmall, t->p2p_ranges,
+                                                    (float4*)t->near, t->dev_err, t->lim);
+      GB_LAUNCH("k_p2p_mix");
+    }
     return;
   }
   k_p2p<R, R4><<<t->nleaf, kThreads, 0, s>>>((const R4*)t->work, t->leaves, t->c.bbeg, t->c.bend, t->p2p_rptr,
@@ -731,23 +1020,26 @@ void build_p2p_items(fmm_tree* t) {
   Arena& a = t->arena;
   cudaStream_t s = t->stream;
   const int nleaf = (int)t->nleaf;
-  const int64_t nmax = (int64_t)nleaf + t->N / kItemTargets + 1;
+  const int per = kItemTargets;
+  const int64_t nmax = (int64_t)nleaf + t->N / per + 1;
   const unsigned bl = (unsigned)((nleaf + 1 + 255) / 256), bm = (unsigned)((nmax + 255) / 256);
   int64_t* ptr = alloc_n<int64_t>(a, nleaf + 1);
-  k_item_count<<<bl, 256, 0, s>>>(t->leaves, t->c.bbeg, t->c.bend, nleaf, ptr);
+  k_item_count<<<bl, 256, 0, s>>>(t->leaves, t->c.bbeg, t->c.bend, nleaf, per, ptr);
   GB_LAUNCH("k_item_count");
-  t->p2p_nitem = alloc_n<long long>(a, 1);
+  t->p2p_nitem = alloc_n<long long>(a, 2);  // item count, then the count of per-block items
+  GB_CK(cudaMemsetAsync(t->p2p_nitem + 1, 0, sizeof(long long), s));
   scan_exclusive_i64_dev(a, ptr, nleaf + 1, (int64_t*)t->p2p_nitem, s);
   int4* items = alloc_n<int4>(a, nmax);
   int2* rng = alloc_n<int2>(a, nmax);
   uint64_t* key = alloc_n<uint64_t>(a, nmax);
   int32_t* val = alloc_n<int32_t>(a, nmax);
-  k_item_fill<<<bl, 256, 0, s>>>(t->leaves, t->c.bbeg, t->c.bend, t->p2p_rptr, t->p2p_ranges, nleaf, ptr, items,
-                                 rng, key, val);
+  k_item_fill<<<bl, 256, 0, s>>>(t->leaves, t->c.bbeg, t->c.bend, t->p2p_rptr, t->p2p_ranges, nleaf, per,
+                                 p2p_warp_src(), ptr, items, rng, key, val,
+                                 reinterpret_cast<unsigned long long*>(t->p2p_nitem + 1));
   GB_LAUNCH("k_item_fill");
   k_item_pad<<<bm, 256, 0, s>>>((const int64_t*)t->p2p_nitem, nmax, key, val);
   GB_LAUNCH("k_item_pad");
-  radix_sort_pairs(a, key, val, nmax, kWorkBits, s);
+  radix_sort_pairs(a, key, val, nmax, kKeyBits, s);
   t->p2p_items = alloc_n<int4>(a, nmax);
   t->p2p_item_rng = alloc_n<int2>(a, nmax);
   k_item_gather<<<bm, 256, 0, s>>>(val, nmax, items, rng, t->p2p_items, t->p2p_item_rng);
