@@ -71,6 +71,7 @@ def _load(path: str):
     L.orc_build.argtypes = [_D, ctypes.c_int64, ctypes.c_int, ctypes.c_double, ctypes.c_int,
                             ctypes.c_int, ctypes.POINTER(ctypes.c_void_p)]
     L.orc_set_order.argtypes = [ctypes.c_void_p, ctypes.c_int]
+    L.orc_centres.argtypes = [ctypes.c_void_p, _D]
     L.orc_free.argtypes = [ctypes.c_void_p]
     L.orc_free.restype = None
     L.orc_info.argtypes = [ctypes.c_void_p, _I64]
@@ -110,17 +111,22 @@ class OracleTree:
     """Tree, lists and evaluation of the oracle for one particle set.
 
     xyzq: (N, 4) array of x, y, z, q (any float dtype, widened to double).
+    circumscribed / tight: the MAC radius (half diagonal; distance from the
+    cube centre to the farthest body).  fitted: expansion centres at the
+    centre of the box of the cell's bodies (their voxel centres), the MAC
+    radius the distance from there to the farthest body.
     """
 
     def __init__(self, xyzq, p: int, theta: float, ncrit: int, circumscribed: bool = False,
-                 tight: bool = False):
+                 tight: bool = False, fitted: bool = False):
         L = lib()
         self.xyzq = _f64(xyzq).reshape(-1, 4)
         self.N = self.xyzq.shape[0]
         self.p = int(p)
         h = ctypes.c_void_p()
         rc = L.orc_build(_dp(self.xyzq), self.N, self.p, float(theta), int(ncrit),
-                         (1 if circumscribed else 0) | (2 if tight else 0), ctypes.byref(h))
+                         (1 if circumscribed else 0) | (2 if tight else 0) | (4 if fitted else 0),
+                         ctypes.byref(h))
         if rc != 0:
             raise ValueError(f"oracle build failed with code {rc}")
         self._h = h
@@ -130,6 +136,12 @@ class OracleTree:
         if h is not None and h.value:
             lib().orc_free(h)
             self._h = None
+
+    def centres(self) -> np.ndarray:
+        """Expansion centre of every cell, (ncell, 3)."""
+        out = np.zeros((self.info()["ncell"], 3))
+        lib().orc_centres(self._h, _dp(out))
+        return out
 
     def set_order(self, p: int) -> None:
         """Evaluate with p terms from now on (same tree and lists)."""

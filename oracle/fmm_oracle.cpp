@@ -246,7 +246,9 @@ struct Tree {
   int ncrit = 0;
   int circumscribed = 0;
   int tight = 0;                         // particle-fitted MAC radius (Sec. II.B)
-  std::vector<int64_t> r2;               // its square per cell (tight only)
+  int fitted = 0;                        // expansion centres at the particle-fitted box (Sec. II.B)
+  std::vector<int64_t> r2;               // squared radius per cell (tight or fitted)
+  std::vector<int64_t> cint;             // fitted: 3 integer centre coordinates per cell (units H / 2^21)
   double lo[3], hi[3], ctr[3], H = 0, r0[3];
   std::vector<double> xyz, q;            // input order (3N, N)
   std::vector<uint64_t> key_sorted;      // keys in sorted order
@@ -391,13 +393,55 @@ void tight_radii(Tree& t) {
   }
 }
 
+// Particle-fitted centres (fitted): per axis the box of the cell's voxel
+// centres 2u + 1 runs from 2 u_min + 1 to 2 u_max + 1, so its centre is the
+// integer u_min + u_max + 1 (units of H / 2^21); the radius is the distance
+// from that centre to the farthest voxel centre, its square an exact integer.
+// The MAC then measures |c_A - c_B| between the fitted centres, and every
+// expansion (P2M, M2M, M2L, L2L, L2P) is taken about them.
+void fitted_centres(Tree& t) {
+  const int n = (int)t.level.size();
+  t.r2.assign(n, 0);
+  t.cint.assign(3 * (size_t)n, 0);
+  for (int c = 0; c < n; ++c) {
+    int64_t lo[3] = {INT64_MAX, INT64_MAX, INT64_MAX}, hi[3] = {-1, -1, -1};
+    for (int i = t.bbeg[c]; i < t.bend[c]; ++i) {
+      const uint64_t k = t.key_sorted[i];
+      const int64_t u[3] = {(int64_t)gather3(k >> 2), (int64_t)gather3(k >> 1), (int64_t)gather3(k)};
+      for (int a = 0; a < 3; ++a) {
+        lo[a] = std::min(lo[a], u[a]);
+        hi[a] = std::max(hi[a], u[a]);
+      }
+    }
+    int64_t ctr[3];
+    for (int a = 0; a < 3; ++a) ctr[a] = t.cint[3 * (size_t)c + a] = lo[a] + hi[a] + 1;
+    int64_t best = 0;
+    for (int i = t.bbeg[c]; i < t.bend[c]; ++i) {
+      const uint64_t k = t.key_sorted[i];
+      const int64_t u[3] = {(int64_t)gather3(k >> 2), (int64_t)gather3(k >> 1), (int64_t)gather3(k)};
+      int64_t d2 = 0;
+      for (int a = 0; a < 3; ++a) {
+        const int64_t d = 2 * u[a] + 1 - ctr[a];
+        d2 += d * d;
+      }
+      best = std::max(best, d2);
+    }
+    t.r2[c] = best;
+  }
+}
+
 bool mac(const Tree& t, int A, int B) {
   const int la = t.level[A], lb = t.level[B];
   int64_t dx = ((2ll * t.ix[A] + 1) << (MAXLEVEL - la)) - ((2ll * t.ix[B] + 1) << (MAXLEVEL - lb));
   int64_t dy = ((2ll * t.iy[A] + 1) << (MAXLEVEL - la)) - ((2ll * t.iy[B] + 1) << (MAXLEVEL - lb));
   int64_t dz = ((2ll * t.iz[A] + 1) << (MAXLEVEL - la)) - ((2ll * t.iz[B] + 1) << (MAXLEVEL - lb));
+  if (t.fitted) {
+    dx = t.cint[3 * (size_t)A] - t.cint[3 * (size_t)B];
+    dy = t.cint[3 * (size_t)A + 1] - t.cint[3 * (size_t)B + 1];
+    dz = t.cint[3 * (size_t)A + 2] - t.cint[3 * (size_t)B + 2];
+  }
   int64_t D2 = dx * dx + dy * dy + dz * dz;
-  if (t.tight) {
+  if (t.tight || t.fitted) {
     const double sr = std::sqrt((double)t.r2[A]) + std::sqrt((double)t.r2[B]);
     return (t.theta * t.theta) * (double)D2 > sr * sr;
   }
@@ -472,6 +516,11 @@ void make_csr(int ncell, std::vector<std::pair<int, int>>& pairs, std::vector<in
 }
 
 void cell_centre(const Tree& t, int c, double out[3]) {
+  if (t.fitted) {
+    const double unit = std::ldexp(t.H, -MAXLEVEL);
+    for (int a = 0; a < 3; ++a) out[a] = t.r0[a] + (double)t.cint[3 * (size_t)c + a] * unit;
+    return;
+  }
   const double R = std::ldexp(t.H, -t.level[c]);
   out[0] = t.r0[0] + (2.0 * t.ix[c] + 1.0) * R;
   out[1] = t.r0[1] + (2.0 * t.iy[c] + 1.0) * R;
@@ -594,7 +643,8 @@ int orc_set_threads(int n) {
 }
 
 // xyzq: N x 4 doubles (x, y, z, q) in input order.
-// mac: bit 0 circumscribed radius, bit 1 particle-fitted (tight) radius.
+// mac: bit 0 circumscribed radius, bit 1 particle-fitted (tight) radius about
+// the cube centre, bit 2 particle-fitted centres and radii (fitted).
 int orc_build(const double* xyzq, int64_t N, int p, double theta, int ncrit, int mac_mode,
               void** out) {
   if (!xyzq || !out || N < 1 || p < 1 || p > 30 || !(theta > 0.0) || ncrit < 1) return -1;
@@ -608,6 +658,7 @@ int orc_build(const double* xyzq, int64_t N, int p, double theta, int ncrit, int
   t->ncrit = ncrit;
   t->circumscribed = (mac_mode & 1) ? 1 : 0;
   t->tight = (mac_mode & 2) ? 1 : 0;
+  t->fitted = (mac_mode & 4) ? 1 : 0;
   t->xyz.resize(3 * N);
   t->q.resize(N);
   for (int64_t i = 0; i < N; ++i) {
@@ -626,7 +677,8 @@ int orc_build(const double* xyzq, int64_t N, int p, double theta, int ncrit, int
   t->key_sorted.resize(N);
   for (int64_t i = 0; i < N; ++i) t->key_sorted[i] = key_in[t->perm[i]];
   build_cells(*t);
-  if (t->tight) tight_radii(*t);
+  if (t->fitted) fitted_centres(*t);
+  else if (t->tight) tight_radii(*t);
   Traversal tr(*t);
   tr.visit(0, 0);
   const int ncell = (int)t->level.size();
@@ -637,6 +689,13 @@ int orc_build(const double* xyzq, int64_t N, int p, double theta, int ncrit, int
 }
 
 void orc_free(void* t) { delete (Tree*)t; }
+
+// Expansion centre of every cell (ncell x 3 doubles).
+int orc_centres(void* tp, double* out) {
+  Tree& t = *(Tree*)tp;
+  for (size_t c = 0; c < t.level.size(); ++c) cell_centre(t, (int)c, out + 3 * c);
+  return 0;
+}
 
 // Expansion order of later evaluations.  The tree and the lists do not
 // depend on it (Sec. III.A: P only sets the number of terms), so one build

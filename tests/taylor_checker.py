@@ -100,9 +100,10 @@ def m2l_pair(p: int, D, b: np.ndarray, q: np.ndarray, a: np.ndarray):
     return phi, grad
 
 
-def evaluate(xyzq: np.ndarray, p: int, cells: dict, lists: dict, keys_perm, root: dict):
+def evaluate(xyzq: np.ndarray, p: int, cells: dict, lists: dict, keys_perm, root: dict, centres=None):
     """(phi, grad) in input order from the oracle's tree and lists, using only
-    direct P2P sums and per-pair Cartesian double-Taylor M2L."""
+    direct P2P sums and per-pair Cartesian double-Taylor M2L.  centres: the
+    expansion centre of every cell, (ncell, 3); default the cube centres."""
     xyzq = np.asarray(xyzq, np.float64)
     _, perm = keys_perm
     xs = xyzq[perm, :3]
@@ -113,6 +114,8 @@ def evaluate(xyzq: np.ndarray, p: int, cells: dict, lists: dict, keys_perm, root
     lev = cells["level"]
     cen = np.stack([r0[i] + (2.0 * cells[k] + 1.0) * np.ldexp(H, -lev)
                     for i, k in enumerate(("ix", "iy", "iz"))], axis=1)
+    if centres is not None:
+        cen = np.asarray(centres, np.float64)
     bb, be = cells["body_begin"], cells["body_end"]
     phi = np.zeros(N)
     grad = np.zeros((N, 3))

@@ -2,8 +2,8 @@
 
 Each case plants one plausible mistake in a copy of ``oracle/fmm_oracle.cpp``:
 a dropped term, a wrong sign, a wrong index or a swapped operand, in every stage
-of the path (harmonics, P2M, M2M, M2L, L2L, L2P, P2P, keys, tree, MAC,
-traversal, adjoint, direct sum).  The copy is built with the oracle's own
+of the path (harmonics, P2M, M2M, M2L, L2L, L2P, P2P, keys, tree, MAC, the
+particle-fitted centres and radii, traversal, adjoint, direct sum).  The copy is built with the oracle's own
 compiler flags, and the pins of ``test_oracle_pins.py`` and the properties of
 ``test_oracle_properties.py`` run against it in a child process; at least one
 must fail.  The unmutated copy goes through the
@@ -58,6 +58,13 @@ MUTANTS = [
     ("tight_radius_not_max", "void tight_radii(", "best = std::max(best, d2);", "best = d2;"),
     ("tight_voxel_corner", "void tight_radii(", "const int64_t d = 2 * u[a] + 1 - ctr[a];",
      "const int64_t d = 2 * u[a] - ctr[a];"),
+    ("fitted_centre_off_by_one", "void fitted_centres(",
+     "ctr[a] = t.cint[3 * (size_t)c + a] = lo[a] + hi[a] + 1;",
+     "ctr[a] = t.cint[3 * (size_t)c + a] = lo[a] + hi[a];"),
+    ("fitted_radius_not_max", "void fitted_centres(", "best = std::max(best, d2);", "best = d2;"),
+    ("fitted_mac_cube_distance", "bool mac(", "if (t.fitted) {", "if (false) {"),
+    ("fitted_centre_unit", "void cell_centre(", "const double unit = std::ldexp(t.H, -MAXLEVEL);",
+     "const double unit = std::ldexp(t.H, -MAXLEVEL + 1);"),
     ("mac_accepts_ties", "bool mac(", "return (t.theta * t.theta) * (double)D2 > (double)S2;",
      "return (t.theta * t.theta) * (double)D2 >= (double)S2;"),
     ("mac_theta_not_squared", "bool mac(",

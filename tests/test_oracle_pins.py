@@ -340,6 +340,147 @@ def test_tight_mac_error_decreases_with_p(orc):
     assert all(b < a for a, b in zip(e, e[1:]))
 
 
+# ------------------------------------------- particle-fitted centres (f3)
+# Sec. II.B: cells are squeezed to fit their particles.  With fitted=True the
+# oracle takes every expansion about the centre of the box of the cell's
+# bodies (their voxel centres 2u + 1, u the 21-bit coordinates; units of
+# H / 2^21), and the MAC radius is the distance from there to the farthest
+# voxel centre.  The pins below derive centres and radii here, from the
+# bodies' coordinates, and check the oracle against them.
+
+def _voxels(T):
+    """(N, 3) int64 voxel coordinates u of the sorted bodies, from the keys
+    (the keys themselves are pinned against their definition)."""
+    keys, _ = T.keys()
+    return np.stack([_deinterleave(keys, 2), _deinterleave(keys, 1), _deinterleave(keys, 0)], 1)
+
+
+def _fitted_geometry(T):
+    """Per cell: the integer centre u_min + u_max + 1 of its voxel box, the
+    squared distance to its farthest voxel centre (exact integers) and the
+    physical centre corner + centre * H / 2^21."""
+    u = _voxels(T)
+    c = T.cells()
+    bb, be = c["body_begin"], c["body_end"]
+    n = c["level"].size
+    ctr = np.zeros((n, 3), np.int64)
+    r2 = np.zeros(n, np.int64)
+    for i in range(n):
+        ui = u[bb[i]:be[i]]
+        ctr[i] = ui.min(0) + ui.max(0) + 1
+        r2[i] = int(((2 * ui + 1 - ctr[i]) ** 2).sum(1).max())
+    r = T.root()
+    phys = r["corner"][None, :] + ctr.astype(np.float64) * np.ldexp(r["H"], -21)
+    return ctr, r2, phys
+
+
+def test_fitted_centres_are_the_box_centres(orc):
+    x = W.plummer(2500, 61)
+    T = orc.OracleTree(x, 4, 0.5, 10, fitted=True)
+    ctr, r2, phys = _fitted_geometry(T)
+    assert np.array_equal(T.centres(), phys)
+    # every body lies within the fitted radius of its cell's centre (up to
+    # its voxel: one unit per axis)
+    c = T.cells()
+    bb, be = c["body_begin"], c["body_end"]
+    _, perm = T.keys()
+    r = T.root()
+    xs = (np.asarray(x, np.float64)[perm, :3] - r["corner"]) * (2.0 ** 21 / r["H"])
+    for i in range(ctr.shape[0]):
+        d = np.sqrt(((xs[bb[i]:be[i]] - ctr[i]) ** 2).sum(1)).max()
+        assert d <= math.sqrt(r2[i]) + math.sqrt(3.0) + 1e-6
+    # a fitted box is never wider than its cube: the centre stays inside it
+    lev = c["level"].astype(np.int64)
+    ijk = np.stack([c["ix"], c["iy"], c["iz"]], 1).astype(np.int64)
+    lo = (2 * ijk) << (21 - lev)[:, None]
+    hi = (2 * ijk + 2) << (21 - lev)[:, None]
+    assert np.all((ctr >= lo) & (ctr <= hi))
+
+
+@pytest.mark.parametrize("theta", [0.5, 0.6])
+def test_fitted_lists_follow_the_acceptance_criterion(orc, theta):
+    """Every M2L pair passes theta |c_A - c_B| > r_A + r_B with the fitted
+    centres and radii derived here, every P2P pair of distinct leaves fails
+    it, and every body pair is covered exactly once."""
+    x = W.plummer(1500, 62)
+    T = orc.OracleTree(x, 4, theta, 8, fitted=True)
+    ctr, r2, _ = _fitted_geometry(T)
+    rad = [math.sqrt(float(v)) for v in r2]
+    L = T.lists()
+
+    def accepted(a, b):
+        d = ctr[a] - ctr[b]
+        s = rad[a] + rad[b]
+        return (theta * theta) * float(int(d @ d)) > s * s
+
+    assert len(L["m2l_tgt"]) > 0
+    assert all(accepted(t, s) for t, s in zip(L["m2l_tgt"], L["m2l_src"]))
+    far_p2p = [(t, s) for t, s in zip(L["p2p_tgt"], L["p2p_src"]) if t != s]
+    assert not any(accepted(t, s) for t, s in far_p2p)
+    c = T.cells()
+    N = x.shape[0]
+    bb, be = c["body_begin"], c["body_end"]
+    cnt = np.zeros((N, N), np.int32)
+    for key in (("p2p_tgt", "p2p_src"), ("m2l_tgt", "m2l_src")):
+        for t, s in zip(L[key[0]], L[key[1]]):
+            cnt[bb[t]:be[t], bb[s]:be[s]] += 1
+    assert np.all(cnt == 1)
+    # fitting the centres as well as the radii sends fewer body pairs to P2P
+    Ttight = orc.OracleTree(x, 4, theta, 8, tight=True)
+    assert T.info()["p2p_pairs"] < Ttight.info()["p2p_pairs"]
+
+
+@pytest.mark.parametrize("dist,p", [("plummer", 4), ("cube", 5)])
+def test_fitted_matches_cartesian_taylor_checker(orc, dist, p):
+    """With the centres derived here, the basis-free double Taylor closed form
+    equals the oracle: pins P2M/M2M/M2L/L2L/L2P about moved centres."""
+    x = W.cube(600, 63) if dist == "cube" else W.plummer(600, 64)
+    T = orc.OracleTree(x, p, 0.5, 12, fitted=True)
+    assert T.info()["n_m2l"] > 0
+    _, _, phys = _fitted_geometry(T)
+    ph, g = T.evaluate()
+    ph2, g2 = taylor_checker.evaluate(x, p, T.cells(), T.lists(), T.keys(), T.root(), centres=phys)
+    assert rel(ph, ph2) < 1e-12
+    assert rel(g, g2) < 1e-11
+
+
+def test_fitted_error_decreases_with_p(orc):
+    x = W.plummer(3000, 65)
+    pd, _ = orc.direct(x)
+    e = [rel(orc.OracleTree(x, p, 0.5, 16, fitted=True).evaluate()[0], pd) for p in (3, 5, 7, 9)]
+    assert all(b < a for a, b in zip(e, e[1:]))
+
+
+def test_fitted_operator_symmetry_and_adjoint(orc):
+    """The double truncation about two moved centres is still symmetric
+    (1/r is even), so w.FMM(q) = q.FMM(w) and the frozen-centre adjoint is the
+    exact derivative: central differences (h = 1e-6) with the tree, lists and
+    centres frozen agree with it."""
+    rng = np.random.default_rng(66)
+    N = 1024
+    xyzq = np.concatenate([rng.random((N, 3)), rng.uniform(-1, 1, (N, 1))], axis=1)
+    w = rng.standard_normal(N)
+    T = orc.OracleTree(xyzq, 7, 0.5, 32, fitted=True)
+    q0 = xyzq[:, 3].copy()
+    pq, _ = T.evaluate(q=q0)
+    pw, _ = T.evaluate(q=w)
+    assert abs(w @ pq - q0 @ pw) <= 1e-12 * np.abs(w) @ np.abs(pq)
+    dq, dx = T.backward(w)
+    xyz0 = xyzq[:, :3].copy()
+
+    def loss(xyz):
+        return w @ T.evaluate(q=q0, xyz=xyz)[0]
+
+    h = 1e-6
+    for i in rng.choice(N, 12, replace=False):
+        for a in range(3):
+            xp = xyz0.copy(); xp[i, a] += h
+            xm = xyz0.copy(); xm[i, a] -= h
+            fd = (loss(xp) - loss(xm)) / (2 * h)
+            assert abs(fd - dx[i, a]) <= 1e-6 * (abs(dx[i, a]) + 1e-3 * np.abs(dx).max())
+    assert rel(dq, pw) < 1e-14
+
+
 def _deinterleave(keys, shift):
     u = np.zeros(keys.shape, np.int64)
     for b in range(21):

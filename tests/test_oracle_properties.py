@@ -16,6 +16,8 @@ error.
 import numpy as np
 import pytest
 
+from tests.test_oracle_pins import _fitted_geometry
+
 hyp = pytest.importorskip("hypothesis")
 from hypothesis import HealthCheck, given, settings  # noqa: E402
 from hypothesis import strategies as st  # noqa: E402
@@ -78,9 +80,9 @@ def _bodies_in_cells(T, x):
 
 @settings(max_examples=300, deadline=None, derandomize=True, suppress_health_check=[HealthCheck.too_slow])
 @given(x=body_sets(), ncrit=st.integers(1, 12), theta=st.sampled_from([0.3, 0.5, 0.7, 0.95]),
-       mode=st.sampled_from(["half", "circumscribed", "tight"]))
+       mode=st.sampled_from(["half", "circumscribed", "tight", "fitted"]))
 def test_traversal_covers_every_pair_once(orc, x, ncrit, theta, mode):
-    T = orc.OracleTree(x, 3, theta, ncrit, circumscribed=mode == "circumscribed", tight=mode == "tight")
+    T = _tree(orc, x, 3, theta, ncrit, mode)
     _covered_once(T, x.shape[0])
     _bodies_in_cells(T, x)
 
@@ -128,13 +130,13 @@ def test_potential_error_within_the_truncation_bound(orc, x, ncrit, theta, p):
 
 @settings(max_examples=150, deadline=None, derandomize=True, suppress_health_check=[HealthCheck.too_slow])
 @given(x=body_sets(FAR_FIELD_SCALES), ncrit=st.integers(1, 12), theta=st.sampled_from([0.3, 0.5, 0.7]),
-       p=st.integers(1, 7), mode=st.sampled_from(["half", "circumscribed", "tight"]),
+       p=st.integers(1, 7), mode=st.sampled_from(["half", "circumscribed", "tight", "fitted"]),
        wseed=st.integers(0, 2 ** 31 - 1))
 def test_operator_is_symmetric(orc, x, ncrit, theta, p, mode, wseed):
     """The truncated kernel of an M2L pair is a polynomial of degree < p in each
     of the two offsets with the coefficients of the even 1/r, and the lists are
     symmetric, so the FMM operator is symmetric: w . FMM(q) = q . FMM(w)."""
-    T = orc.OracleTree(x, p, theta, ncrit, circumscribed=mode == "circumscribed", tight=mode == "tight")
+    T = _tree(orc, x, p, theta, ncrit, mode)
     q = x[:, 3]
     w = np.random.default_rng(wseed).uniform(-1, 1, x.shape[0])
     pq, _ = T.evaluate(q)
@@ -148,15 +150,18 @@ def test_operator_is_symmetric(orc, x, ncrit, theta, p, mode, wseed):
 
 @settings(max_examples=60, deadline=None, derandomize=True, suppress_health_check=[HealthCheck.too_slow])
 @given(x=body_sets((1e-3, 1.0, 1e3)), ncrit=st.integers(1, 8), theta=st.sampled_from([0.5, 0.7]),
-       p=st.integers(1, 4), mode=st.sampled_from(["half", "circumscribed", "tight"]))
+       p=st.integers(1, 4), mode=st.sampled_from(["half", "circumscribed", "tight", "fitted"]))
 def test_matches_the_cartesian_checker(orc, x, ncrit, theta, p, mode):
     """The whole oracle equals the basis-free double Taylor closed form of the
     same lists (an independent Cartesian evaluation with no M2M or L2L)."""
     from tests import taylor_checker
     x = x[:60]
-    T = orc.OracleTree(x, p, theta, ncrit, circumscribed=mode == "circumscribed", tight=mode == "tight")
+    T = _tree(orc, x, p, theta, ncrit, mode)
     ph, g = T.evaluate()
-    ph2, g2 = taylor_checker.evaluate(x, p, T.cells(), T.lists(), T.keys(), T.root())
+    # fitted: the centres derived from the bodies' voxel coordinates, not read
+    # from the oracle
+    centres = _fitted_geometry(T)[2] if mode == "fitted" else None
+    ph2, g2 = taylor_checker.evaluate(x, p, T.cells(), T.lists(), T.keys(), T.root(), centres=centres)
     # sizes of the summed terms, sum_j |q_j| / r_ij and sum_j |q_j| / r_ij^2,
     # set the rounding tolerance
     d = np.linalg.norm(x[:, None, :3] - x[None, :, :3], axis=2)
@@ -165,6 +170,11 @@ def test_matches_the_cartesian_checker(orc, x, ncrit, theta, p, mode):
     s2 = (inv * inv) @ np.abs(x[:, 3])
     assert np.all(np.abs(ph - ph2) <= 1e-11 * s1)
     assert np.all(np.abs(g - g2).max(1) <= 1e-10 * s2)
+
+
+def _tree(orc, x, p, theta, ncrit, mode):
+    return orc.OracleTree(x, p, theta, ncrit, circumscribed=mode == "circumscribed", tight=mode == "tight",
+                          fitted=mode == "fitted")
 
 
 def _brute_tree(x, ncrit):
