@@ -174,7 +174,8 @@ def run_gpu(args):
     stream = torch.cuda.current_stream(dev)
 
     extra = F.FMM_FLAG_MUTUAL_P2P if args.p2p == "mutual" else 0
-    extra |= {"half": 0, "circ": F.FMM_FLAG_CIRCUMSCRIBED, "tight": F.FMM_FLAG_TIGHT_MAC}[args.mac]
+    extra |= {"half": 0, "circ": F.FMM_FLAG_CIRCUMSCRIBED, "tight": F.FMM_FLAG_TIGHT_MAC,
+              "fitted": F.FMM_FLAG_FITTED_CENTRES}[args.mac]
 
     def step(flags=F.FMM_FLAG_TIMING):
         T = F.Tree(x, p, theta, ncrit, flags | extra)
@@ -340,7 +341,7 @@ def cpu_baseline(workload: str, steps: int, mac: str = "half") -> dict:
     t0 = time.perf_counter()
     for _ in range(steps):
         T = oracle.OracleTree(x, spec["p"], spec["theta"], spec["ncrit"], circumscribed=mac == "circ",
-                              tight=mac == "tight")
+                              tight=mac == "tight", fitted=mac == "fitted")
         T.backward(w)  # evaluates with q (forward) and with w (adjoint)
         del T
     dt = time.perf_counter() - t0
@@ -474,8 +475,9 @@ def main():
     ap.add_argument("--sweep", default=None, choices=["precision"],
                     help="precision/scale sweep (cube16m: FP32 vs all-FP64 at p = 4..16), JSON lines")
     ap.add_argument("--sweep-max-p-f64", type=int, default=16, help="largest p of the double path in the sweep")
-    ap.add_argument("--mac", default="half", choices=["half", "circ", "tight"],
-                    help="MAC radius: half side of the cube (default), half diagonal, or particle-fitted")
+    ap.add_argument("--mac", default="half", choices=["half", "circ", "tight", "fitted"],
+                    help="MAC radius: half side of the cube (default), half diagonal, particle-fitted; "
+                         "fitted: expansion centres and radii fitted to the bodies")
     ap.add_argument("--p2p", default="one-sided", choices=["one-sided", "mutual"],
                     help="near field: one block per target leaf, or mutual interaction")
     args = ap.parse_args()

@@ -73,11 +73,20 @@ enum {
   FMM_FLAG_MUTUAL_P2P = 1u << 5,    /* near field by mutual interaction: each unordered leaf
                                        pair visited once, both leaves updated (floating-point
                                        atomics: results are not bit-reproducible) */
-  FMM_FLAG_TIGHT_MAC = 1u << 6      /* MAC radius of a cell = the distance from its (cube)
+  FMM_FLAG_TIGHT_MAC = 1u << 6,     /* MAC radius of a cell = the distance from its (cube)
                                        centre to its farthest body, from the 21-bit integer
                                        body coordinates (Sec. II.B's particle-fitted bound;
                                        expansion centres stay the cube centres); overrides
                                        FMM_FLAG_CIRCUMSCRIBED */
+  FMM_FLAG_FITTED_CENTRES = 1u << 7 /* cells fitted to their bodies (Sec. II.B): every
+                                       expansion is taken about the centre of the box of the
+                                       cell's bodies (their voxel centres, 21-bit integer
+                                       coordinates), and the MAC uses those centres and the
+                                       distance from there to the farthest body.  Operators are
+                                       no longer shared between cell pairs: M2M, L2L and M2L
+                                       run per pair on CUDA cores.  The adjoint keeps the
+                                       centres frozen.  Overrides FMM_FLAG_CIRCUMSCRIBED and
+                                       FMM_FLAG_TIGHT_MAC */
 };
 
 /* Optional stream-ordered allocator.  NULL selects the library's memory pool
@@ -117,7 +126,8 @@ typedef struct {
   double theta;
   uint32_t flags;
   int32_t m2l_engine;        /* 0 CUDA cores; tensor cores (tcgen05, 3xTF32): 1 one tile
-                                per CTA, 2 four tiles per CTA sharing each operator */
+                                per CTA, 2 four tiles per CTA sharing each operator;
+                                3 per pair on CUDA cores (FMM_FLAG_FITTED_CENTRES) */
   int64_t workspace_bytes;   /* device bytes held by the tree */
   int32_t evaluations;       /* fmm_evaluate calls on this tree */
   int32_t device_errors;     /* bits of the tree's device error word, sticky for

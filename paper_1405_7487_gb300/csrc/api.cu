@@ -38,7 +38,8 @@ void create_tree(fmm_tree* t, const R* xyzq) {
   t->precision = f64 ? 64 : 32;
   t->K = t->p * t->p;
   t->Kp = (t->K + 15) / 16 * 16;
-  t->m2l_engine = (!f64 && !(t->flags & FMM_FLAG_M2L_CUDA_CORE)) ? 1 : 0;
+  const bool fitted = (t->flags & FMM_FLAG_FITTED_CENTRES) != 0;
+  t->m2l_engine = fitted ? 3 : ((!f64 && !(t->flags & FMM_FLAG_M2L_CUDA_CORE)) ? 1 : 0);
   {
     int lo = 0, hi = 0;  // numerically greatest = lowest priority
     GB_CK(cudaDeviceGetStreamPriorityRange(&lo, &hi));
@@ -69,10 +70,18 @@ void create_tree(fmm_tree* t, const R* xyzq) {
   if (!f64) build_p2p_items(t);
   mark(FMM_PH_BUILD_LISTS, 1);
   mark(FMM_PH_BUILD_PLAN, 0);
-  build_m2l_plan(t);
+  if (fitted) {
+    // fitted centres: no shared operators; the centres and the M2L list by
+    // target instead of the plan
+    t->tile_eptr = alloc_n<int32_t>(a, 1);
+    GB_CK(cudaMemsetAsync(t->tile_eptr, 0, sizeof(int32_t), s));
+    build_fitted(t);
+  } else {
+    build_m2l_plan(t);
+  }
   mark(FMM_PH_BUILD_PLAN, 1);
   mark(FMM_PH_BUILD_OPS, 0);
-  build_operators(t);
+  if (!fitted) build_operators(t);
   const size_t rs = sizeof(R);
   t->M = a.alloc(rs * (size_t)t->ncell * t->Kp);
   t->L = a.alloc(rs * (size_t)t->ncell * t->Kp);
@@ -105,7 +114,7 @@ void create_tree(fmm_tree* t, const R* xyzq) {
 
 constexpr uint32_t kKnownFlags = FMM_FLAG_CIRCUMSCRIBED | FMM_FLAG_TIMING | FMM_FLAG_M2L_CUDA_CORE |
                                  FMM_FLAG_SORTED_PLAN | FMM_FLAG_SERIAL_PHASES | FMM_FLAG_MUTUAL_P2P |
-                                 FMM_FLAG_TIGHT_MAC;
+                                 FMM_FLAG_TIGHT_MAC | FMM_FLAG_FITTED_CENTRES;
 
 template <class R>
 int build_common(const R* xyzq, int64_t n, int p, double theta, int ncrit, uint32_t flags,
@@ -186,11 +195,17 @@ void run_pass(fmm_tree* t, cudaStream_t s, int mode, R* a, R* b) {
   T.begin(FMM_PH_P2M);
   launch_p2m<R>(t, fs);
   T.end(FMM_PH_P2M);
+  const bool fitted = t->m2l_engine == 3;
   T.begin(FMM_PH_M2M);
-  for (int l = t->nlevel - 2; l >= 0; --l) launch_m2m<R>(t, l, fs);
+  for (int l = t->nlevel - 2; l >= 0; --l) {
+    if (fitted) launch_m2m_fit<R>(t, l, fs);
+    else launch_m2m<R>(t, l, fs);
+  }
   T.end(FMM_PH_M2M);
   T.begin(FMM_PH_M2L);
-  if (t->m2l_engine == 1) {
+  if (fitted) {
+    launch_m2l_fit<R>(t, fs);
+  } else if (t->m2l_engine == 1) {
     launch_split_tf32(t, fs);
     launch_m2l_tcgen05(t, fs);
   } else {
@@ -198,7 +213,10 @@ void run_pass(fmm_tree* t, cudaStream_t s, int mode, R* a, R* b) {
   }
   T.end(FMM_PH_M2L);
   T.begin(FMM_PH_L2L);
-  for (int l = 1; l < t->nlevel; ++l) launch_l2l<R>(t, l, fs);
+  for (int l = 1; l < t->nlevel; ++l) {
+    if (fitted) launch_l2l_fit<R>(t, l, fs);
+    else launch_l2l<R>(t, l, fs);
+  }
   T.end(FMM_PH_L2L);
   if (!serial) {
     GB_CK(cudaEventRecord(t->join_far, fs));

@@ -120,6 +120,16 @@ struct fmm_tree {
   gbfmm::Cells c;
   int32_t* leaves = nullptr;  // leaf cell ids in cell order
   int32_t* leaf_of_cell = nullptr;  // cell -> leaf index or -1
+  // FMM_FLAG_FITTED_CENTRES: integer centres (3 per cell, units H / 2^21),
+  // expansion centres (3 doubles per cell) and their float pairs (hi[3],
+  // lo[3] per cell), and the M2L list as CSR by target (sources in order)
+  int32_t* fit_c = nullptr;
+  double* fit_cen = nullptr;
+  float* fit_cenf = nullptr;
+  int32_t* m2l_ptr = nullptr;
+  int32_t* m2l_csr_src = nullptr;
+  int fit_ntgt = 0;                 // cells with M2L sources, and their ids
+  int32_t* fit_tgts = nullptr;
 
   int64_t n_p2p = 0, n_m2l = 0, n_p2p_ranges = 0, p2p_body_pairs = 0;
   int32_t *p2p_tgt = nullptr, *p2p_src = nullptr, *m2l_tgt = nullptr, *m2l_src = nullptr;

@@ -42,13 +42,19 @@ struct RootF {
 // by FMA and a compensated sum), and an offset is (x - c_hi) - c_lo in FP32
 // -- x - c_hi is exact wherever the cell is at least its own size away from
 // the origin, and small otherwise -- scaled by 1/R = 2^level / H in float.
+// With particle-fitted centres (fcen / fcenf not null: 3 doubles, or hi[3]
+// lo[3] floats, per cell) the centre is read instead; R stays the cube's half
+// side.
 template <class R>
 struct Frame {
   double c[3], inv;
-  __device__ void init(const double* __restrict__ root, const RootF&, int level, int ix, int iy, int iz) {
+  __device__ void init(const double* __restrict__ root, const RootF&, int level, int ix, int iy, int iz, int cell,
+                       const double* __restrict__ fcen, const float* __restrict__) {
     double Rc;
     cell_geom(root, level, ix, iy, iz, c, Rc);
     inv = 1.0 / Rc;
+    if (fcen)
+      for (int a = 0; a < 3; ++a) c[a] = fcen[3 * cell + a];
   }
   __device__ __forceinline__ R operator()(R x, int a) const { return (R)(((double)x - c[a]) * inv); }
   __device__ __forceinline__ R inv_r() const { return (R)inv; }
@@ -56,7 +62,16 @@ struct Frame {
 template <>
 struct Frame<float> {
   float hi[3], lo[3], inv;
-  __device__ void init(const double* __restrict__, const RootF& g, int level, int ix, int iy, int iz) {
+  __device__ void init(const double* __restrict__, const RootF& g, int level, int ix, int iy, int iz, int cell,
+                       const double* __restrict__, const float* __restrict__ fcenf) {
+    inv = ldexpf(g.ih, level);
+    if (fcenf) {
+      for (int a = 0; a < 3; ++a) {
+        hi[a] = fcenf[6 * cell + a];
+        lo[a] = fcenf[6 * cell + 3 + a];
+      }
+      return;
+    }
     const float rh = ldexpf(g.hh, -level), rl = ldexpf(g.hl, -level);
     const int k3[3] = {ix, iy, iz};
 #pragma unroll
@@ -71,7 +86,6 @@ struct Frame<float> {
       hi[a] = s + l;
       lo[a] = l - (hi[a] - s);
     }
-    inv = ldexpf(g.ih, level);
   }
   __device__ __forceinline__ float operator()(float x, int a) const { return ((x - hi[a]) - lo[a]) * inv; }
   __device__ __forceinline__ float inv_r() const { return inv; }
@@ -98,8 +112,8 @@ __global__ void __launch_bounds__(32 * kWarps, 6) k_p2m(const R4* __restrict__ w
                       const int32_t* __restrict__ level, const int32_t* __restrict__ ix,
                       const int32_t* __restrict__ iy, const int32_t* __restrict__ iz,
                       const int32_t* __restrict__ bbeg, const int32_t* __restrict__ bend,
-                      const double* __restrict__ root, RootF rootf, int p, int Kp, R* __restrict__ M,
-                      Lim lim) {
+                      const double* __restrict__ root, RootF rootf, const double* __restrict__ fcen,
+                      const float* __restrict__ fcenf, int p, int Kp, R* __restrict__ M, Lim lim) {
   const int lane = threadIdx.x & 31;
   const int li = blockIdx.x * kWarps + (threadIdx.x >> 5);
   if (li >= nleaf) return;
@@ -108,7 +122,7 @@ __global__ void __launch_bounds__(32 * kWarps, 6) k_p2m(const R4* __restrict__ w
   if (!in_range(cell, lim.ncell, 311, lim.rec)) return;
 #endif
   Frame<R> off;
-  off.init(root, rootf, level[cell], ix[cell], iy[cell], iz[cell]);
+  off.init(root, rootf, level[cell], ix[cell], iy[cell], iz[cell], cell, fcen, fcenf);
   const int s = bbeg[cell], e = bend[cell];
   const int G = 32 / p;  // p <= 16: at least two groups
   const int g = lane / p, m = lane - g * p;
@@ -263,8 +277,8 @@ __global__ void k_l2p_finalize(const R4* __restrict__ work, const int32_t* __res
                                const int32_t* __restrict__ level, const int32_t* __restrict__ ix,
                                const int32_t* __restrict__ iy, const int32_t* __restrict__ iz,
                                const int32_t* __restrict__ bbeg, const int32_t* __restrict__ bend,
-                               const double* __restrict__ root, RootF rootf, int p, int Kp,
-                               const R* __restrict__ L,
+                               const double* __restrict__ root, RootF rootf, const double* __restrict__ fcen,
+                               const float* __restrict__ fcenf, int p, int Kp, const R* __restrict__ L,
                                const R4* __restrict__ near, const int32_t* __restrict__ perm, int mode,
                                R* __restrict__ out_a, R* __restrict__ out_b, R4* __restrict__ grad_q,
                                R* __restrict__ q_last, Lim lim) {
@@ -289,7 +303,7 @@ __global__ void k_l2p_finalize(const R4* __restrict__ work, const int32_t* __res
   for (int i = lane; i < p * p; i += 32) Ls[i] = GB_LD(L, (int64_t)cell * Kp + i, lim.ncell * lim.Kp, 342);
   __syncwarp();
   Frame<R> off;
-  off.init(root, rootf, level[cell], ix[cell], iy[cell], iz[cell]);
+  off.init(root, rootf, level[cell], ix[cell], iy[cell], iz[cell], cell, fcen, fcenf);
   const R inv_r = off.inv_r();
   const int s = bbeg[cell], e = bend[cell];
   for (int i = s + lane; i < e; i += 32) {
@@ -412,7 +426,7 @@ void launch_p2m(fmm_tree* t, cudaStream_t s) {
   using R4 = typename Vec4<R>::type;
   k_p2m<R, R4><<<blocks(t->nleaf, kWarps), 32 * kWarps, 0, s>>>(
       (const R4*)t->work, t->leaves, t->nleaf, t->c.level, t->c.ix, t->c.iy, t->c.iz, t->c.bbeg, t->c.bend,
-      t->d_root, root_f(t), t->p, t->Kp, (R*)t->M, t->lim);
+      t->d_root, root_f(t), t->fit_cen, t->fit_cenf, t->p, t->Kp, (R*)t->M, t->lim);
   GB_LAUNCH("k_p2m");
 }
 
@@ -442,8 +456,8 @@ void launch_l2p_finalize(fmm_tree* t, int mode, R* a, R* b, cudaStream_t s) {
   k_l2p_finalize<R, R4><<<blocks(t->nleaf, kWarps), 32 * kWarps,
                           sizeof(R) * (kMaxP * kMaxP + kMaxP + kWarps * t->Kp), s>>>(
       (const R4*)t->work, t->leaves, t->nleaf, t->c.level, t->c.ix, t->c.iy, t->c.iz, t->c.bbeg, t->c.bend,
-      t->d_root, root_f(t), t->p, t->Kp, (const R*)t->L, (const R4*)t->near, t->perm, mode, a, b, (R4*)t->grad_q,
-      (R*)t->q_last, t->lim);
+      t->d_root, root_f(t), t->fit_cen, t->fit_cenf, t->p, t->Kp, (const R*)t->L, (const R4*)t->near, t->perm, mode,
+      a, b, (R4*)t->grad_q, (R*)t->q_last, t->lim);
   GB_LAUNCH("k_l2p_finalize");
 }
 

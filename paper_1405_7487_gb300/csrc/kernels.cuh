@@ -61,6 +61,12 @@ void build_p2p_items(fmm_tree* t);
 // (a = dq, b = dx; the pass charges are the weights w).
 template <class R> void launch_l2p_finalize(fmm_tree* t, int mode, R* a, R* b, cudaStream_t s);
 void launch_m2l_tcgen05(fmm_tree* t, cudaStream_t s);
+// FMM_FLAG_FITTED_CENTRES (fitted.cu): build-time centres and M2L CSR, and
+// the per-child / per-pair translations
+void build_fitted(fmm_tree* t);
+template <class R> void launch_m2m_fit(fmm_tree* t, int level, cudaStream_t s);
+template <class R> void launch_l2l_fit(fmm_tree* t, int level, cudaStream_t s);
+template <class R> void launch_m2l_fit(fmm_tree* t, cudaStream_t s);
 void launch_split_tf32(fmm_tree* t, cudaStream_t s);
 void build_m2l_chunks(fmm_tree* t, int per);
 

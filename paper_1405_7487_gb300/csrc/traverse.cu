@@ -19,7 +19,10 @@
 // to its farthest body (the particle-fitted bound of Sec. II.B, the centre
 // kept): its square is an exact integer over the bodies' 21-bit coordinates,
 // and the test is theta^2 D^2 > (sqrt(r2_A) + sqrt(r2_B))^2 in correctly
-// rounded double operations, the same on every device.
+// rounded double operations, the same on every device.  With
+// FMM_FLAG_FITTED_CENTRES the centres move as well: to the centre of the box
+// of the cell's voxel centres, an integer u_min + u_max + 1 per axis in the
+// same units, and the radius is measured from there.
 #include <algorithm>
 #include <climits>
 
@@ -33,7 +36,8 @@ inline unsigned blocks(int64_t n) { return (unsigned)((n + kThreads - 1) / kThre
 
 struct CellView {
   const int32_t *level, *ix, *iy, *iz, *cbeg, *nch;
-  const long long* r2;  // FMM_FLAG_TIGHT_MAC: squared particle-fitted radius per cell, else null
+  const long long* r2;  // particle-fitted radius (tight MAC or fitted centres): its square per cell, else null
+  const int32_t* fc;    // fitted centres: 3 integer coordinates per cell (units H / 2^21), else null
 };
 
 __device__ __forceinline__ bool mac(const CellView& c, int A, int B, double theta2, int circ) {
@@ -41,7 +45,12 @@ __device__ __forceinline__ bool mac(const CellView& c, int A, int B, double thet
   const int64_t dx = ((2ll * c.ix[A] + 1) << (kMaxLevel - la)) - ((2ll * c.ix[B] + 1) << (kMaxLevel - lb));
   const int64_t dy = ((2ll * c.iy[A] + 1) << (kMaxLevel - la)) - ((2ll * c.iy[B] + 1) << (kMaxLevel - lb));
   const int64_t dz = ((2ll * c.iz[A] + 1) << (kMaxLevel - la)) - ((2ll * c.iz[B] + 1) << (kMaxLevel - lb));
-  const int64_t D2 = dx * dx + dy * dy + dz * dz;
+  int64_t D2 = dx * dx + dy * dy + dz * dz;
+  if (c.fc) {
+    const int64_t fx = (int64_t)c.fc[3 * A] - c.fc[3 * B], fy = (int64_t)c.fc[3 * A + 1] - c.fc[3 * B + 1],
+                  fz = (int64_t)c.fc[3 * A + 2] - c.fc[3 * B + 2];
+    D2 = fx * fx + fy * fy + fz * fz;
+  }
   if (c.r2) {
     const double sr = __dadd_rn(__dsqrt_rn((double)c.r2[A]), __dsqrt_rn((double)c.r2[B]));
     return __dmul_rn(theta2, (double)D2) > __dmul_rn(sr, sr);
@@ -314,6 +323,67 @@ __global__ void k_cell_r2(const uint64_t* __restrict__ keys, const int32_t* __re
   }
 }
 
+// Fitted centres: per cell the box of its bodies' voxel centres 2u + 1 (u
+// their 21-bit coordinates, read back from the sorted keys), its centre
+// u_min + u_max + 1 per axis and the squared distance from there to the
+// farthest voxel centre, all exact integers in units of H / 2^21.  One block
+// per cell.
+__global__ void k_cell_fit(const uint64_t* __restrict__ keys, const int32_t* __restrict__ bbeg,
+                           const int32_t* __restrict__ bend, int32_t* __restrict__ fc, long long* __restrict__ r2) {
+  const int c = blockIdx.x;
+  __shared__ int wl[3][32], wh[3][32];
+  __shared__ int ctr[3];
+  __shared__ long long wm[32];
+  int lo[3] = {INT_MAX, INT_MAX, INT_MAX}, hi[3] = {-1, -1, -1};
+  for (int i = bbeg[c] + threadIdx.x; i < bend[c]; i += blockDim.x) {
+    const uint64_t k = keys[i];
+    const int u[3] = {(int)compact3(k >> 2), (int)compact3(k >> 1), (int)compact3(k)};
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      lo[a] = min(lo[a], u[a]);
+      hi[a] = max(hi[a], u[a]);
+    }
+  }
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+    for (int o = 16; o > 0; o >>= 1) {
+      lo[a] = min(lo[a], __shfl_down_sync(0xffffffffu, lo[a], o));
+      hi[a] = max(hi[a], __shfl_down_sync(0xffffffffu, hi[a], o));
+    }
+  const int w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  if ((threadIdx.x & 31) == 0)
+    for (int a = 0; a < 3; ++a) {
+      wl[a][w] = lo[a];
+      wh[a][w] = hi[a];
+    }
+  __syncthreads();
+  if (threadIdx.x == 0)
+    for (int a = 0; a < 3; ++a) {
+      int l = wl[a][0], h = wh[a][0];
+      for (int v = 1; v < nw; ++v) {
+        l = min(l, wl[a][v]);
+        h = max(h, wh[a][v]);
+      }
+      ctr[a] = l + h + 1;
+      fc[3 * c + a] = ctr[a];
+    }
+  __syncthreads();
+  long long m = 0;
+  for (int i = bbeg[c] + threadIdx.x; i < bend[c]; i += blockDim.x) {
+    const uint64_t k = keys[i];
+    const int64_t dx = 2 * compact3(k >> 2) + 1 - ctr[0], dy = 2 * compact3(k >> 1) + 1 - ctr[1],
+                  dz = 2 * compact3(k) + 1 - ctr[2];
+    m = max(m, (long long)(dx * dx + dy * dy + dz * dz));
+  }
+  for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_down_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) wm[w] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int v = 1; v < nw; ++v) m = max(m, wm[v]);
+    r2[c] = m;
+  }
+}
+
 }  // namespace
 
 // Smallest b with 2^b > v.
@@ -340,13 +410,20 @@ void build_lists(fmm_tree* t) {
   Arena& a = t->arena;
   cudaStream_t s = t->stream;
   long long* r2 = nullptr;
-  if (t->flags & FMM_FLAG_TIGHT_MAC) {
+  if (t->flags & FMM_FLAG_FITTED_CENTRES) {
+    // the integer centres stay with the tree (the expansion centres follow
+    // from them)
+    r2 = alloc_n<long long>(a, t->ncell);
+    t->fit_c = alloc_n<int32_t>(a, 3 * (size_t)t->ncell);
+    k_cell_fit<<<(unsigned)t->ncell, 128, 0, s>>>(t->keys, t->c.bbeg, t->c.bend, t->fit_c, r2);
+    GB_LAUNCH("k_cell_fit");
+  } else if (t->flags & FMM_FLAG_TIGHT_MAC) {
     r2 = alloc_n<long long>(a, t->ncell);
     k_cell_r2<<<(unsigned)t->ncell, 128, 0, s>>>(t->keys, t->c.level, t->c.ix, t->c.iy, t->c.iz, t->c.bbeg,
                                                 t->c.bend, r2);
     GB_LAUNCH("k_cell_r2");
   }
-  CellView cv{t->c.level, t->c.ix, t->c.iy, t->c.iz, t->c.cbeg, t->c.nch, r2};
+  CellView cv{t->c.level, t->c.ix, t->c.iy, t->c.iz, t->c.cbeg, t->c.nch, r2, t->fit_c};
   const double theta2 = t->theta * t->theta;
   const int circ = (t->flags & FMM_FLAG_CIRCUMSCRIBED) ? 1 : 0;
 

@@ -27,6 +27,7 @@ FMM_FLAG_SORTED_PLAN = 8
 FMM_FLAG_SERIAL_PHASES = 16
 FMM_FLAG_MUTUAL_P2P = 32
 FMM_FLAG_TIGHT_MAC = 64
+FMM_FLAG_FITTED_CENTRES = 128
 
 PHASES = ("p2m", "m2m", "m2l", "l2l", "p2p", "l2p", "eval_total", "build_total",
           "build_tree", "build_lists", "build_plan", "build_ops")

@@ -73,7 +73,7 @@ def test_build_arguments_checked_before_any_gpu_work(libpath):
     h = ctypes.c_void_p(1)
     ok = dict(n=1000, p=4, theta=0.4, ncrit=8, flags=0)
     bad = [dict(n=0), dict(n=1 << 31), dict(p=0), dict(p=17), dict(theta=0.0), dict(theta=1.0),
-           dict(theta=float("nan")), dict(theta=-0.5), dict(ncrit=0), dict(flags=1 << 7),
+           dict(theta=float("nan")), dict(theta=-0.5), dict(ncrit=0), dict(flags=1 << 8),
            dict(flags=1 << 31)]
     for b in bad:
         a = dict(ok, **b)

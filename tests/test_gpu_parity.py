@@ -52,13 +52,15 @@ CASES = {
 # ------------------------------------------------------------ structure
 
 @pytest.mark.parametrize("name", ["cube4k_p4", "plummer60k_p8", "sphere40k_p6"])
-@pytest.mark.parametrize("mac", ["half", "circ", "tight"])
+@pytest.mark.parametrize("mac", ["half", "circ", "tight", "fitted"])
 def test_tree_and_lists_bit_identical(fmm, orc, name, mac):
     gen, p, theta, ncrit = CASES[name]
     x = gen()
-    flags = {"half": 0, "circ": fmm.FMM_FLAG_CIRCUMSCRIBED, "tight": fmm.FMM_FLAG_TIGHT_MAC}[mac]
+    flags = {"half": 0, "circ": fmm.FMM_FLAG_CIRCUMSCRIBED, "tight": fmm.FMM_FLAG_TIGHT_MAC,
+             "fitted": fmm.FMM_FLAG_FITTED_CENTRES}[mac]
     T = gpu_tree(fmm, x, p, theta, ncrit, flags)
-    O = orc.OracleTree(x, p, theta, ncrit, circumscribed=mac == "circ", tight=mac == "tight")
+    O = orc.OracleTree(x, p, theta, ncrit, circumscribed=mac == "circ", tight=mac == "tight",
+                       fitted=mac == "fitted")
     r_g, r_o = T.root(), O.root()
     for k in ("lo", "hi", "centre", "corner"):
         assert np.array_equal(r_g[k], r_o[k])
@@ -139,6 +141,38 @@ def test_tight_mac_matches_oracle(fmm, orc, name, f64):
     torch.cuda.synchronize()
     dqo, dxo = O.backward(np.asarray(w, np.float64))
     assert rel(dq.double().cpu().numpy(), dqo) < tp and rel(dx.double().cpu().numpy(), dxo) < tf
+
+
+@pytest.mark.parametrize("name,f64", [("cube65k_p10", False), ("plummer60k_p8", False), ("sphere40k_p6", False),
+                                      ("cube20k_p16", False), ("cube3k_p1", False), ("cube4k_p4", True),
+                                      ("plummer60k_p8", True)])
+def test_fitted_centres_match_oracle(fmm, orc, name, f64):
+    """Expansion centres at the particle-fitted boxes (row f3): M2M, L2L and M2L
+    per pair about the moved centres, against the oracle built the same way,
+    forward and backward (frozen centres), single and double precision."""
+    gen, p, theta, ncrit = CASES[name]
+    x = gen()
+    T = gpu_tree(fmm, x, p, theta, ncrit, fmm.FMM_FLAG_FITTED_CENTRES, f64=f64)
+    assert T.stats()["m2l_engine"] == 3
+    ph, f = evaluate(T)
+    O = orc.OracleTree(x, p, theta, ncrit, fitted=True)
+    po, go = O.evaluate()
+    tp, tf = (TOL64_PHI, TOL64_F) if f64 else (TOL_PHI, TOL_F)
+    bp, bf = (1e-9, 1e-8) if f64 else (1e-4, 1e-3)
+    assert_match(ph, po, f, -go, tp, tf, bp, bf)
+    Mg, Lg = T.expansions()
+    Mo, Lo = O.expansions()
+    cells = O.cells()
+    R = np.ldexp(O.root()["H"], -cells["level"].astype(np.int64))
+    Ms, Ls = scale_oracle(Mo, Lo, R, p)
+    assert rel(unpack(Mg.astype(np.float64), p), Ms) < (1e-12 if f64 else 1e-6)
+    assert rel(unpack(Lg.astype(np.float64), p), Ls) < (1e-11 if f64 else 1e-5)
+    w = W.weights(x.shape[0], 32)
+    dq, dx = T.backward(torch.from_numpy(np.asarray(w, np.float64 if f64 else np.float32)).cuda())
+    torch.cuda.synchronize()
+    dqo, dxo = O.backward(np.asarray(w, np.float64))
+    assert_match(dq.double().cpu().numpy(), dqo, dx.double().cpu().numpy(), dxo, tp, tf, bp, bf)
+    T.check()
 
 
 @pytest.mark.parametrize("name,f64", [("cube65k_p10", False), ("plummer60k_p8", False), ("sphere40k_p6", False),
