@@ -31,9 +31,7 @@ namespace gbfmm {
 namespace {
 
 constexpr int kThreads = 128;
-constexpr int kSrcRound = 4;   // M2L sources per round (one warp each for the harmonics)
-constexpr int kPT = 2 * kMaxP - 1;  // degrees of the M2L harmonics
-constexpr int kTriT = kPT * (kPT + 1) / 2;
+constexpr int kSrcRound = 8;   // M2L sources per round (tasks: kSrcRound x p(p+1)/2)
 constexpr int kTriP = kMaxP * (kMaxP + 1) / 2;
 
 inline unsigned blocks(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
@@ -100,22 +98,24 @@ __device__ __forceinline__ void regular_column(R x, R y, R z, int m, int P, cx<R
 // Column m of Th_n^m(u) / n! for a unit vector u (degrees m .. P - 1), from
 // Th_m^m = -(2m-1) (x + i y) Th_{m-1}^{m-1} and
 // Th_n^m = (2n-1) z Th_{n-1}^m - (n+m-1)(n-m-1) Th_{n-2}^m   (|u| = 1),
-// divided through by n!.
+// divided through by n! (rcp[q] = 1/q, rcp[0] = 0); stored at T[n*n + n + m] together with the order -m
+// (Th_n^-m = (-1)^m conj(Th_n^m)).
 template <class R>
-__device__ __forceinline__ void irregular_column(R x, R y, R z, int m, int P, cx<R>* T) {
+__device__ __forceinline__ void irregular_column_full(R x, R y, R z, int m, int P, const R* __restrict__ rcp,
+                                                      cx<R>* T) {
   cx<R> d{(R)1, (R)0};
   for (int k = 1; k <= m; ++k) {
     d = cmul(d, cx<R>{x, y});
-    const R f = -(R)(2 * k - 1) / (R)k;
+    const R f = -(R)(2 * k - 1) * rcp[k];
     d.re *= f;
     d.im *= f;
   }
-  cx<R> a = d, b{(R)0, (R)0};  // degrees n and n - 1
+  cx<R> a = d, b{(R)0, (R)0};
   for (int n = m; n < P; ++n) {
-    T[tri(n, m)] = a;
-    // degree n + 1 from n and n - 1
-    const R c1 = (R)(2 * n + 1) * z / (R)(n + 1);
-    const R c2 = n >= 1 ? (R)(n + m) * (R)(n - m) / ((R)(n + 1) * (R)n) : (R)0;
+    T[n * n + n + m] = a;
+    if (m) T[n * n + n - m] = (m & 1) ? cx<R>{-a.re, a.im} : cx<R>{a.re, -a.im};
+    const R c1 = (R)(2 * n + 1) * z * rcp[n + 1];
+    const R c2 = (R)((n + m) * (n - m)) * rcp[n + 1] * rcp[n];  // rcp[0] = 0
     const cx<R> c{c1 * a.re - c2 * b.re, c1 * a.im - c2 * b.im};
     b = a;
     a = c;
@@ -231,114 +231,178 @@ __global__ void k_l2l_fit(int first, int ncell, const int32_t* __restrict__ pare
 }
 
 // M2L: one block per target cell with M2L sources (sources [ptr[t], ptr[t+1])
-// of the sorted list), kSrcRound sources per round: warp w forms the scaled
-// harmonics of source w's pair, then every thread adds the round's
-// contributions to its output coefficients (k, l >= 0).
-template <class R>
+// of the sorted list), kSrcRound sources per round.  The block forms each
+// source's harmonics Th_j^i(u) / j! (all orders -j .. j; a thread per order
+// column), its multipoles M~_n^m rho_A^n n! (all m) and the target factors in
+// shared memory.  Then
+// thread t takes the tasks t, t + kThreads, ... of the round, a task being a
+// (source slot r, output (k, l >= 0)) pair, and adds the contribution to its
+// own accumulator for that task (compensated).  Slot r takes sources r,
+// r + kSrcRound, ... of the target's list, in order, and the slots are summed
+// in order at the end, so the results are reproducible.
+// In single precision the geometry comes from the integer centres: their
+// differences (below 2^22 units of H / 2^21) are exact in FP32, and the cube
+// half side R = 2^(21 - level) units, so no FP64 runs per pair.
+template <class R, int kSlots>
 __global__ void __launch_bounds__(kThreads) k_m2l_fit(const int32_t* __restrict__ ptr, const int32_t* __restrict__ tgt_of,
                                                        const int32_t* __restrict__ src, const int32_t* __restrict__ level,
-                                                       const double* __restrict__ cen, const double* __restrict__ root,
-                                                       int p, int Kp, const R* __restrict__ M, R* __restrict__ L) {
+                                                       const int32_t* __restrict__ fc, const double* __restrict__ cen,
+                                                       const double* __restrict__ root, int p, int Kp,
+                                                       const R* __restrict__ M, R* __restrict__ L) {
   extern __shared__ unsigned char smem_raw[];
-  cx<R>* T = reinterpret_cast<cx<R>*>(smem_raw);       // kSrcRound x kTriT
-  cx<R>* Mr = T + kSrcRound * kTriT;                   // kSrcRound x p^2 (all m): M~ rho_A^n n!
-  R* fk = reinterpret_cast<R*>(Mr + kSrcRound * kMaxP * kMaxP);  // kSrcRound x p: (-1)^k rho_B^(k+1) k!
+  const int PT = 2 * p - 1, nT = PT * PT, nM = p * p, nt = p * (p + 1) / 2;
+  cx<R>* T = reinterpret_cast<cx<R>*>(smem_raw);      // kSrcRound x PT^2, index j*j + j + i
+  cx<R>* Mr = T + kSrcRound * nT;                     // kSrcRound x p^2, index n*n + n + m
+  R* fk = reinterpret_cast<R*>(Mr + kSrcRound * nM);  // kSrcRound x p: (-1)^k rho_B^(k+1) k!
+  R* gA = fk + kSrcRound * p;                         // kSrcRound x p: rho_A^n n!
+  R* geo = gA + kSrcRound * p;                        // kSrcRound x 3: d / |d|
+  R* bin = geo + kSrcRound * 3;                       // p x p: C(n + k, k) at n * p + k
+  R* rcp = bin + p * p;                               // 2 kMaxP: 1 / q (rcp[0] = 0)
   const int tb = tgt_of[blockIdx.x];
   const int e0 = ptr[tb], e1 = ptr[tb + 1];
-  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int nt = p * (p + 1) / 2, PT = 2 * p - 1;
-  const double RB = ldexp(root[9], -level[tb]);
-  // output coefficients of this thread (at most two: p <= 16 gives <= 136)
-  int ok_[2], ol_[2];
-  for (int oi = 0; oi < 2; ++oi) {
-    const int o = threadIdx.x + oi * kThreads;
-    int k = 0;
-    while ((k + 1) * (k + 2) / 2 <= o) ++k;
-    ok_[oi] = o < nt ? k : -1;
-    ol_[oi] = o - k * (k + 1) / 2;
+  for (int i = threadIdx.x; i < p * p; i += kThreads) {
+    const int n = i / p, k = i - n * p;
+    R c = 1;
+    for (int q = 1; q <= k; ++q) c = c * (R)(n + q) / (R)q;
+    bin[i] = c;
   }
-  cx<R> sum[2] = {{(R)0, (R)0}, {(R)0, (R)0}}, comp[2] = {{(R)0, (R)0}, {(R)0, (R)0}};
+  if (threadIdx.x < 2 * kMaxP) rcp[threadIdx.x] = threadIdx.x ? (R)1 / (R)threadIdx.x : (R)0;
+  // this thread's tasks (kSlots >= kSrcRound * nt / kThreads): r in bits
+  // 16.., k in bits 8..15, l in bits 0..7 (-1 = none)
+  int task[kSlots];
+  cx<R> sum[kSlots], comp[kSlots];
+#pragma unroll
+  for (int j = 0; j < kSlots; ++j) {
+    const int g = threadIdx.x + j * kThreads;
+    task[j] = -1;
+    if (g < kSrcRound * nt) {
+      const int r = g / nt, o = g - r * nt;
+      int k = 0;
+      while ((k + 1) * (k + 2) / 2 <= o) ++k;
+      task[j] = (r << 16) | (k << 8) | (o - k * (k + 1) / 2);
+    }
+    sum[j] = {(R)0, (R)0};
+    comp[j] = {(R)0, (R)0};
+  }
   for (int e = e0; e < e1; e += kSrcRound) {
     const int nr = min(kSrcRound, e1 - e);
     __syncthreads();
-    if (w < nr) {
-      const int sa = src[e + w];
-      const double dx = cen[3 * tb] - cen[3 * sa], dy = cen[3 * tb + 1] - cen[3 * sa + 1],
-                   dz = cen[3 * tb + 2] - cen[3 * sa + 2];
-      const double r = sqrt(dx * dx + dy * dy + dz * dz);
-      const double RA = ldexp(root[9], -level[sa]);
-      const R rhoA = (R)(RA / r), rhoB = (R)(RB / r);
-      const R ux = (R)(dx / r), uy = (R)(dy / r), uz = (R)(dz / r);
-      if (lane < PT) irregular_column<R>(ux, uy, uz, lane, PT, T + w * kTriT);
-      // M~ rho_A^n n!, all orders
-      for (int i = lane; i < p * p; i += 32) {
-        int n = 0;
-        while ((n + 1) * (n + 1) <= i) ++n;
-        const int m = i - n * n - n;  // -n .. n
-        const int am = m < 0 ? -m : m;
-        const R* mrow = M + (int64_t)sa * Kp;
-        cx<R> v{mrow[ridx(n, am, 0)], am ? mrow[ridx(n, am, 1)] : (R)0};
-        if (m < 0) {
-          v.im = -v.im;
-          if (am & 1) {
-            v.re = -v.re;
-            v.im = -v.im;
-          }
-        }
-        R f = 1;
-        for (int q = 1; q <= n; ++q) f *= rhoA * (R)q;
-        Mr[w * kMaxP * kMaxP + i] = {v.re * f, v.im * f};
+    // geometry and the per-degree factors, a thread per (source, degree)
+    for (int g = threadIdx.x; g < nr * p; g += kThreads) {
+      const int r = g / p, n = g - r * p;
+      const int sa = src[e + r];
+      R ux, uy, uz, rhoA, rhoB;
+      if constexpr (sizeof(R) == 4) {
+        const float dx = (float)(fc[3 * tb] - fc[3 * sa]), dy = (float)(fc[3 * tb + 1] - fc[3 * sa + 1]),
+                    dz = (float)(fc[3 * tb + 2] - fc[3 * sa + 2]);
+        const float inv = 1.0f / sqrtf(dx * dx + dy * dy + dz * dz);
+        ux = dx * inv;
+        uy = dy * inv;
+        uz = dz * inv;
+        rhoA = ldexpf(inv, kMaxLevel - level[sa]);
+        rhoB = ldexpf(inv, kMaxLevel - level[tb]);
+      } else {
+        const double dx = cen[3 * tb] - cen[3 * sa], dy = cen[3 * tb + 1] - cen[3 * sa + 1],
+                     dz = cen[3 * tb + 2] - cen[3 * sa + 2];
+        const double rr = sqrt(dx * dx + dy * dy + dz * dz);
+        ux = dx / rr;
+        uy = dy / rr;
+        uz = dz / rr;
+        rhoA = ldexp(root[9], -level[sa]) / rr;
+        rhoB = ldexp(root[9], -level[tb]) / rr;
       }
-      if (lane < p) {
-        R f = rhoB;
-        for (int q = 1; q <= lane; ++q) f *= rhoB * (R)q;
-        fk[w * kMaxP + lane] = (lane & 1) ? -f : f;
+      if (n == 0) {
+        geo[3 * r] = ux;
+        geo[3 * r + 1] = uy;
+        geo[3 * r + 2] = uz;
       }
+      R fa = 1, fb = rhoB;
+      for (int q = 1; q <= n; ++q) {
+        fa *= rhoA * (R)q;
+        fb *= rhoB * (R)q;
+      }
+      gA[r * p + n] = fa;
+      fk[r * p + n] = (n & 1) ? -fb : fb;
     }
     __syncthreads();
-    for (int oi = 0; oi < 2; ++oi) {
-      const int k = ok_[oi], l = ol_[oi];
-      if (k < 0) continue;
-      cx<R> part{(R)0, (R)0};
-      for (int r = 0; r < nr; ++r) {
-        const cx<R>* Tr = T + r * kTriT;
-        const cx<R>* Mq = Mr + r * kMaxP * kMaxP;
-        cx<R> acc{(R)0, (R)0};
-        R bin = 1;  // C(n + k, k)
-        for (int n = 0; n < p; ++n) {
-          cx<R> an{(R)0, (R)0};
-          for (int m = -n; m <= n; ++m) {
-            const cx<R> a = Mq[n * n + n + m], t = hget(Tr, n + k, m + l);
-            an.re += a.re * t.re - a.im * t.im;
-            an.im += a.re * t.im + a.im * t.re;
-          }
-          acc.re += bin * an.re;
-          acc.im += bin * an.im;
-          bin = bin * (R)(n + 1 + k) / (R)(n + 1);
+    // harmonics, a thread per (source, order column); scaled multipoles
+    for (int g = threadIdx.x; g < nr * PT; g += kThreads) {
+      const int r = g / PT, m = g - r * PT;
+      irregular_column_full<R>(geo[3 * r], geo[3 * r + 1], geo[3 * r + 2], m, PT, rcp, T + r * nT);
+    }
+    for (int g = threadIdx.x; g < nr * nM; g += kThreads) {
+      const int r = g / nM, i = g - r * nM;
+      int n = (int)sqrtf((float)i);
+      n -= n * n > i;
+      const int m = i - n * n - n;  // -n .. n
+      const int am = m < 0 ? -m : m;
+      const R* mrow = M + (int64_t)src[e + r] * Kp;
+      cx<R> v{mrow[ridx(n, am, 0)], am ? mrow[ridx(n, am, 1)] : (R)0};
+      if (m < 0) {  // X_n^-m = (-1)^m conj(X_n^m)
+        v.im = -v.im;
+        if (am & 1) {
+          v.re = -v.re;
+          v.im = -v.im;
         }
-        const R f = fk[r * kMaxP + k];
-        part.re += f * acc.re;
-        part.im += f * acc.im;
       }
-      // compensated addition of the round's contribution
+      const R f = gA[r * p + n];
+      Mr[r * nM + i] = {v.re * f, v.im * f};
+    }
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < kSlots; ++j) {
+      const int tk = task[j];
+      if (tk < 0 || (tk >> 16) >= nr) continue;
+      const int r = tk >> 16, k = (tk >> 8) & 0xff, l = tk & 0xff;
+      const cx<R>* Tr = T + r * nT;
+      const cx<R>* Mq = Mr + r * nM;
+      cx<R> acc{(R)0, (R)0};
+      for (int n = 0; n < p; ++n) {
+        const int jd = n + k;
+        const cx<R>* trow = Tr + jd * jd + jd + l;  // trow[m] = Th_{n+k}^{m+l} / (n+k)!
+        const cx<R>* mrow = Mq + n * n + n;         // mrow[m] = M~_n^m rho_A^n n!
+        cx<R> an{(R)0, (R)0};
+        for (int m = -n; m <= n; ++m) {
+          const cx<R> a = mrow[m], t = trow[m];
+          an.re += a.re * t.re - a.im * t.im;
+          an.im += a.re * t.im + a.im * t.re;
+        }
+        const R b = bin[n * p + k];
+        acc.re += b * an.re;
+        acc.im += b * an.im;
+      }
+      const R f = fk[r * p + k];
       {
-        const R y = part.re - comp[oi].re, t = sum[oi].re + y;
-        comp[oi].re = (t - sum[oi].re) - y;
-        sum[oi].re = t;
+        const R y = f * acc.re - comp[j].re, t = sum[j].re + y;
+        comp[j].re = (t - sum[j].re) - y;
+        sum[j].re = t;
       }
       {
-        const R y = part.im - comp[oi].im, t = sum[oi].im + y;
-        comp[oi].im = (t - sum[oi].im) - y;
-        sum[oi].im = t;
+        const R y = f * acc.im - comp[j].im, t = sum[j].im + y;
+        comp[j].im = (t - sum[j].im) - y;
+        sum[j].im = t;
       }
     }
   }
+  // slot sums in order (the harmonics buffer holds them: kSrcRound * nt <= kSrcRound * PT^2)
+  __syncthreads();
+  cx<R>* part = T;
+#pragma unroll
+  for (int j = 0; j < kSlots; ++j)
+    if (task[j] >= 0) part[threadIdx.x + j * kThreads] = {sum[j].re - comp[j].re, sum[j].im - comp[j].im};
+  __syncthreads();
   R* out = L + (int64_t)tb * Kp;
-  for (int oi = 0; oi < 2; ++oi) {
-    const int k = ok_[oi], l = ol_[oi];
-    if (k < 0) continue;
-    out[ridx(k, l, 0)] = sum[oi].re;
-    if (l) out[ridx(k, l, 1)] = sum[oi].im;
+  for (int o = threadIdx.x; o < nt; o += kThreads) {
+    int k = 0;
+    while ((k + 1) * (k + 2) / 2 <= o) ++k;
+    const int l = o - k * (k + 1) / 2;
+    cx<R> s{(R)0, (R)0};
+    for (int r = 0; r < kSrcRound; ++r) {
+      s.re += part[r * nt + o].re;
+      s.im += part[r * nt + o].im;
+    }
+    out[ridx(k, l, 0)] = s.re;
+    if (l) out[ridx(k, l, 1)] = s.im;
   }
 }
 
@@ -413,10 +477,14 @@ void launch_l2l_fit(fmm_tree* t, int level, cudaStream_t s) {
 template <class R>
 void launch_m2l_fit(fmm_tree* t, cudaStream_t s) {
   if (t->fit_ntgt == 0) return;
-  const size_t smem = sizeof(cx<R>) * (size_t)kSrcRound * (kTriT + kMaxP * kMaxP) + sizeof(R) * kSrcRound * kMaxP;
-  GB_CK(cudaFuncSetAttribute(k_m2l_fit<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  k_m2l_fit<R><<<t->fit_ntgt, kThreads, smem, s>>>(t->m2l_ptr, t->fit_tgts, t->m2l_csr_src, t->c.level, t->fit_cen,
-                                                    t->d_root, t->p, t->Kp, (const R*)t->M, (R*)t->L);
+  const int p = t->p, PT = 2 * p - 1;
+  const size_t smem = sizeof(cx<R>) * (size_t)kSrcRound * (PT * PT + p * p) +
+                      sizeof(R) * ((size_t)kSrcRound * (2 * p + 3) + p * p + 2 * kMaxP);
+  // task slots per thread: ceil(kSrcRound * p (p + 1) / 2 / kThreads) for p <= 8, 12, 16
+  auto kern = p <= 8 ? k_m2l_fit<R, 3> : p <= 12 ? k_m2l_fit<R, 5> : k_m2l_fit<R, 9>;
+  GB_CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  kern<<<t->fit_ntgt, kThreads, smem, s>>>(t->m2l_ptr, t->fit_tgts, t->m2l_csr_src, t->c.level, t->fit_c, t->fit_cen,
+                                           t->d_root, p, t->Kp, (const R*)t->M, (R*)t->L);
   GB_LAUNCH("k_m2l_fit");
 }
 
