@@ -31,7 +31,8 @@ namespace gbfmm {
 namespace {
 
 constexpr int kThreads = 128;
-constexpr int kSrcRound = 8;   // M2L sources per round (tasks: kSrcRound x p(p+1)/2)
+constexpr int kSrcRound = 8;   // M2L sources per round
+constexpr int kLB = 4;         // M2L outputs (consecutive orders l of one degree k) per task
 constexpr int kTriP = kMaxP * (kMaxP + 1) / 2;
 
 inline unsigned blocks(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
@@ -234,10 +235,11 @@ __global__ void k_l2l_fit(int first, int ncell, const int32_t* __restrict__ pare
 // of the sorted list), kSrcRound sources per round.  The block forms each
 // source's harmonics Th_j^i(u) / j! (all orders -j .. j; a thread per order
 // column), its multipoles M~_n^m rho_A^n n! (all m) and the target factors in
-// shared memory.  Then
-// thread t takes the tasks t, t + kThreads, ... of the round, a task being a
-// (source slot r, output (k, l >= 0)) pair, and adds the contribution to its
-// own accumulator for that task (compensated).  Slot r takes sources r,
+// shared memory.  Then thread t takes the tasks t, t + kThreads, ... of the
+// round, a task being a source slot r and the kLB outputs (k, l0 .. l0 + kLB
+// - 1) of one degree, which share each multipole load and a sliding window of
+// harmonics, and adds the contributions to its own accumulators
+// (compensated).  Slot r takes sources r,
 // r + kSrcRound, ... of the target's list, in order, and the slots are summed
 // in order at the end, so the results are reproducible.
 // In single precision the geometry comes from the integer centres: their
@@ -267,22 +269,26 @@ __global__ void __launch_bounds__(kThreads) k_m2l_fit(const int32_t* __restrict_
     bin[i] = c;
   }
   if (threadIdx.x < 2 * kMaxP) rcp[threadIdx.x] = threadIdx.x ? (R)1 / (R)threadIdx.x : (R)0;
-  // this thread's tasks (kSlots >= kSrcRound * nt / kThreads): r in bits
-  // 16.., k in bits 8..15, l in bits 0..7 (-1 = none)
+  // This thread's tasks: slot j is task threadIdx.x + j * kThreads, a
+  // (source slot r, row k, outputs l0 .. l0 + kLB - 1) block, kLB | l0 <= k;
+  // encoded r << 16 | k << 8 | l0 (-1 = none).  kSlots covers
+  // kSrcRound * sum_k ceil((k + 1) / kLB) tasks.
   int task[kSlots];
-  cx<R> sum[kSlots], comp[kSlots];
+  cx<R> sum[kSlots][kLB], comp[kSlots][kLB];
+  int nb = 0;  // blocks per source
+  for (int k = 0; k < p; ++k) nb += (k + kLB) / kLB;
 #pragma unroll
   for (int j = 0; j < kSlots; ++j) {
     const int g = threadIdx.x + j * kThreads;
     task[j] = -1;
-    if (g < kSrcRound * nt) {
-      const int r = g / nt, o = g - r * nt;
-      int k = 0;
-      while ((k + 1) * (k + 2) / 2 <= o) ++k;
-      task[j] = (r << 16) | (k << 8) | (o - k * (k + 1) / 2);
+    if (g < kSrcRound * nb) {
+      const int r = g / nb;
+      int b = g - r * nb, k = 0;
+      while (b >= (k + kLB) / kLB) b -= (k++ + kLB) / kLB;
+      task[j] = (r << 16) | (k << 8) | (b * kLB);
     }
-    sum[j] = {(R)0, (R)0};
-    comp[j] = {(R)0, (R)0};
+#pragma unroll
+    for (int q = 0; q < kLB; ++q) sum[j][q] = comp[j][q] = {(R)0, (R)0};
   }
   for (int e = e0; e < e1; e += kSrcRound) {
     const int nr = min(kSrcRound, e1 - e);
@@ -353,34 +359,55 @@ __global__ void __launch_bounds__(kThreads) k_m2l_fit(const int32_t* __restrict_
     for (int j = 0; j < kSlots; ++j) {
       const int tk = task[j];
       if (tk < 0 || (tk >> 16) >= nr) continue;
-      const int r = tk >> 16, k = (tk >> 8) & 0xff, l = tk & 0xff;
+      const int r = tk >> 16, k = (tk >> 8) & 0xff, l0 = tk & 0xff;
       const cx<R>* Tr = T + r * nT;
       const cx<R>* Mq = Mr + r * nM;
-      cx<R> acc{(R)0, (R)0};
+      cx<R> acc[kLB];
+#pragma unroll
+      for (int q = 0; q < kLB; ++q) acc[q] = {(R)0, (R)0};
       for (int n = 0; n < p; ++n) {
         const int jd = n + k;
-        const cx<R>* trow = Tr + jd * jd + jd + l;  // trow[m] = Th_{n+k}^{m+l} / (n+k)!
-        const cx<R>* mrow = Mq + n * n + n;         // mrow[m] = M~_n^m rho_A^n n!
-        cx<R> an{(R)0, (R)0};
+        // trow[m + q] = Th_{n+k}^{m+l0+q} / (n+k)!; past the row's end (l0 + q > k,
+        // outputs that are not stored) it reads the next row or, for the last
+        // row of the last slot, the first entries of Mr: inside the buffer.
+        const cx<R>* trow = Tr + jd * jd + jd + l0;
+        const cx<R>* mrow = Mq + n * n + n;  // mrow[m] = M~_n^m rho_A^n n!
+        cx<R> an[kLB], win[kLB];
+#pragma unroll
+        for (int q = 0; q < kLB; ++q) an[q] = {(R)0, (R)0};
+#pragma unroll
+        for (int q = 0; q + 1 < kLB; ++q) win[q] = trow[-n + q];
         for (int m = -n; m <= n; ++m) {
-          const cx<R> a = mrow[m], t = trow[m];
-          an.re += a.re * t.re - a.im * t.im;
-          an.im += a.re * t.im + a.im * t.re;
+          win[kLB - 1] = trow[m + kLB - 1];
+          const cx<R> a = mrow[m];
+#pragma unroll
+          for (int q = 0; q < kLB; ++q) {
+            an[q].re += a.re * win[q].re - a.im * win[q].im;
+            an[q].im += a.re * win[q].im + a.im * win[q].re;
+          }
+#pragma unroll
+          for (int q = 0; q + 1 < kLB; ++q) win[q] = win[q + 1];
         }
         const R b = bin[n * p + k];
-        acc.re += b * an.re;
-        acc.im += b * an.im;
+#pragma unroll
+        for (int q = 0; q < kLB; ++q) {
+          acc[q].re += b * an[q].re;
+          acc[q].im += b * an[q].im;
+        }
       }
       const R f = fk[r * p + k];
-      {
-        const R y = f * acc.re - comp[j].re, t = sum[j].re + y;
-        comp[j].re = (t - sum[j].re) - y;
-        sum[j].re = t;
-      }
-      {
-        const R y = f * acc.im - comp[j].im, t = sum[j].im + y;
-        comp[j].im = (t - sum[j].im) - y;
-        sum[j].im = t;
+#pragma unroll
+      for (int q = 0; q < kLB; ++q) {
+        {
+          const R y = f * acc[q].re - comp[j][q].re, t = sum[j][q].re + y;
+          comp[j][q].re = (t - sum[j][q].re) - y;
+          sum[j][q].re = t;
+        }
+        {
+          const R y = f * acc[q].im - comp[j][q].im, t = sum[j][q].im + y;
+          comp[j][q].im = (t - sum[j][q].im) - y;
+          sum[j][q].im = t;
+        }
       }
     }
   }
@@ -388,8 +415,14 @@ __global__ void __launch_bounds__(kThreads) k_m2l_fit(const int32_t* __restrict_
   __syncthreads();
   cx<R>* part = T;
 #pragma unroll
-  for (int j = 0; j < kSlots; ++j)
-    if (task[j] >= 0) part[threadIdx.x + j * kThreads] = {sum[j].re - comp[j].re, sum[j].im - comp[j].im};
+  for (int j = 0; j < kSlots; ++j) {
+    const int tk = task[j];
+    if (tk < 0) continue;
+    const int r = tk >> 16, k = (tk >> 8) & 0xff, l0 = tk & 0xff;
+#pragma unroll
+    for (int q = 0; q < kLB; ++q)
+      if (l0 + q <= k) part[r * nt + tri(k, l0 + q)] = {sum[j][q].re - comp[j][q].re, sum[j][q].im - comp[j][q].im};
+  }
   __syncthreads();
   R* out = L + (int64_t)tb * Kp;
   for (int o = threadIdx.x; o < nt; o += kThreads) {
@@ -480,8 +513,9 @@ void launch_m2l_fit(fmm_tree* t, cudaStream_t s) {
   const int p = t->p, PT = 2 * p - 1;
   const size_t smem = sizeof(cx<R>) * (size_t)kSrcRound * (PT * PT + p * p) +
                       sizeof(R) * ((size_t)kSrcRound * (2 * p + 3) + p * p + 2 * kMaxP);
-  // task slots per thread: ceil(kSrcRound * p (p + 1) / 2 / kThreads) for p <= 8, 12, 16
-  auto kern = p <= 8 ? k_m2l_fit<R, 3> : p <= 12 ? k_m2l_fit<R, 5> : k_m2l_fit<R, 9>;
+  // task slots per thread: kSrcRound * sum_k ceil((k + 1) / kLB) / kThreads
+  // rounded up (96, 192 and 320 tasks at p = 8, 12, 16)
+  auto kern = p <= 8 ? k_m2l_fit<R, 1> : p <= 12 ? k_m2l_fit<R, 2> : k_m2l_fit<R, 3>;
   GB_CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   kern<<<t->fit_ntgt, kThreads, smem, s>>>(t->m2l_ptr, t->fit_tgts, t->m2l_csr_src, t->c.level, t->fit_c, t->fit_cen,
                                            t->d_root, p, t->Kp, (const R*)t->M, (R*)t->L);
