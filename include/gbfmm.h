@@ -136,6 +136,7 @@ typedef struct {
                                 are not valid); 4 a kernel block ended with a
                                 copy or tensor-core operation it issued not seen
                                 to complete (treat every output as invalid) */
+  int32_t build_host_syncs;  /* times fmm_build waited for its stream (size read-backs) */
   float ms[FMM_PH_COUNT];    /* last evaluate/build phase times (FMM_FLAG_TIMING) */
 } fmm_stats;
 

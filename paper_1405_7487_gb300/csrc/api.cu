@@ -79,6 +79,10 @@ void create_tree(fmm_tree* t, const R* xyzq) {
   } else {
     build_m2l_plan(t);
   }
+  a.release(t->m2l_has);
+  a.release(t->m2l_maxd);
+  t->m2l_has = nullptr;
+  t->m2l_maxd = nullptr;
   mark(FMM_PH_BUILD_PLAN, 1);
   mark(FMM_PH_BUILD_OPS, 0);
   if (!fitted) build_operators(t);
@@ -100,13 +104,12 @@ void create_tree(fmm_tree* t, const R* xyzq) {
   t->lim = Lim{t->N, t->ncell, t->nleaf, t->Kp, t->ntile, t->nentry, t->nclass, t->n_p2p_ranges, t->check_rec};
   mark(FMM_PH_BUILD_OPS, 1);
   mark(FMM_PH_BUILD_TOTAL, 1);
+  long long nitem[2] = {0, 0};
+  if (t->p2p_nitem) GB_CK(cudaMemcpyAsync(nitem, t->p2p_nitem, sizeof(nitem), cudaMemcpyDeviceToHost, s));
   check_scan_error(a, s);  // synchronises
-  if (t->p2p_nitem) {
-    long long h[2] = {0, 0};
-    GB_CK(cudaMemcpy(h, t->p2p_nitem, sizeof(h), cudaMemcpyDeviceToHost));
-    t->p2p_nitem_host = h[0];
-    t->p2p_nbig_host = h[1];
-  }
+  t->p2p_nitem_host = nitem[0];
+  t->p2p_nbig_host = nitem[1];
+  t->build_syncs = a.nsync;
   if (timing)
     for (int ph : {FMM_PH_BUILD_TOTAL, FMM_PH_BUILD_TREE, FMM_PH_BUILD_LISTS, FMM_PH_BUILD_PLAN, FMM_PH_BUILD_OPS})
       cudaEventElapsedTime(&t->ms[ph], t->ev[2 * ph], t->ev[2 * ph + 1]);
@@ -392,6 +395,7 @@ int fmm_get_stats(const fmm_tree* tc, fmm_stats* o) {
   const int derr = read_device_errors(t);
   if (derr < 0) return FMM_ERR_CUDA;
   o->device_errors = derr;
+  o->build_host_syncs = t->build_syncs;
   if ((t->flags & FMM_FLAG_TIMING) && t->evaluations > 0) {
     if (cudaEventSynchronize(t->ev[2 * FMM_PH_EVAL_TOTAL + 1]) != cudaSuccess) {
       cudaGetLastError();

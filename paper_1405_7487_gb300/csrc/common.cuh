@@ -44,6 +44,7 @@ struct Arena {
   bool has_user = false;
   cudaStream_t stream = nullptr;
   int* err = nullptr;  // the owning tree's device error word (kErr* bits), set before any scan
+  int nsync = 0;       // host synchronisations of the stream (host_sync)
   std::vector<void*> live;
   void* alloc(size_t bytes);
   void release(void* p);
@@ -67,6 +68,9 @@ void scan_exclusive_i64_dev(Arena& a, int64_t* d, int64_t n, int64_t* total_dev,
 // returns the total: synchronises the stream, reads the total and the error
 // word, and fails with FMM_ERR_TIMEOUT if kErrScan is set
 int64_t scan_exclusive_i64_total(Arena& a, int64_t* d, int64_t n, cudaStream_t s);
+// host: waits for the stream and counts the wait in a.nsync (every host
+// synchronisation of a build goes through it)
+void host_sync(Arena& a, cudaStream_t s);
 // host: fails with FMM_ERR_TIMEOUT if kErrScan is set in the error word
 // (synchronises the stream first)
 void check_scan_error(Arena& a, cudaStream_t s);
@@ -133,6 +137,8 @@ struct fmm_tree {
 
   int64_t n_p2p = 0, n_m2l = 0, n_p2p_ranges = 0, p2p_body_pairs = 0;
   int32_t *p2p_tgt = nullptr, *p2p_src = nullptr, *m2l_tgt = nullptr, *m2l_src = nullptr;
+  int32_t* m2l_has = nullptr;             // per cell: takes M2L (traversal, for the plan)
+  unsigned long long* m2l_maxd = nullptr;  // largest M2L class offset component (traversal, for the plan)
   int32_t* p2p_rptr = nullptr;  // per leaf: ranges [rptr[l], rptr[l+1])
   int2* p2p_ranges = nullptr;   // (begin, end) sorted body ranges, self excluded
   int64_t n_p2p_upairs = 0;     // mutual interaction: unordered leaf pairs (cells a < b)
@@ -170,6 +176,7 @@ struct fmm_tree {
   int4* p2p_items = nullptr;       // single precision: near-field work items (t0, nt, s, e), largest first
   int2* p2p_item_rng = nullptr;    //   and their neighbour ranges [r0, r1)
   long long* p2p_nitem = nullptr;  //   item count, then the count of per-block items (device)
+  int build_syncs = 0;              // host synchronisations of fmm_build
   int64_t p2p_nbig_host = 0;       //   items of the per-block kernel (the first ones), read back
   int64_t p2p_nitem_max = 0;       //   bound on it (array size)
   int64_t p2p_nitem_host = 0;      //   item count, read back at the end of the build

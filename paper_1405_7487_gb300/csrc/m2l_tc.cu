@@ -847,7 +847,7 @@ void build_m2l_quads(fmm_tree* t, int per, const std::vector<int32_t>& eptr) {
     k_quad_ptr<<<(unsigned)((nquad + 256) / 256), 256, 0, s>>>(qid, nquad, t->nclass, nq, d_qptr);
     GB_LAUNCH("k_quad_ptr");
     GB_CK(cudaMemcpyAsync(qptr.data(), d_qptr, sizeof(int32_t) * (nquad + 1), cudaMemcpyDeviceToHost, s));
-    GB_CK(cudaStreamSynchronize(s));
+    host_sync(a, s);
     a.release(qid);
     a.release(d_qptr);
     build_m2l_quad_chunks(t, per, qptr);
@@ -856,7 +856,7 @@ void build_m2l_quads(fmm_tree* t, int per, const std::vector<int32_t>& eptr) {
   std::vector<int32_t> ecls(t->nentry);
   if (t->nentry)
     GB_CK(cudaMemcpyAsync(ecls.data(), t->entry_class, sizeof(int32_t) * t->nentry, cudaMemcpyDeviceToHost, s));
-  GB_CK(cudaStreamSynchronize(s));
+  host_sync(a, s);
   std::vector<int32_t> qcls;
   std::vector<int4> qent;
   qcls.reserve(t->nentry);
@@ -917,7 +917,7 @@ void build_m2l_quad_chunks(fmm_tree* t, int per, const std::vector<int32_t>& qpt
   GB_CK(cudaMemcpyAsync(t->m2l_chunks, ch.data(), sizeof(int4) * ch.size(), cudaMemcpyHostToDevice, s));
   GB_CK(cudaMemcpyAsync(t->tile_cptr, cptr.data(), sizeof(int32_t) * cptr.size(), cudaMemcpyHostToDevice, s));
   t->m2l_part = alloc_n<float>(a, (size_t)t->nchunk * kQuad * kTile * t->Kp);
-  GB_CK(cudaStreamSynchronize(s));
+  host_sync(a, s);
 }
 
 void build_m2l_chunks(fmm_tree* t, int per) {
@@ -925,7 +925,7 @@ void build_m2l_chunks(fmm_tree* t, int per) {
   cudaStream_t s = t->stream;
   std::vector<int32_t> eptr(t->ntile + 1);
   GB_CK(cudaMemcpyAsync(eptr.data(), t->tile_eptr, sizeof(int32_t) * (t->ntile + 1), cudaMemcpyDeviceToHost, s));
-  GB_CK(cudaStreamSynchronize(s));
+  host_sync(a, s);
   t->M_lo = alloc_n<float>(a, 2 * (size_t)t->ncell * t->Kp);
   if (t->nclass > 0) {
     const int64_t rows = (int64_t)t->nclass * t->Kp;
@@ -956,7 +956,7 @@ void build_m2l_chunks(fmm_tree* t, int per) {
   GB_CK(cudaMemcpyAsync(t->m2l_chunks, ch.data(), sizeof(int4) * ch.size(), cudaMemcpyHostToDevice, s));
   GB_CK(cudaMemcpyAsync(t->tile_cptr, cptr.data(), sizeof(int32_t) * cptr.size(), cudaMemcpyHostToDevice, s));
   t->m2l_part = alloc_n<float>(a, (size_t)t->nchunk * kTile * t->Kp);
-  GB_CK(cudaStreamSynchronize(s));
+  host_sync(a, s);
 }
 
 }  // namespace gbfmm

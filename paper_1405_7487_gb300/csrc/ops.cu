@@ -122,8 +122,11 @@ __device__ __forceinline__ void put(R* op, int Kp, bool out_major, int ro, int r
   if (sizeof(R) == 4 && !(fabs(v) <= (double)FLT_MAX)) *range_bad = 1;
 }
 
-// Real Kp x Kp matrices of one operator per block.  geom: per operator
-// (x, y, z, log2(R_A / r), log2(R_B / r)) in double; X built in shared memory.
+// Real Kp x Kp matrices of one operator per blockIdx.x; the gridDim.y blocks
+// of an operator split its entries (each forms the harmonics X in shared
+// memory).  geom: per operator (x, y, z, log2(R_A / r), log2(R_B / r)) in
+// double.  Every entry of the K x K corner is written once, so the blocks
+// zero only the padding and need no ordering among themselves.
 template <class R>
 __global__ void k_build_ops(int kind, int p, int Kp, const double* __restrict__ geom, int nops,
                             R* __restrict__ ops, float* __restrict__ ops_lo, bool out_major,
@@ -148,14 +151,15 @@ __global__ void k_build_ops(int kind, int p, int Kp, const double* __restrict__ 
   Coef C{kind, eA, eB, X, scale};
   R* o = ops + (int64_t)op * Kp * Kp;
   float* olo = ops_lo ? ops_lo + (int64_t)op * Kp * Kp : nullptr;
-  // zero (padding rows/columns stay zero)
-  for (int i = threadIdx.x; i < Kp * Kp; i += blockDim.x) {
+  // the padding rows and columns (index >= K) are zero
+  const int K = p * p, part = blockIdx.y, nparts = gridDim.y;
+  for (int i = threadIdx.x + part * blockDim.x; i < Kp * Kp; i += blockDim.x * nparts) {
+    if (i / Kp < K && i % Kp < K) continue;
     o[i] = (R)0;
     if (olo) olo[i] = 0.0f;
   }
-  __syncthreads();
   const int nt = p * (p + 1) / 2;
-  for (int w = threadIdx.x; w < nt * nt; w += blockDim.x) {
+  for (int w = threadIdx.x + part * blockDim.x; w < nt * nt; w += blockDim.x * nparts) {
     const int oi = w / nt, ii = w % nt;
     int a = 0;
     while ((a + 1) * (a + 2) / 2 <= oi) ++a;
@@ -212,12 +216,6 @@ struct CellView {
   const int32_t *level, *ix, *iy, *iz;
 };
 
-__global__ void k_target_flags(const int32_t* __restrict__ tgt, int64_t n, int32_t* __restrict__ has) {
-  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  if (i == 0 || tgt[i] != tgt[i - 1]) has[tgt[i]] = 1;
-}
-
 // Targets ordered by (level, octant within the parent, boundary pattern,
 // cell).  The pattern is, per axis, how many cells (up to kPatternReach) the
 // domain still holds below and above the cell: interior cells and cells at
@@ -270,27 +268,6 @@ __device__ __forceinline__ void pair_offset(const CellView& c, int A, int B, int
   d[1] = (((2ll * c.iy[A] + 1) << (kMaxLevel - la)) - ((2ll * c.iy[B] + 1) << (kMaxLevel - lb))) >> sh;
   d[2] = (((2ll * c.iz[A] + 1) << (kMaxLevel - la)) - ((2ll * c.iz[B] + 1) << (kMaxLevel - lb))) >> sh;
   dl = la - lb;
-}
-
-// Largest |offset| component over all M2L pairs (sizes the class keys).
-__global__ void k_class_maxd(const int32_t* __restrict__ tgt, const int32_t* __restrict__ src, int64_t n,
-                             CellView c, unsigned long long* __restrict__ maxd) {
-  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  unsigned long long m = 0;
-  if (i < n) {
-    int64_t d[3];
-    int dl;
-    pair_offset(c, src[i], tgt[i], d, dl);
-    for (int k = 0; k < 3; ++k) m = max(m, (unsigned long long)(d[k] < 0 ? -d[k] : d[k]));
-  }
-  for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_down_sync(0xffffffffu, m, o));
-  __shared__ unsigned long long wm[kThreads / 32];
-  if ((threadIdx.x & 31) == 0) wm[threadIdx.x >> 5] = m;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    for (int w = 1; w < kThreads / 32; ++w) m = max(m, wm[w]);
-    if (m) atomicMax(maxd, m);
-  }
 }
 
 // Class key of a pair: (level difference, offset in units of the smaller
@@ -394,11 +371,15 @@ __device__ __forceinline__ uint64_t class_key(const CellView& c, int A, int B, i
          ((uint64_t)(d[1] + maxd) << b) | (uint64_t)(d[2] + maxd);
 }
 
+// Marks the class key of every pair in the dense table and keeps the key per
+// pair (the entry passes then read it instead of gathering both cells again).
 __global__ void k_class_mark(const int32_t* __restrict__ tgt, const int32_t* __restrict__ src, int64_t n,
-                             CellView c, int b, int64_t maxd, int64_t* __restrict__ mark) {
+                             CellView c, int b, int64_t maxd, int64_t* __restrict__ mark,
+                             uint32_t* __restrict__ pkey) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= n) return;
   const uint64_t k = class_key(c, src[i], tgt[i], b, maxd);
+  pkey[i] = (uint32_t)k;
   // read first: 16.8 M pairs share a few hundred classes, so almost every
   // pair finds its mark set and stores nothing (a plain store from every
   // pair contends for those few addresses)
@@ -434,12 +415,10 @@ __global__ void k_class_desc_dense(const int64_t* __restrict__ excl, int64_t nke
 struct ClassOf {
   const int32_t* class_of;  // sorted numbering, else null
   const int64_t* key_excl;  // dense numbering: scanned key table
-  CellView c;
-  int b;
-  int64_t maxd;
-  __device__ __forceinline__ int operator()(int64_t i, int src, int tgt) const {
+  const uint32_t* pkey;     // dense numbering: the class key of every pair
+  __device__ __forceinline__ int operator()(int64_t i) const {
     if (class_of) return class_of[i];
-    return (int)key_excl[class_key(c, src, tgt, b, maxd)];
+    return (int)key_excl[pkey[i]];
   }
 };
 
@@ -449,7 +428,7 @@ __global__ void k_entry_mark(const int32_t* __restrict__ tgt, const int32_t* __r
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= n) return;
   const int t = tgt[i];
-  const int64_t e = (int64_t)(rank_of[t] / kTile) * nclass + cls(i, src[i], t);
+  const int64_t e = (int64_t)(rank_of[t] / kTile) * nclass + cls(i);
   mark[e] = 1;  // plain store: the entries are many, each marked by at most 128 pairs
 }
 
@@ -460,7 +439,7 @@ __global__ void k_entry_fill_dense(const int32_t* __restrict__ tgt, const int32_
   if (i >= n) return;
   const int t = tgt[i], sr = src[i];
   const int r = rank_of[t];
-  const int64_t e = excl[(int64_t)(r / kTile) * nclass + cls(i, sr, t)];
+  const int64_t e = excl[(int64_t)(r / kTile) * nclass + cls(i)];
   entry_src[e * kTile + (r % kTile)] = sr;
 }
 
@@ -620,11 +599,9 @@ void build_m2l_plan(fmm_tree* t) {
     GB_CK(cudaMemsetAsync(t->tile_eptr, 0, sizeof(int32_t), s));
     return;
   }
-  // --- targets and tiles
-  int32_t* has = alloc_n<int32_t>(a, t->ncell);
-  GB_CK(cudaMemsetAsync(has, 0, sizeof(int32_t) * t->ncell, s));
-  k_target_flags<<<blocks(nm), kThreads, 0, s>>>(t->m2l_tgt, nm, has);
-  GB_LAUNCH("k_target_flags");
+  // --- targets and tiles (the traversal marked the cells that take M2L and
+  // found the largest class offset)
+  int32_t* has = t->m2l_has;
   uint64_t* tkey = alloc_n<uint64_t>(a, t->ncell);
   unsigned long long* d_cnt = alloc_n<unsigned long long>(a, 2);  // target count, largest offset
   GB_CK(cudaMemsetAsync(d_cnt, 0, sizeof(unsigned long long), s));
@@ -633,15 +610,13 @@ void build_m2l_plan(fmm_tree* t) {
   while ((1ll << cbits) <= (int64_t)t->ncell) ++cbits;
   k_target_keys<<<blocks(t->ncell), kThreads, 0, s>>>(has, cv, t->ncell, cbits, tkey, d_cnt);
   GB_LAUNCH("k_target_keys");
-  // the largest offset of the translation classes, read back together with
-  // the target count (one host synchronisation)
-  GB_CK(cudaMemsetAsync(d_cnt + 1, 0, sizeof(unsigned long long), s));
-  k_class_maxd<<<blocks(nm), kThreads, 0, s>>>(t->m2l_tgt, t->m2l_src, nm, cv, d_cnt + 1);
-  GB_LAUNCH("k_class_maxd");
+  // the largest offset of the translation classes is read back together
+  // with the target count (one host synchronisation)
+  GB_CK(cudaMemcpyAsync(d_cnt + 1, t->m2l_maxd, sizeof(unsigned long long), cudaMemcpyDeviceToDevice, s));
   radix_sort_keys(a, tkey, t->ncell, cbits + kTargetKeyExtra, s);
   unsigned long long hc[2] = {0, 0};
   GB_CK(cudaMemcpyAsync(hc, d_cnt, sizeof(hc), cudaMemcpyDeviceToHost, s));
-  GB_CK(cudaStreamSynchronize(s));
+  host_sync(a, s);
   const unsigned long long ntgt = hc[0], maxd = hc[1];
   t->ntile = (int)((ntgt + kTile - 1) / kTile);
   const int64_t padded = (int64_t)t->ntile * kTile;
@@ -650,7 +625,6 @@ void build_m2l_plan(fmm_tree* t) {
   k_target_rank<<<blocks(padded), kThreads, 0, s>>>(tkey, (int64_t)ntgt, padded, cbits, t->tile_tgt, rank_of);
   GB_LAUNCH("k_target_rank");
   a.release(tkey);
-  a.release(has);
   a.release(d_cnt);
 
   // --- translation classes
@@ -662,11 +636,14 @@ void build_m2l_plan(fmm_tree* t) {
   const bool dense_cls = !sorted_only && b <= 19 && kbits <= kDenseBits;
   int32_t* class_of = nullptr;
   int64_t* key_excl = nullptr;  // dense numbering: kept for the entry kernels
+  uint32_t* pkey = nullptr;     // dense numbering: class key per pair
   if (dense_cls) {
     const int64_t nkey = 1ll << kbits;
     key_excl = alloc_n<int64_t>(a, nkey);
+    pkey = alloc_n<uint32_t>(a, nm);
     GB_CK(cudaMemsetAsync(key_excl, 0, sizeof(int64_t) * nkey, s));
-    k_class_mark<<<blocks(nm), kThreads, 0, s>>>(t->m2l_tgt, t->m2l_src, nm, cv, b, (int64_t)maxd, key_excl);
+    k_class_mark<<<blocks(nm), kThreads, 0, s>>>(t->m2l_tgt, t->m2l_src, nm, cv, b, (int64_t)maxd, key_excl,
+                                                 pkey);
     GB_LAUNCH("k_class_mark");
     const int64_t ncls = scan_exclusive_i64_total(a, key_excl, nkey, s);
     t->nclass = (int)ncls;
@@ -700,7 +677,7 @@ void build_m2l_plan(fmm_tree* t) {
     const int64_t nk = (int64_t)t->ntile * t->nclass;
     int64_t* mark = alloc_n<int64_t>(a, nk);
     GB_CK(cudaMemsetAsync(mark, 0, sizeof(int64_t) * nk, s));
-    const ClassOf cls{class_of, key_excl, cv, b, (int64_t)maxd};
+    const ClassOf cls{class_of, key_excl, pkey};
     k_entry_mark<<<blocks(nm), kThreads, 0, s>>>(t->m2l_tgt, t->m2l_src, cls, rank_of, nm, t->nclass, mark);
     GB_LAUNCH("k_entry_mark");
     const int64_t ne = scan_exclusive_i64_total(a, mark, nk, s);
@@ -718,9 +695,11 @@ void build_m2l_plan(fmm_tree* t) {
     a.release(mark);
     if (class_of) a.release(class_of);
     if (key_excl) a.release(key_excl);
+    if (pkey) a.release(pkey);
     a.release(rank_of);
     return;
   }
+  if (pkey) a.release(pkey);
   if (!class_of) {
     // dense class numbering, sorted entries: the per-pair classes
     class_of = alloc_n<int32_t>(a, nm);
@@ -784,12 +763,15 @@ void build_operators(fmm_tree* t) {
   const size_t sm_reg = sizeof(double) * 2 * (size_t)p * (p + 1) / 2;
   const int Pt = 2 * p - 1;
   const size_t sm_irr = sizeof(double) * 2 * (size_t)Pt * (Pt + 1) / 2;
+  // 8 octant operators each, their entries split over 16 blocks (the FP64
+  // pipe of 8 SMs alone took 60 us per set at p = 10)
+  const dim3 g8x16(8, 16);
   if (f64) {
-    k_build_ops<double><<<8, 256, sm_reg, s>>>(kM2M, p, Kp, g8, 8, (double*)t->m2m_ops, nullptr, false, bad);
-    k_build_ops<double><<<8, 256, sm_reg, s>>>(kL2L, p, Kp, g8, 8, (double*)t->l2l_ops, nullptr, false, bad);
+    k_build_ops<double><<<g8x16, 256, sm_reg, s>>>(kM2M, p, Kp, g8, 8, (double*)t->m2m_ops, nullptr, false, bad);
+    k_build_ops<double><<<g8x16, 256, sm_reg, s>>>(kL2L, p, Kp, g8, 8, (double*)t->l2l_ops, nullptr, false, bad);
   } else {
-    k_build_ops<float><<<8, 256, sm_reg, s>>>(kM2M, p, Kp, g8, 8, (float*)t->m2m_ops, nullptr, false, bad);
-    k_build_ops<float><<<8, 256, sm_reg, s>>>(kL2L, p, Kp, g8, 8, (float*)t->l2l_ops, nullptr, false, bad);
+    k_build_ops<float><<<g8x16, 256, sm_reg, s>>>(kM2M, p, Kp, g8, 8, (float*)t->m2m_ops, nullptr, false, bad);
+    k_build_ops<float><<<g8x16, 256, sm_reg, s>>>(kL2L, p, Kp, g8, 8, (float*)t->l2l_ops, nullptr, false, bad);
   }
   GB_LAUNCH("k_build_ops m2m/l2l");
   if (t->nclass > 0) {
@@ -810,7 +792,7 @@ void build_operators(fmm_tree* t) {
   }
   int hbad = 0;
   GB_CK(cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, s));
-  GB_CK(cudaStreamSynchronize(s));
+  host_sync(a, s);
   a.release(bad);
   a.release(g8);
   if (hbad) fail(FMM_ERR_RANGE, "translation operator overflows the working precision");

@@ -287,10 +287,15 @@ void scan_rec(Arena& a, int64_t* d, int64_t n, int64_t* total, cudaStream_t s) {
 
 }  // namespace
 
+void host_sync(Arena& a, cudaStream_t s) {
+  ++a.nsync;
+  GB_CK(cudaStreamSynchronize(s));
+}
+
 void check_scan_error(Arena& a, cudaStream_t s) {
   int h = 0;
   GB_CK(cudaMemcpyAsync(&h, a.err, sizeof(int), cudaMemcpyDeviceToHost, s));
-  GB_CK(cudaStreamSynchronize(s));
+  host_sync(a, s);
   if (h & kErrScan) fail(FMM_ERR_TIMEOUT, "a device scan's bounded look-back wait gave up");
 }
 

@@ -74,60 +74,126 @@ __device__ __forceinline__ int decide(const CellView& c, int A, int B, double th
   return la ? 5 : 4;
 }
 
-__global__ void k_trav_count(const int2* __restrict__ fr, int64_t n, CellView c, double theta2,
-                             int circ, int64_t* __restrict__ cnt) {
-  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  const int A = fr[i].x, B = fr[i].y;
-  const int k = decide(c, A, B, theta2, circ);
-  int64_t nn = 0, nm = 0, np = 0;
+// The (next, M2L, P2P) counts of one pair.
+__device__ __forceinline__ void pair_counts(const CellView& c, int A, int B, int k, int& nn, int& nm, int& np) {
+  nn = nm = np = 0;
   switch (k) {
     case 0: np = 1; break;
-    case 1: nn = (int64_t)c.nch[A] * (c.nch[A] + 1) / 2; break;
+    case 1: nn = c.nch[A] * (c.nch[A] + 1) / 2; break;
     case 2: nm = 2; break;
     case 3: np = 2; break;
     case 4: nn = c.nch[A]; break;
     case 5: nn = c.nch[B]; break;
-    default: nn = (int64_t)c.nch[A] * c.nch[B]; break;
+    default: nn = c.nch[A] * c.nch[B]; break;
   }
-  cnt[i] = nn;
-  cnt[n + i] = nm;
-  cnt[2 * n + i] = np;
+}
+
+// Exclusive prefix of three per-thread counts over the block (kThreads
+// threads, in thread order); the block's totals in tot.
+__device__ __forceinline__ void block_scan3(int v[3], int tot[3]) {
+  __shared__ int ws[3][kThreads / 32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  int inc[3] = {v[0], v[1], v[2]};
+#pragma unroll
+  for (int j = 0; j < 3; ++j)
+    for (int o = 1; o < 32; o <<= 1) {
+      const int u = __shfl_up_sync(0xffffffffu, inc[j], o);
+      if (lane >= o) inc[j] += u;
+    }
+  if (lane == 31)
+    for (int j = 0; j < 3; ++j) ws[j][w] = inc[j];
+  __syncthreads();
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    int before = 0, all = 0;
+    for (int q = 0; q < kThreads / 32; ++q) {
+      before += q < w ? ws[j][q] : 0;
+      all += ws[j][q];
+    }
+    v[j] = before + inc[j] - v[j];
+    tot[j] = all;
+  }
+}
+
+// Per block of frontier pairs: the totals of the three outputs, segment-major
+// (cnt[j * nb + block]), so that one exclusive scan gives every block's
+// output offsets in frontier order.
+__global__ void __launch_bounds__(kThreads) k_trav_count(const int2* __restrict__ fr, int64_t n, CellView c,
+                                                         double theta2, int circ, int64_t* __restrict__ cnt) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  int v[3] = {0, 0, 0}, tot[3];
+  if (i < n) {
+    const int A = fr[i].x, B = fr[i].y;
+    pair_counts(c, A, B, decide(c, A, B, theta2, circ), v[0], v[1], v[2]);
+  }
+  block_scan3(v, tot);
+  if (threadIdx.x == 0)
+    for (int j = 0; j < 3; ++j) cnt[(int64_t)j * gridDim.x + blockIdx.x] = tot[j];
 }
 
 __device__ __forceinline__ uint64_t pair_key(int tgt, int src) {
   return ((uint64_t)(uint32_t)tgt << 32) | (uint32_t)src;
 }
 
-__global__ void k_trav_write(const int2* __restrict__ fr, int64_t n, CellView c, double theta2,
-                             int circ, const int64_t* __restrict__ off, int64_t base_m,
-                             int64_t base_p, int2* __restrict__ next, uint64_t* __restrict__ m2l,
-                             int64_t m2l_at, uint64_t* __restrict__ p2p, int64_t p2p_at) {
+__global__ void __launch_bounds__(kThreads) k_trav_write(const int2* __restrict__ fr, int64_t n, CellView c,
+                                                         double theta2, int circ, const int64_t* __restrict__ off,
+                                                         int64_t base_m, int64_t base_p, int2* __restrict__ next,
+                                                         uint64_t* __restrict__ m2l, int64_t m2l_at,
+                                                         uint64_t* __restrict__ p2p, int64_t p2p_at,
+                                                         int32_t* __restrict__ m2l_has,
+                                                         unsigned long long* __restrict__ m2l_maxd) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  int A = 0, B = 0, k = -1, v[3] = {0, 0, 0}, tot[3];
+  unsigned dm = 0;  // M2L pair: largest |offset| component in units of the smaller cell's half side
+  if (i < n) {
+    A = fr[i].x;
+    B = fr[i].y;
+    k = decide(c, A, B, theta2, circ);
+    pair_counts(c, A, B, k, v[0], v[1], v[2]);
+    if (k == 2) {
+      const int la = c.level[A], lb = c.level[B], sh = kMaxLevel - (la > lb ? la : lb);
+      const int co[2][3] = {{c.ix[A], c.iy[A], c.iz[A]}, {c.ix[B], c.iy[B], c.iz[B]}};
+      for (int d = 0; d < 3; ++d) {
+        const int64_t o = (((2ll * co[0][d] + 1) << (kMaxLevel - la)) - ((2ll * co[1][d] + 1) << (kMaxLevel - lb))) >> sh;
+        dm = max(dm, (unsigned)(o < 0 ? -o : o));
+      }
+      // the cells that take M2L (read first: a cell has many M2L pairs)
+      if (!m2l_has[A]) m2l_has[A] = 1;
+      if (!m2l_has[B]) m2l_has[B] = 1;
+    }
+  }
+  block_scan3(v, tot);
+  {
+    __shared__ unsigned wmax[kThreads / 32];
+    dm = __reduce_max_sync(0xffffffffu, dm);
+    if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = dm;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      for (int w = 1; w < kThreads / 32; ++w) dm = max(dm, wmax[w]);
+      if (dm > *(volatile unsigned long long*)m2l_maxd) atomicMax(m2l_maxd, (unsigned long long)dm);
+    }
+  }
   if (i >= n) return;
-  const int A = fr[i].x, B = fr[i].y;
-  const int k = decide(c, A, B, theta2, circ);
-  int64_t o = off[i];
+  const int nb = gridDim.x;
+  int64_t o = off[blockIdx.x] + v[0];
+  const int64_t om = m2l_at + off[nb + blockIdx.x] - base_m + v[1];
+  const int64_t op = p2p_at + off[2 * nb + blockIdx.x] - base_p + v[2];
   switch (k) {
-    case 0: p2p[p2p_at + off[2 * n + i] - base_p] = pair_key(A, A); break;
+    case 0: p2p[op] = pair_key(A, A); break;
     case 1: {
       const int a0 = c.cbeg[A], na = c.nch[A];
       for (int x = 0; x < na; ++x)
         for (int y = x; y < na; ++y) next[o++] = make_int2(a0 + x, a0 + y);
       break;
     }
-    case 2: {
-      const int64_t m = m2l_at + off[n + i] - base_m;
-      m2l[m] = pair_key(B, A);
-      m2l[m + 1] = pair_key(A, B);
+    case 2:
+      m2l[om] = pair_key(B, A);
+      m2l[om + 1] = pair_key(A, B);
       break;
-    }
-    case 3: {
-      const int64_t m = p2p_at + off[2 * n + i] - base_p;
-      p2p[m] = pair_key(B, A);
-      p2p[m + 1] = pair_key(A, B);
+    case 3:
+      p2p[op] = pair_key(B, A);
+      p2p[op + 1] = pair_key(A, B);
       break;
-    }
     case 4: {
       const int a0 = c.cbeg[A], na = c.nch[A];
       for (int x = 0; x < na; ++x) next[o++] = make_int2(a0 + x, B);
@@ -433,6 +499,11 @@ void build_lists(fmm_tree* t) {
   uint64_t* p2p = alloc_n<uint64_t>(a, cap_p);
   int64_t nm = 0, np = 0;
 
+  // for the M2L plan: the cells that take M2L and the largest class offset
+  t->m2l_has = alloc_n<int32_t>(a, t->ncell);
+  t->m2l_maxd = alloc_n<unsigned long long>(a, 1);
+  GB_CK(cudaMemsetAsync(t->m2l_has, 0, sizeof(int32_t) * t->ncell, s));
+  GB_CK(cudaMemsetAsync(t->m2l_maxd, 0, sizeof(unsigned long long), s));
   int64_t nf = 1;
   int64_t* d_seg = alloc_n<int64_t>(a, 3);
   int2* fr = alloc_n<int2>(a, 1);
@@ -441,18 +512,19 @@ void build_lists(fmm_tree* t) {
     GB_CK(cudaMemcpyAsync(fr, &h, sizeof(int2), cudaMemcpyHostToDevice, s));
   }
   while (nf > 0) {
-    int64_t* cnt = alloc_n<int64_t>(a, 3 * nf);
-    k_trav_count<<<blocks(nf), kThreads, 0, s>>>(fr, nf, cv, theta2, circ, cnt);
+    const int64_t nb = blocks(nf);
+    int64_t* cnt = alloc_n<int64_t>(a, 3 * nb);
+    k_trav_count<<<(unsigned)nb, kThreads, 0, s>>>(fr, nf, cv, theta2, circ, cnt);
     GB_LAUNCH("k_trav_count");
-    // one scan over the three count segments; the segment starts and the
-    // total are read back together (one host synchronisation per level)
+    // one scan over the three segments of block totals; the segment starts
+    // and the total are read back together (one host synchronisation per level)
     int64_t* scanned = cnt;
-    scan_exclusive_i64_dev(a, scanned, 3 * nf, d_seg + 2, s);
-    GB_CK(cudaMemcpyAsync(&d_seg[0], scanned + nf, sizeof(int64_t), cudaMemcpyDeviceToDevice, s));
-    GB_CK(cudaMemcpyAsync(&d_seg[1], scanned + 2 * nf, sizeof(int64_t), cudaMemcpyDeviceToDevice, s));
+    scan_exclusive_i64_dev(a, scanned, 3 * nb, d_seg + 2, s);
+    GB_CK(cudaMemcpyAsync(&d_seg[0], scanned + nb, sizeof(int64_t), cudaMemcpyDeviceToDevice, s));
+    GB_CK(cudaMemcpyAsync(&d_seg[1], scanned + 2 * nb, sizeof(int64_t), cudaMemcpyDeviceToDevice, s));
     int64_t seg[3];
     GB_CK(cudaMemcpyAsync(seg, d_seg, sizeof(seg), cudaMemcpyDeviceToHost, s));
-    GB_CK(cudaStreamSynchronize(s));
+    host_sync(a, s);
     const int64_t total = seg[2];
     const int64_t n_next = seg[0], n_m = seg[1] - seg[0], n_p = total - seg[1];
     auto grow = [&](uint64_t*& buf, int64_t& cap, int64_t used, int64_t need) {
@@ -467,8 +539,8 @@ void build_lists(fmm_tree* t) {
     grow(m2l, cap_m, nm, n_m);
     grow(p2p, cap_p, np, n_p);
     int2* next = alloc_n<int2>(a, n_next);
-    k_trav_write<<<blocks(nf), kThreads, 0, s>>>(fr, nf, cv, theta2, circ, scanned, seg[0], seg[1],
-                                                 next, m2l, nm, p2p, np);
+    k_trav_write<<<(unsigned)nb, kThreads, 0, s>>>(fr, nf, cv, theta2, circ, scanned, seg[0], seg[1], next, m2l,
+                                                   nm, p2p, np, t->m2l_has, t->m2l_maxd);
     GB_LAUNCH("k_trav_write");
     nm += n_m;
     np += n_p;
@@ -535,7 +607,7 @@ void build_lists(fmm_tree* t) {
   GB_LAUNCH("k_i64_to_i32");
   unsigned long long hp = 0;
   GB_CK(cudaMemcpyAsync(&hp, d_pairs, sizeof(hp), cudaMemcpyDeviceToHost, s));
-  GB_CK(cudaStreamSynchronize(s));
+  host_sync(a, s);
   t->p2p_body_pairs = (int64_t)hp - t->N;
   a.release(d_pairs);
   a.release(rval);

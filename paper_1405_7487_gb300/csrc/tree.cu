@@ -27,26 +27,28 @@ struct Body4<double> {
   using type = double4_32a;
 };
 
-__device__ __forceinline__ bool finite4(double a, double b, double c, double d) {
-  return isfinite(a) && isfinite(b) && isfinite(c) && isfinite(d);
-}
-
-// Per-block min/max of each axis (exact: the inputs are widened to double)
-// and a non-finite flag.
+// Per-block min/max of each axis and a non-finite flag.  Minima and maxima
+// are exact in the input's own precision, so the single-precision path
+// reduces in FP32 (no FP64 per body) and widens each thread's result.
 template <class R>
 __global__ void k_bbox_partial(const R* __restrict__ xyzq, int64_t n, double* __restrict__ part) {
-  double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
-  double bad = 0.0;
+  R lr[3] = {(R)INFINITY, (R)INFINITY, (R)INFINITY}, hr[3] = {-(R)INFINITY, -(R)INFINITY, -(R)INFINITY};
+  bool bad_r = false;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
-    double x = xyzq[4 * i], y = xyzq[4 * i + 1], z = xyzq[4 * i + 2], q = xyzq[4 * i + 3];
-    if (!finite4(x, y, z, q)) {
-      bad = 1.0;
+    const R x = xyzq[4 * i], y = xyzq[4 * i + 1], z = xyzq[4 * i + 2], q = xyzq[4 * i + 3];
+    if (!(isfinite(x) && isfinite(y) && isfinite(z) && isfinite(q))) {
+      bad_r = true;
       continue;
     }
-    lo[0] = fmin(lo[0], x); hi[0] = fmax(hi[0], x);
-    lo[1] = fmin(lo[1], y); hi[1] = fmax(hi[1], y);
-    lo[2] = fmin(lo[2], z); hi[2] = fmax(hi[2], z);
+    lr[0] = fmin(lr[0], x); hr[0] = fmax(hr[0], x);
+    lr[1] = fmin(lr[1], y); hr[1] = fmax(hr[1], y);
+    lr[2] = fmin(lr[2], z); hr[2] = fmax(hr[2], z);
+  }
+  double lo[3], hi[3], bad = bad_r ? 1.0 : 0.0;
+  for (int a = 0; a < 3; ++a) {
+    lo[a] = (double)lr[a];
+    hi[a] = (double)hr[a];
   }
   for (int o = 16; o > 0; o >>= 1) {
     for (int a = 0; a < 3; ++a) {
@@ -334,7 +336,7 @@ void build_tree_impl(fmm_tree* t, const R* xyzq) {
   int hbad = 0;
   GB_CK(cudaMemcpyAsync(hroot, t->d_root, sizeof(hroot), cudaMemcpyDeviceToHost, s));
   GB_CK(cudaMemcpyAsync(&hbad, d_bad, sizeof(int), cudaMemcpyDeviceToHost, s));
-  GB_CK(cudaStreamSynchronize(s));
+  host_sync(a, s);
   a.release(part);
   a.release(d_bad);
   if (hbad) fail(FMM_ERR_NONFINITE, "non-finite position or charge");

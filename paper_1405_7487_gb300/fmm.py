@@ -53,7 +53,7 @@ class Stats(ctypes.Structure):
                 ("ncrit", ctypes.c_int32), ("precision_bits", ctypes.c_int32), ("theta", ctypes.c_double),
                 ("flags", ctypes.c_uint32), ("m2l_engine", ctypes.c_int32),
                 ("workspace_bytes", ctypes.c_int64), ("evaluations", ctypes.c_int32),
-                ("device_errors", ctypes.c_int32),
+                ("device_errors", ctypes.c_int32), ("build_host_syncs", ctypes.c_int32),
                 ("ms", ctypes.c_float * len(PHASES))]
 
 

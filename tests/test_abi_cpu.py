@@ -152,3 +152,27 @@ def test_plain_c_client_compiles_links_and_runs(libpath, tmp_path):
     r = subprocess.run([str(exe)], capture_output=True, text=True, timeout=60)
     assert r.returncode == 0, (r.returncode, r.stdout, r.stderr)
     assert r.stdout.strip() == "invalid argument"
+
+
+def test_stats_struct_layout_matches_header(tmp_path):
+    """The binding's fmm_stats mirror has the header's size and field offsets
+    (a C program prints them)."""
+    import shutil
+    import subprocess
+    if shutil.which("gcc") is None:
+        pytest.skip("needs gcc")
+    from paper_1405_7487_gb300 import fmm
+    names = [n for n, _ in fmm.Stats._fields_]
+    prog = "#include <stdio.h>\n#include <stddef.h>\n#include \"gbfmm.h\"\nint main(void) {\n"
+    prog += '  printf("%zu\\n", sizeof(fmm_stats));\n'
+    for n in names:
+        prog += '  printf("%zu\\n", offsetof(fmm_stats, ' + n + '));\n'
+    prog += "  return 0;\n}\n"
+    src = tmp_path / "layout.c"
+    src.write_text(prog)
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c99", "-Wall", "-Werror", "-I", os.path.join(ROOT, "include"), str(src), "-o",
+                    str(exe)], check=True)
+    out = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
+    assert out[0] == ctypes.sizeof(fmm.Stats)
+    assert out[1:] == [getattr(fmm.Stats, n).offset for n in names]
