@@ -22,6 +22,7 @@ constexpr int kM2LChunk = 16;   // entries accumulated per TMEM partial (tensor-
 constexpr int kErrWait = 1;   // an evaluation kernel gave up on a copy or MMA: that pass is invalid
 constexpr int kErrScan = 2;   // a device scan's look-back gave up: the build is invalid
 constexpr int kErrDrain = 4;  // a block ended while a copy or MMA it issued had not been seen to complete
+constexpr int kErrGrid = 8;   // a grid barrier of a cooperative build kernel gave up: the build is invalid
 
 struct Error {
   int code;

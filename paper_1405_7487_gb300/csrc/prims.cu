@@ -297,6 +297,7 @@ void check_scan_error(Arena& a, cudaStream_t s) {
   GB_CK(cudaMemcpyAsync(&h, a.err, sizeof(int), cudaMemcpyDeviceToHost, s));
   host_sync(a, s);
   if (h & kErrScan) fail(FMM_ERR_TIMEOUT, "a device scan's bounded look-back wait gave up");
+  if (h & kErrGrid) fail(FMM_ERR_TIMEOUT, "a grid barrier of the tree build gave up");
 }
 
 void scan_exclusive_i64(Arena& a, int64_t* d, int64_t n, cudaStream_t s) {

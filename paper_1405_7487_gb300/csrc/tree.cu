@@ -197,125 +197,233 @@ struct Octants {
   unsigned group;  // nonempty-octant bits of this cell's eight lanes
 };
 
-__device__ __forceinline__ Octants octants(const uint64_t* __restrict__ keys, const int32_t* __restrict__ bbeg,
-                                           const int32_t* __restrict__ bend, int ncell, int level, int ncrit) {
+// Lanes d = 0..7 of an aligned group of eight lanes take octant d of cell
+// `cell` (valid false: no cell).  The cell arrays are read through L2: the
+// cooperative level kernel reads cells that other blocks wrote.
+__device__ __forceinline__ Octants octants_at(const uint64_t* __restrict__ keys, const int32_t* bbeg,
+                                              const int32_t* bend, int cell, int d, bool valid, int level,
+                                              int ncrit) {
   Octants o;
-  const int g = blockIdx.x * blockDim.x + threadIdx.x;
-  o.c = g >> 3;
-  o.d = g & 7;
-  o.valid = o.c < ncell;
-  o.s = o.valid ? bbeg[o.c] : 0;
-  o.e = o.valid ? bend[o.c] : 0;
-  o.split = o.valid && o.e - o.s > ncrit && level < kMaxLevel;
+  o.c = cell;
+  o.d = d;
+  o.valid = valid;
+  o.s = valid ? __ldcg(bbeg + cell) : 0;
+  o.e = valid ? __ldcg(bend + cell) : 0;
+  o.split = valid && o.e - o.s > ncrit && level < kMaxLevel;
   o.b = o.s;
-  if (o.split && o.d > 0) o.b = lower_digit(keys, o.s, o.e, 3 * (kMaxLevel - level - 1), o.d);
+  if (o.split && d > 0) o.b = lower_digit(keys, o.s, o.e, 3 * (kMaxLevel - level - 1), d);
   o.nb = __shfl_down_sync(0xffffffffu, o.b, 1, 8);
-  if (o.d == 7) o.nb = o.e;
+  if (d == 7) o.nb = o.e;
   const unsigned m = __ballot_sync(0xffffffffu, o.split && o.nb > o.b);
   o.group = (m >> (threadIdx.x & 24)) & 0xffu;
   return o;
 }
 
-__global__ void k_split_count(const uint64_t* __restrict__ keys, const int32_t* __restrict__ bbeg,
-                              const int32_t* __restrict__ bend, int ncell, int level, int ncrit,
-                              int64_t* __restrict__ nchild) {
-  const Octants o = octants(keys, bbeg, bend, ncell, level, ncrit);
-  if (o.valid && o.d == 0) nchild[o.c] = __popc(o.group);
-}
-
-__global__ void k_split_write(const uint64_t* __restrict__ keys, const int32_t* __restrict__ bbeg,
-                              const int32_t* __restrict__ bend, const int32_t* __restrict__ ix,
-                              const int32_t* __restrict__ iy, const int32_t* __restrict__ iz,
-                              int ncell, int level, int ncrit, int first_cell, int first_child,
-                              const int64_t* __restrict__ off, int32_t* __restrict__ cbeg,
-                              int32_t* __restrict__ nch, int32_t* __restrict__ o_bbeg,
-                              int32_t* __restrict__ o_bend, int32_t* __restrict__ o_ix,
-                              int32_t* __restrict__ o_iy, int32_t* __restrict__ o_iz,
-                              int32_t* __restrict__ o_parent) {
-  const Octants o = octants(keys, bbeg, bend, ncell, level, ncrit);
-  if (!o.valid) return;
-  const int k0 = (int)off[o.c];
-  const int n = __popc(o.group);
-  if ((o.group >> o.d) & 1u) {
-    const int k = k0 + __popc(o.group & ((1u << o.d) - 1u));
-    o_bbeg[k] = o.b;
-    o_bend[k] = o.nb;
-    o_ix[k] = 2 * ix[o.c] + ((o.d >> 2) & 1);
-    o_iy[k] = 2 * iy[o.c] + ((o.d >> 1) & 1);
-    o_iz[k] = 2 * iz[o.c] + (o.d & 1);
-    o_parent[k] = first_cell + o.c;
-  }
-  if (o.d == 0) {
-    cbeg[o.c] = n > 0 ? first_child + k0 : -1;
-    nch[o.c] = n;
-  }
-}
-
-__global__ void k_leaf_flags(const int32_t* __restrict__ nch, int n, int64_t* __restrict__ f) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) f[i] = nch[i] == 0;
-}
-
-__global__ void k_leaf_compact(const int32_t* __restrict__ nch, const int64_t* __restrict__ off,
-                               int n, int32_t* __restrict__ leaves, int32_t* __restrict__ leaf_of) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  if (nch[i] == 0) {
-    leaves[off[i]] = i;
-    leaf_of[i] = (int32_t)off[i];
-  } else {
-    leaf_of[i] = -1;
-  }
-}
-
 inline unsigned blocks(int64_t n, int t = kThreads) { return (unsigned)((n + t - 1) / t); }
 
-// The root cell: all bodies, integer coordinates 0, no parent.
-__global__ void k_root_cell(int32_t n, int32_t* bbeg, int32_t* bend, int32_t* ix, int32_t* iy, int32_t* iz,
-                            int32_t* parent) {
-  *bbeg = 0;
-  *bend = n;
-  *ix = *iy = *iz = 0;
-  *parent = -1;
+// ---------------------------------------------------------------- levels
+// All levels and the leaf list in one cooperative launch (every block is
+// resident, so blocks can wait for one another).  Level l's cells are split
+// into contiguous chunks, one per block; a level takes two grid barriers:
+//   count: each block counts the children of its cells (eight lanes per cell,
+//          as in octants_at()) and publishes its total;
+//   write: each block adds the totals of the blocks before it (the children
+//          of a level keep their parents' order, so the cell order is the
+//          breadth-first (level, Morton) order) and writes its children.
+// The barrier waits are bounded; one that runs out sets kErrGrid and an abort
+// flag that ends every other wait.
+struct LevelState {
+  int level_begin[kMaxLevel + 3];  // first cell of each level, then the end
+  int nlevel, ncell, nleaf, overflow;
+  unsigned bar_count, bar_gen, abort;
+};
+
+constexpr long long kGridWaitNs = 2000000000ll;  // 2 s: far beyond any real wait
+
+__device__ __forceinline__ long long tree_ns() {
+  long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
 }
 
-struct LevelArrays {
-  int n = 0;
-  int32_t *bbeg, *bend, *ix, *iy, *iz, *parent, *cbeg, *nch;
-};
-
-// One level's arrays for the concatenation kernel: its first cell and the
-// eight per-cell fields (ix, iy, iz, bbeg, bend, cbeg, nch, parent).
-struct LevelSrc {
-  int first;
-  const int32_t* f[8];
-};
-
-// Breadth-first cell arrays from the per-level arrays, every level in one
-// launch: cell i finds its level by binary search over the first cells.
-__global__ void k_concat_levels(const LevelSrc* __restrict__ lv, int nlevel, int ncell, int32_t* __restrict__ level,
-                                int32_t* __restrict__ o0, int32_t* __restrict__ o1, int32_t* __restrict__ o2,
-                                int32_t* __restrict__ o3, int32_t* __restrict__ o4, int32_t* __restrict__ o5,
-                                int32_t* __restrict__ o6, int32_t* __restrict__ o7) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= ncell) return;
-  int lo = 0, hi = nlevel;  // last level whose first cell is <= i
-  while (hi - lo > 1) {
-    const int mid = (lo + hi) >> 1;
-    if (lv[mid].first <= i) lo = mid;
-    else hi = mid;
+// Grid-wide barrier of a cooperative launch; false once a wait has given up
+// (this block's or another's).
+__device__ bool grid_barrier(LevelState* st, int* err) {
+  __shared__ int ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    ok = 1;
+    volatile unsigned* gen = &st->bar_gen;
+    const unsigned g = *gen;
+    __threadfence();
+    if (atomicAdd(&st->bar_count, 1u) == gridDim.x - 1) {
+      atomicExch(&st->bar_count, 0u);
+      __threadfence();
+      atomicAdd(&st->bar_gen, 1u);
+    } else {
+      const long long t0 = tree_ns();
+      while (*gen == g) {
+        if (*(volatile unsigned*)&st->abort || tree_ns() - t0 > kGridWaitNs) {
+          atomicOr(err, kErrGrid);
+          atomicExch(&st->abort, 1u);
+          ok = 0;
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    __threadfence();
   }
-  const LevelSrc& L = lv[lo];
-  const int k = i - L.first;
-  level[i] = lo;
-  o0[i] = L.f[0][k];
-  o1[i] = L.f[1][k];
-  o2[i] = L.f[2][k];
-  o3[i] = L.f[3][k];
-  o4[i] = L.f[4][k];
-  o5[i] = L.f[5][k];
-  o6[i] = L.f[6][k];
-  o7[i] = L.f[7][k];
+  __syncthreads();
+  return ok != 0;
+}
+
+// Sum of partial[0 .. upto) and of partial[0 .. n) over the block.
+__device__ void block_prefix_total(const int* partial, int upto, int n, int& before, int& total) {
+  __shared__ int sb[kThreads / 32], st_[kThreads / 32];
+  int b = 0, t = 0;
+  for (int j = threadIdx.x; j < n; j += blockDim.x) {
+    const int v = __ldcg(partial + j);
+    t += v;
+    if (j < upto) b += v;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    b += __shfl_down_sync(0xffffffffu, b, o);
+    t += __shfl_down_sync(0xffffffffu, t, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    sb[threadIdx.x >> 5] = b;
+    st_[threadIdx.x >> 5] = t;
+  }
+  __syncthreads();
+  before = total = 0;
+  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+    before += sb[w];
+    total += st_[w];
+  }
+  __syncthreads();
+}
+
+__global__ void __launch_bounds__(kThreads) k_tree_levels(const uint64_t* __restrict__ keys, int n, int ncrit,
+                                                          int cap, Cells c, int32_t* __restrict__ leaves,
+                                                          int32_t* __restrict__ leaf_of, int* __restrict__ partial,
+                                                          LevelState* __restrict__ st, int* __restrict__ err) {
+  __shared__ int pass_cnt[kThreads / 8];
+  __shared__ int chunk_sum;
+  const int G = gridDim.x, blk = blockIdx.x;
+  const int lane8 = threadIdx.x & 7, slot = threadIdx.x >> 3;  // 32 cells per pass
+  if (blk == 0 && threadIdx.x == 0) {
+    c.level[0] = 0;
+    c.bbeg[0] = 0;
+    c.bend[0] = n;
+    c.ix[0] = c.iy[0] = c.iz[0] = 0;
+    c.parent[0] = -1;
+  }
+  int lb = 0, le = 1, nlevel = 0;
+  bool fine = grid_barrier(st, err), over = false;
+  for (int l = 0; fine && le > lb; ++l) {
+    nlevel = l + 1;
+    const int ncur = le - lb, ch = (ncur + G - 1) / G;
+    const int c0 = lb + min(blk * ch, ncur), c1 = lb + min((blk + 1) * ch, ncur);
+    // count
+    if (threadIdx.x == 0) chunk_sum = 0;
+    __syncthreads();
+    for (int cb = c0; cb < c1; cb += kThreads / 8) {
+      const int cell = cb + slot;
+      const Octants o = octants_at(keys, c.bbeg, c.bend, cell, lane8, cell < c1, l, ncrit);
+      if (o.valid && lane8 == 0) atomicAdd(&chunk_sum, __popc(o.group));
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) partial[blk] = chunk_sum;
+    fine = grid_barrier(st, err);
+    if (!fine) break;
+    int before, total;
+    block_prefix_total(partial, blk, G, before, total);
+    if ((int64_t)le + total > cap) {  // every block sees the same total
+      if (blk == 0 && threadIdx.x == 0) st->overflow = 1;
+      over = true;
+      break;
+    }
+    // write
+    int run = le + before;
+    for (int cb = c0; cb < c1; cb += kThreads / 8) {
+      const int cell = cb + slot;
+      const Octants o = octants_at(keys, c.bbeg, c.bend, cell, lane8, cell < c1, l, ncrit);
+      const int nchild = __popc(o.group);
+      if (lane8 == 0) pass_cnt[slot] = o.valid ? nchild : 0;
+      __syncthreads();
+      int k0 = run;
+      for (int q = 0; q < slot; ++q) k0 += pass_cnt[q];
+      int pass_total = 0;
+      for (int q = 0; q < kThreads / 8; ++q) pass_total += pass_cnt[q];
+      if (o.valid) {
+        if ((o.group >> lane8) & 1u) {
+          const int k = k0 + __popc(o.group & ((1u << lane8) - 1u));
+          c.bbeg[k] = o.b;
+          c.bend[k] = o.nb;
+          c.ix[k] = 2 * __ldcg(c.ix + cell) + ((lane8 >> 2) & 1);
+          c.iy[k] = 2 * __ldcg(c.iy + cell) + ((lane8 >> 1) & 1);
+          c.iz[k] = 2 * __ldcg(c.iz + cell) + (lane8 & 1);
+          c.parent[k] = cell;
+          c.level[k] = l + 1;
+        }
+        if (lane8 == 0) {
+          c.cbeg[cell] = nchild > 0 ? k0 : -1;
+          c.nch[cell] = nchild;
+        }
+      }
+      run += pass_total;
+      __syncthreads();
+    }
+    if (blk == 0 && threadIdx.x == 0) st->level_begin[l + 1] = le;
+    lb = le;
+    le += total;
+    fine = grid_barrier(st, err);
+  }
+  if (!fine || over) return;
+  const int ncell = le;
+  // leaves, in cell order
+  {
+    const int ch = (ncell + G - 1) / G;
+    const int c0 = min(blk * ch, ncell), c1 = min((blk + 1) * ch, ncell);
+    if (threadIdx.x == 0) chunk_sum = 0;
+    __syncthreads();
+    for (int i = c0 + threadIdx.x; i < c1; i += blockDim.x)
+      if (__ldcg(c.nch + i) == 0) atomicAdd(&chunk_sum, 1);
+    __syncthreads();
+    if (threadIdx.x == 0) partial[blk] = chunk_sum;
+    if (!grid_barrier(st, err)) return;
+    int before, total;
+    block_prefix_total(partial, blk, G, before, total);
+    __shared__ int wcnt[kThreads / 32];
+    int run = before;
+    for (int cb = c0; cb < c1; cb += blockDim.x) {
+      const int i = cb + threadIdx.x;
+      const bool leaf = i < c1 && __ldcg(c.nch + i) == 0;
+      const unsigned m = __ballot_sync(0xffffffffu, leaf);
+      if ((threadIdx.x & 31) == 0) wcnt[threadIdx.x >> 5] = __popc(m);
+      __syncthreads();
+      int k = run + __popc(m & ((1u << (threadIdx.x & 31)) - 1u));
+      int pass_total = 0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+        if (w < (int)(threadIdx.x >> 5)) k += wcnt[w];
+        pass_total += wcnt[w];
+      }
+      if (i < c1) {
+        leaf_of[i] = leaf ? k : -1;
+        if (leaf) leaves[k] = i;
+      }
+      run += pass_total;
+      __syncthreads();
+    }
+    if (blk == 0 && threadIdx.x == 0) {
+      st->level_begin[0] = 0;
+      st->level_begin[nlevel] = ncell;
+      st->nlevel = nlevel;
+      st->ncell = ncell;
+      st->nleaf = total;
+    }
+  }
 }
 
 template <class R>
@@ -332,23 +440,10 @@ void build_tree_impl(fmm_tree* t, const R* xyzq) {
   GB_LAUNCH("k_bbox_partial");
   k_bbox_final<<<1, kThreads, 0, s>>>(part, nb, t->d_root, d_bad);
   GB_LAUNCH("k_bbox_final");
-  double hroot[13];
-  int hbad = 0;
-  GB_CK(cudaMemcpyAsync(hroot, t->d_root, sizeof(hroot), cudaMemcpyDeviceToHost, s));
-  GB_CK(cudaMemcpyAsync(&hbad, d_bad, sizeof(int), cudaMemcpyDeviceToHost, s));
-  host_sync(a, s);
-  a.release(part);
-  a.release(d_bad);
-  if (hbad) fail(FMM_ERR_NONFINITE, "non-finite position or charge");
-  for (int k = 0; k < 3; ++k) {
-    t->root.lo[k] = hroot[k];
-    t->root.hi[k] = hroot[3 + k];
-    t->root.centre[k] = hroot[6 + k];
-    t->root.corner[k] = hroot[10 + k];
-  }
-  t->root.H = hroot[9];
   // --- keys and stable sort (ties keep input order: LSD radix is stable and
-  // the initial order is the input order)
+  // the initial order is the input order).  The root cube stays on the
+  // device until the levels are read back; a non-finite input still gives
+  // in-range keys (the conversion of NaN gives 0 and the key is clamped).
   uint64_t* keys = alloc_n<uint64_t>(a, N);
   int32_t* idx = alloc_n<int32_t>(a, N);
   k_keys<R><<<blocks(N), kThreads, 0, s>>>(xyzq, N, t->d_root, keys, idx);
@@ -364,88 +459,74 @@ void build_tree_impl(fmm_tree* t, const R* xyzq) {
   t->work = alloc_n<B4>(a, N);
   GB_CK(cudaMemcpyAsync(t->work, bodies, sizeof(B4) * N, cudaMemcpyDeviceToDevice, s));
 
-  // --- levels
-  std::vector<LevelArrays> lv;
-  LevelArrays root;
-  root.n = 1;
-  root.bbeg = alloc_n<int32_t>(a, 1);
-  root.bend = alloc_n<int32_t>(a, 1);
-  root.ix = alloc_n<int32_t>(a, 1);
-  root.iy = alloc_n<int32_t>(a, 1);
-  root.iz = alloc_n<int32_t>(a, 1);
-  root.parent = alloc_n<int32_t>(a, 1);
-  k_root_cell<<<1, 1, 0, s>>>((int32_t)N, root.bbeg, root.bend, root.ix, root.iy, root.iz, root.parent);
-  GB_LAUNCH("k_root_cell");
-  lv.push_back(root);
-  int first = 0;
-  for (int l = 0;; ++l) {
-    LevelArrays& cur = lv[l];
-    cur.cbeg = alloc_n<int32_t>(a, cur.n);
-    cur.nch = alloc_n<int32_t>(a, cur.n);
-    int64_t* off = alloc_n<int64_t>(a, cur.n);
-    k_split_count<<<blocks(8 * (int64_t)cur.n), kThreads, 0, s>>>(t->keys, cur.bbeg, cur.bend, cur.n, l,
-                                                                   t->ncrit, off);
-    GB_LAUNCH("k_split_count");
-    const int64_t nnext = scan_exclusive_i64_total(a, off, cur.n, s);
-    if (nnext > 0x7fffffff - first - cur.n) fail(FMM_ERR_ARG, "too many cells");
-    LevelArrays nx;
-    nx.n = (int)nnext;
-    if (nnext > 0) {
-      nx.bbeg = alloc_n<int32_t>(a, nnext);
-      nx.bend = alloc_n<int32_t>(a, nnext);
-      nx.ix = alloc_n<int32_t>(a, nnext);
-      nx.iy = alloc_n<int32_t>(a, nnext);
-      nx.iz = alloc_n<int32_t>(a, nnext);
-      nx.parent = alloc_n<int32_t>(a, nnext);
-    }
-    k_split_write<<<blocks(8 * (int64_t)cur.n), kThreads, 0, s>>>(
-        t->keys, cur.bbeg, cur.bend, cur.ix, cur.iy, cur.iz, cur.n, l, t->ncrit, first,
-        first + cur.n, off, cur.cbeg, cur.nch, nx.bbeg, nx.bend, nx.ix, nx.iy, nx.iz, nx.parent);
-    GB_LAUNCH("k_split_write");
-    a.release(off);
-    first += cur.n;
-    if (nnext == 0) break;
-    lv.push_back(nx);
-  }
-  // --- concatenate the levels (breadth-first cell order)
-  t->nlevel = (int)lv.size();
-  t->level_begin.assign(1, 0);
-  for (auto& L : lv) t->level_begin.push_back(t->level_begin.back() + L.n);
-  const int nc = t->level_begin.back();
-  t->ncell = nc;
-  Cells& c = t->c;
-  int32_t** fields[9] = {&c.level, &c.ix, &c.iy, &c.iz, &c.bbeg, &c.bend, &c.cbeg, &c.nch, &c.parent};
-  for (auto f : fields) *f = alloc_n<int32_t>(a, nc);
+  // --- levels and leaves: one cooperative launch, then one read-back of the
+  // level sizes together with the root cube.  The cell arrays are sized for
+  // 8 N / ncrit + 4096 cells first (the trees here hold 2 to 4 N / ncrit);
+  // if the tree needs more, the launch is repeated at the bound
+  // sum_l min(8^l, N, 8 floor(N / (ncrit + 1))), l <= 21.
+  int sms = 0, dev = 0, per_sm = 0;
+  GB_CK(cudaGetDevice(&dev));
+  GB_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  GB_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tree_levels, kThreads, 0));
+  const int G = std::max(1, std::min(2, per_sm) * sms);
+  int64_t bound = 0;
   {
-    std::vector<LevelSrc> h(lv.size());
-    for (size_t l = 0; l < lv.size(); ++l) {
-      const LevelArrays& L = lv[l];
-      h[l].first = t->level_begin[l];
-      const int32_t* f[8] = {L.ix, L.iy, L.iz, L.bbeg, L.bend, L.cbeg, L.nch, L.parent};
-      for (int k = 0; k < 8; ++k) h[l].f[k] = f[k];
+    const int64_t split_max = 8 * (N / ((int64_t)t->ncrit + 1));
+    int64_t p8 = 1;
+    for (int l = 0; l <= kMaxLevel; ++l) {
+      bound += l == 0 ? 1 : std::min(std::min(p8, N), split_max);
+      p8 = std::min<int64_t>(p8 * 8, 1ll << 40);
     }
-    LevelSrc* d = alloc_n<LevelSrc>(a, h.size());
-    GB_CK(cudaMemcpyAsync(d, h.data(), sizeof(LevelSrc) * h.size(), cudaMemcpyHostToDevice, s));
-    k_concat_levels<<<blocks(nc), kThreads, 0, s>>>(d, (int)h.size(), nc, c.level, c.ix, c.iy, c.iz, c.bbeg,
-                                                     c.bend, c.cbeg, c.nch, c.parent);
-    GB_LAUNCH("k_concat_levels");
-    // the H2D copy reads h (pageable) before returning; d is freed in order
-    a.release(d);
   }
-  for (auto& L : lv) {
-    int32_t* all[8] = {L.ix, L.iy, L.iz, L.bbeg, L.bend, L.cbeg, L.nch, L.parent};
-    for (auto p : all) a.release(p);
+  if (bound > 0x7fffffff) bound = 0x7fffffff;
+  int64_t cap = std::min<int64_t>(bound, 8 * ((N + t->ncrit - 1) / t->ncrit) + 4096);
+  int* partial = alloc_n<int>(a, G);
+  LevelState* d_st = alloc_n<LevelState>(a, 1);
+  LevelState hst;
+  double hroot[13];
+  int hbad = 0;
+  for (int attempt = 0;; ++attempt) {
+    Cells& c = t->c;
+    int32_t** fields[9] = {&c.level, &c.ix, &c.iy, &c.iz, &c.bbeg, &c.bend, &c.cbeg, &c.nch, &c.parent};
+    for (auto f : fields) *f = alloc_n<int32_t>(a, cap);
+    t->leaves = alloc_n<int32_t>(a, cap);
+    t->leaf_of_cell = alloc_n<int32_t>(a, cap);
+    GB_CK(cudaMemsetAsync(d_st, 0, sizeof(LevelState), s));
+    const int n32 = (int)N, ncrit = t->ncrit, cap32 = (int)cap;
+    int* err = a.err;
+    void* args[] = {(void*)&keys, (void*)&n32, (void*)&ncrit, (void*)&cap32, (void*)&c,
+                    (void*)&t->leaves, (void*)&t->leaf_of_cell, (void*)&partial, (void*)&d_st, (void*)&err};
+    GB_CK(cudaLaunchCooperativeKernel((const void*)k_tree_levels, dim3(G), dim3(kThreads), args, 0, s));
+    GB_LAUNCH("k_tree_levels");
+    GB_CK(cudaMemcpyAsync(&hst, d_st, sizeof(LevelState), cudaMemcpyDeviceToHost, s));
+    if (attempt == 0) {
+      GB_CK(cudaMemcpyAsync(hroot, t->d_root, sizeof(hroot), cudaMemcpyDeviceToHost, s));
+      GB_CK(cudaMemcpyAsync(&hbad, d_bad, sizeof(int), cudaMemcpyDeviceToHost, s));
+    }
+    check_scan_error(a, s);  // synchronises; a grid wait past its limit is FMM_ERR_TIMEOUT
+    if (attempt == 0 && hbad) fail(FMM_ERR_NONFINITE, "non-finite position or charge");
+    if (!hst.overflow) break;
+    if (cap >= bound) fail(FMM_ERR_ARG, "too many cells");
+    for (auto f : fields) a.release(*f);
+    a.release(t->leaves);
+    a.release(t->leaf_of_cell);
+    cap = bound;
   }
-  // --- leaves
-  int64_t* flag = alloc_n<int64_t>(a, nc);
-  k_leaf_flags<<<blocks(nc), kThreads, 0, s>>>(c.nch, nc, flag);
-  GB_LAUNCH("k_leaf_flags");
-  t->nleaf = (int)scan_exclusive_i64_total(a, flag, nc, s);
-  t->leaves = alloc_n<int32_t>(a, t->nleaf);
-  t->leaf_of_cell = alloc_n<int32_t>(a, nc);
-  k_leaf_compact<<<blocks(nc), kThreads, 0, s>>>(c.nch, flag, nc, t->leaves, t->leaf_of_cell);
-  GB_LAUNCH("k_leaf_compact");
-  a.release(flag);
+  a.release(partial);
+  a.release(d_st);
+  a.release(part);
+  a.release(d_bad);
+  for (int k = 0; k < 3; ++k) {
+    t->root.lo[k] = hroot[k];
+    t->root.hi[k] = hroot[3 + k];
+    t->root.centre[k] = hroot[6 + k];
+    t->root.corner[k] = hroot[10 + k];
+  }
+  t->root.H = hroot[9];
+  t->nlevel = hst.nlevel;
+  t->ncell = hst.ncell;
+  t->nleaf = hst.nleaf;
+  t->level_begin.assign(hst.level_begin, hst.level_begin + hst.nlevel + 1);
 }
 
 }  // namespace
