@@ -101,14 +101,17 @@ void create_tree(fmm_tree* t, const R* xyzq) {
   }
   t->check_rec = alloc_n<unsigned long long>(a, 4);
   GB_CK(cudaMemsetAsync(t->check_rec, 0, 4 * sizeof(unsigned long long), s));
-  t->lim = Lim{t->N, t->ncell, t->nleaf, t->Kp, t->ntile, t->nentry, t->nclass, t->n_p2p_ranges, t->check_rec};
   mark(FMM_PH_BUILD_OPS, 1);
   mark(FMM_PH_BUILD_TOTAL, 1);
-  long long nitem[2] = {0, 0};
+  long long nitem[2] = {0, 0}, tail[4] = {0, 0, 0, 0};
   if (t->p2p_nitem) GB_CK(cudaMemcpyAsync(nitem, t->p2p_nitem, sizeof(nitem), cudaMemcpyDeviceToHost, s));
+  GB_CK(cudaMemcpyAsync(tail, t->d_tail, sizeof(tail), cudaMemcpyDeviceToHost, s));
   check_scan_error(a, s);  // synchronises
   t->p2p_nitem_host = nitem[0];
   t->p2p_nbig_host = nitem[1];
+  t->n_p2p_ranges = tail[0];
+  t->p2p_body_pairs = tail[1] - t->N;
+  t->lim = Lim{t->N, t->ncell, t->nleaf, t->Kp, t->ntile, t->nentry, t->nclass, t->n_p2p_ranges, t->check_rec};
   t->build_syncs = a.nsync;
   if (timing)
     for (int ph : {FMM_PH_BUILD_TOTAL, FMM_PH_BUILD_TREE, FMM_PH_BUILD_LISTS, FMM_PH_BUILD_PLAN, FMM_PH_BUILD_OPS})

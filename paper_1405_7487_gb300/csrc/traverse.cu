@@ -27,6 +27,7 @@
 #include <climits>
 
 #include "common.cuh"
+#include "grid.cuh"
 
 namespace gbfmm {
 namespace {
@@ -113,6 +114,7 @@ __device__ __forceinline__ void block_scan3(int v[3], int tot[3]) {
     v[j] = before + inc[j] - v[j];
     tot[j] = all;
   }
+  __syncthreads();  // ws is free for the next call
 }
 
 // Per block of frontier pairs: the totals of the three outputs, segment-major
@@ -135,49 +137,26 @@ __device__ __forceinline__ uint64_t pair_key(int tgt, int src) {
   return ((uint64_t)(uint32_t)tgt << 32) | (uint32_t)src;
 }
 
-__global__ void __launch_bounds__(kThreads) k_trav_write(const int2* __restrict__ fr, int64_t n, CellView c,
-                                                         double theta2, int circ, const int64_t* __restrict__ off,
-                                                         int64_t base_m, int64_t base_p, int2* __restrict__ next,
-                                                         uint64_t* __restrict__ m2l, int64_t m2l_at,
-                                                         uint64_t* __restrict__ p2p, int64_t p2p_at,
-                                                         int32_t* __restrict__ m2l_has,
-                                                         unsigned long long* __restrict__ m2l_maxd) {
-  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  int A = 0, B = 0, k = -1, v[3] = {0, 0, 0}, tot[3];
-  unsigned dm = 0;  // M2L pair: largest |offset| component in units of the smaller cell's half side
-  if (i < n) {
-    A = fr[i].x;
-    B = fr[i].y;
-    k = decide(c, A, B, theta2, circ);
-    pair_counts(c, A, B, k, v[0], v[1], v[2]);
-    if (k == 2) {
-      const int la = c.level[A], lb = c.level[B], sh = kMaxLevel - (la > lb ? la : lb);
-      const int co[2][3] = {{c.ix[A], c.iy[A], c.iz[A]}, {c.ix[B], c.iy[B], c.iz[B]}};
-      for (int d = 0; d < 3; ++d) {
-        const int64_t o = (((2ll * co[0][d] + 1) << (kMaxLevel - la)) - ((2ll * co[1][d] + 1) << (kMaxLevel - lb))) >> sh;
-        dm = max(dm, (unsigned)(o < 0 ? -o : o));
-      }
-      // the cells that take M2L (read first: a cell has many M2L pairs)
-      if (!m2l_has[A]) m2l_has[A] = 1;
-      if (!m2l_has[B]) m2l_has[B] = 1;
-    }
+// M2L pair {A, B}: marks both cells as M2L cells (read first: a cell has
+// many M2L pairs) and returns the largest |offset| component in units of the
+// smaller cell's half side (the class offsets of the plan).
+__device__ __forceinline__ unsigned mark_m2l(const CellView& c, int A, int B, int32_t* __restrict__ m2l_has) {
+  const int la = c.level[A], lb = c.level[B], sh = kMaxLevel - (la > lb ? la : lb);
+  const int co[2][3] = {{c.ix[A], c.iy[A], c.iz[A]}, {c.ix[B], c.iy[B], c.iz[B]}};
+  unsigned dm = 0;
+  for (int d = 0; d < 3; ++d) {
+    const int64_t o = (((2ll * co[0][d] + 1) << (kMaxLevel - la)) - ((2ll * co[1][d] + 1) << (kMaxLevel - lb))) >> sh;
+    dm = max(dm, (unsigned)(o < 0 ? -o : o));
   }
-  block_scan3(v, tot);
-  {
-    __shared__ unsigned wmax[kThreads / 32];
-    dm = __reduce_max_sync(0xffffffffu, dm);
-    if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = dm;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      for (int w = 1; w < kThreads / 32; ++w) dm = max(dm, wmax[w]);
-      if (dm > *(volatile unsigned long long*)m2l_maxd) atomicMax(m2l_maxd, (unsigned long long)dm);
-    }
-  }
-  if (i >= n) return;
-  const int nb = gridDim.x;
-  int64_t o = off[blockIdx.x] + v[0];
-  const int64_t om = m2l_at + off[nb + blockIdx.x] - base_m + v[1];
-  const int64_t op = p2p_at + off[2 * nb + blockIdx.x] - base_p + v[2];
+  if (!m2l_has[A]) m2l_has[A] = 1;
+  if (!m2l_has[B]) m2l_has[B] = 1;
+  return dm;
+}
+
+// The outputs of pair {A, B} (decision k) at next[o..], m2l[om..], p2p[op..].
+__device__ __forceinline__ void write_pair(const CellView& c, int A, int B, int k, int64_t o, int64_t om, int64_t op,
+                                           int2* __restrict__ next, uint64_t* __restrict__ m2l,
+                                           uint64_t* __restrict__ p2p) {
   switch (k) {
     case 0: p2p[op] = pair_key(A, A); break;
     case 1: {
@@ -210,6 +189,141 @@ __global__ void __launch_bounds__(kThreads) k_trav_write(const int2* __restrict_
         for (int y = 0; y < nb; ++y) next[o++] = make_int2(a0 + x, b0 + y);
       break;
     }
+  }
+}
+
+// The largest class offset of the block's M2L pairs into *m2l_maxd (read
+// first: most blocks find it already as large).
+__device__ __forceinline__ void block_maxd(unsigned dm, unsigned long long* __restrict__ m2l_maxd) {
+  __shared__ unsigned wmax[kThreads / 32];
+  dm = __reduce_max_sync(0xffffffffu, dm);
+  if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = dm;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < kThreads / 32; ++w) dm = max(dm, wmax[w]);
+    if (dm > *(volatile unsigned long long*)m2l_maxd) atomicMax(m2l_maxd, (unsigned long long)dm);
+  }
+  __syncthreads();
+}
+
+__global__ void __launch_bounds__(kThreads) k_trav_write(const int2* __restrict__ fr, int64_t n, CellView c,
+                                                         double theta2, int circ, const int64_t* __restrict__ off,
+                                                         int64_t base_m, int64_t base_p, int2* __restrict__ next,
+                                                         uint64_t* __restrict__ m2l, int64_t m2l_at,
+                                                         uint64_t* __restrict__ p2p, int64_t p2p_at,
+                                                         int32_t* __restrict__ m2l_has,
+                                                         unsigned long long* __restrict__ m2l_maxd) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  int A = 0, B = 0, k = -1, v[3] = {0, 0, 0}, tot[3];
+  unsigned dm = 0;
+  if (i < n) {
+    A = fr[i].x;
+    B = fr[i].y;
+    k = decide(c, A, B, theta2, circ);
+    pair_counts(c, A, B, k, v[0], v[1], v[2]);
+    if (k == 2) dm = mark_m2l(c, A, B, m2l_has);
+  }
+  block_scan3(v, tot);
+  block_maxd(dm, m2l_maxd);
+  if (i >= n) return;
+  const int nb = gridDim.x;
+  write_pair(c, A, B, k, off[blockIdx.x] + v[0], m2l_at + off[nb + blockIdx.x] - base_m + v[1],
+             p2p_at + off[2 * nb + blockIdx.x] - base_p + v[2], next, m2l, p2p);
+}
+
+// The whole traversal in one cooperative launch, while the frontier and the
+// lists fit the buffers given (capF pairs per frontier, cap_m and cap_p list
+// entries).  Each level splits the frontier into contiguous chunks, one per
+// block: the blocks count their outputs, publish the three totals and, after
+// a grid barrier, add the totals of the blocks before them and write, so the
+// outputs come in frontier order, as with the per-level launches.  The next
+// frontier alternates between F0 and F1 (read through L2: other blocks wrote
+// it).  If a level would overflow a buffer every block stops before writing
+// it and st->overflow is set.
+struct TravState {
+  long long nm, np;
+  int nlevel, overflow;
+  GridBar bar;
+};
+
+__global__ void __launch_bounds__(kThreads) k_traverse(CellView c, double theta2, int circ, int2* F0, int2* F1,
+                                                       long long capF, uint64_t* __restrict__ m2l, long long cap_m,
+                                                       uint64_t* __restrict__ p2p, long long cap_p,
+                                                       int32_t* __restrict__ m2l_has,
+                                                       unsigned long long* __restrict__ m2l_maxd,
+                                                       long long* __restrict__ partial, TravState* st,
+                                                       int* __restrict__ err) {
+  const int G = gridDim.x, blk = blockIdx.x;
+  if (blk == 0 && threadIdx.x == 0) F0[0] = make_int2(0, 0);
+  int2 *cur = F0, *nxt = F1;
+  long long nf = 1, nm = 0, np = 0;
+  int nlevel = 0;
+  unsigned dm = 0;
+  bool fine = grid_barrier(&st->bar, err), over = false;
+  while (fine && nf > 0) {
+    ++nlevel;
+    const long long ch = (nf + G - 1) / G;
+    const long long f0 = min(blk * ch, nf), f1 = min((blk + 1) * ch, nf);
+    long long cnt[3] = {0, 0, 0};
+    for (long long i = f0 + threadIdx.x; i < f1; i += kThreads) {
+      const int2 pr = __ldcg(cur + i);
+      int v[3];
+      pair_counts(c, pr.x, pr.y, decide(c, pr.x, pr.y, theta2, circ), v[0], v[1], v[2]);
+      for (int j = 0; j < 3; ++j) cnt[j] += v[j];
+    }
+    {
+      __shared__ long long wc[3][kThreads / 32];
+      for (int j = 0; j < 3; ++j)
+        for (int o = 16; o > 0; o >>= 1) cnt[j] += __shfl_down_sync(0xffffffffu, cnt[j], o);
+      if ((threadIdx.x & 31) == 0)
+        for (int j = 0; j < 3; ++j) wc[j][threadIdx.x >> 5] = cnt[j];
+      __syncthreads();
+      if (threadIdx.x == 0)
+        for (int j = 0; j < 3; ++j) {
+          long long t = 0;
+          for (int w = 0; w < kThreads / 32; ++w) t += wc[j][w];
+          partial[(int64_t)j * G + blk] = t;
+        }
+    }
+    fine = grid_barrier(&st->bar, err);
+    if (!fine) break;
+    long long before[3], total[3];
+    block_prefix_totals<long long, 3>(partial, blk, G, before, total);
+    if (total[0] > capF || nm + total[1] > cap_m || np + total[2] > cap_p) {  // the same in every block
+      if (blk == 0 && threadIdx.x == 0) st->overflow = 1;
+      over = true;
+      break;
+    }
+    long long run[3] = {before[0], nm + before[1], np + before[2]};
+    for (long long base = f0; base < f1; base += kThreads) {
+      const long long i = base + threadIdx.x;
+      int A = 0, B = 0, k = -1, v[3] = {0, 0, 0}, tot[3];
+      if (i < f1) {
+        const int2 pr = __ldcg(cur + i);
+        A = pr.x;
+        B = pr.y;
+        k = decide(c, A, B, theta2, circ);
+        pair_counts(c, A, B, k, v[0], v[1], v[2]);
+        if (k == 2) dm = max(dm, mark_m2l(c, A, B, m2l_has));
+      }
+      block_scan3(v, tot);
+      if (i < f1) write_pair(c, A, B, k, run[0] + v[0], run[1] + v[1], run[2] + v[2], nxt, m2l, p2p);
+      for (int j = 0; j < 3; ++j) run[j] += tot[j];
+    }
+    fine = grid_barrier(&st->bar, err);
+    int2* t = cur;
+    cur = nxt;
+    nxt = t;
+    nf = total[0];
+    nm += total[1];
+    np += total[2];
+  }
+  if (!fine) return;
+  block_maxd(dm, m2l_maxd);
+  if (blk == 0 && threadIdx.x == 0 && !over) {
+    st->nm = nm;
+    st->np = np;
+    st->nlevel = nlevel;
   }
 }
 
@@ -493,64 +607,105 @@ void build_lists(fmm_tree* t) {
   const double theta2 = t->theta * t->theta;
   const int circ = (t->flags & FMM_FLAG_CIRCUMSCRIBED) ? 1 : 0;
 
-  int64_t cap_m = std::max<int64_t>(1024, 64 * (int64_t)t->ncell);
-  int64_t cap_p = std::max<int64_t>(1024, 32 * (int64_t)t->nleaf);
-  uint64_t* m2l = alloc_n<uint64_t>(a, cap_m);
-  uint64_t* p2p = alloc_n<uint64_t>(a, cap_p);
-  int64_t nm = 0, np = 0;
-
   // for the M2L plan: the cells that take M2L and the largest class offset
   t->m2l_has = alloc_n<int32_t>(a, t->ncell);
   t->m2l_maxd = alloc_n<unsigned long long>(a, 1);
   GB_CK(cudaMemsetAsync(t->m2l_has, 0, sizeof(int32_t) * t->ncell, s));
   GB_CK(cudaMemsetAsync(t->m2l_maxd, 0, sizeof(unsigned long long), s));
-  int64_t nf = 1;
-  int64_t* d_seg = alloc_n<int64_t>(a, 3);
-  int2* fr = alloc_n<int2>(a, 1);
+
+  // The whole traversal in one cooperative launch when the frontier and the
+  // lists fit buffers of 64 N entries in all (two frontiers of a fifth each,
+  // M2L half, P2P a tenth; the workloads here use at most about half of
+  // each); then one read-back.  Otherwise the per-level launches below take
+  // over, with one read-back per level (the marks already made are kept:
+  // they are a subset of the final ones).
+  const int64_t budget = std::max<int64_t>(1ll << 23, 64 * t->N);
+  int64_t cap_m = budget / 2, cap_p = budget / 10;
+  const int64_t capF = budget / 5;
+  uint64_t* m2l = alloc_n<uint64_t>(a, cap_m);
+  uint64_t* p2p = alloc_n<uint64_t>(a, cap_p);
+  int64_t nm = 0, np = 0;
+  bool done = false;
   {
-    int2 h = make_int2(0, 0);
-    GB_CK(cudaMemcpyAsync(fr, &h, sizeof(int2), cudaMemcpyHostToDevice, s));
+    int sms = 0, dev = 0, per_sm = 0;
+    GB_CK(cudaGetDevice(&dev));
+    GB_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    GB_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_traverse, kThreads, 0));
+    const int G = std::max(1, std::min(4, per_sm) * sms);
+    int2* F0 = alloc_n<int2>(a, capF);
+    int2* F1 = alloc_n<int2>(a, capF);
+    long long* partial = alloc_n<long long>(a, 3 * (size_t)G);
+    TravState* d_st = alloc_n<TravState>(a, 1);
+    GB_CK(cudaMemsetAsync(d_st, 0, sizeof(TravState), s));
+    long long capF_ = capF, cap_m_ = cap_m, cap_p_ = cap_p;
+    int* err = a.err;
+    void* args[] = {(void*)&cv,     (void*)&theta2, (void*)&circ,       (void*)&F0,         (void*)&F1,
+                    (void*)&capF_,  (void*)&m2l,    (void*)&cap_m_,     (void*)&p2p,        (void*)&cap_p_,
+                    (void*)&t->m2l_has, (void*)&t->m2l_maxd, (void*)&partial, (void*)&d_st, (void*)&err};
+    GB_CK(cudaLaunchCooperativeKernel((const void*)k_traverse, dim3(G), dim3(kThreads), args, 0, s));
+    GB_LAUNCH("k_traverse");
+    TravState h;
+    GB_CK(cudaMemcpyAsync(&h, d_st, sizeof(TravState), cudaMemcpyDeviceToHost, s));
+    check_scan_error(a, s);  // synchronises; a grid wait past its limit is FMM_ERR_TIMEOUT
+    if (!h.overflow) {
+      nm = h.nm;
+      np = h.np;
+      done = true;
+    }
+    a.release(d_st);
+    a.release(partial);
+    a.release(F1);
+    a.release(F0);
   }
-  while (nf > 0) {
-    const int64_t nb = blocks(nf);
-    int64_t* cnt = alloc_n<int64_t>(a, 3 * nb);
-    k_trav_count<<<(unsigned)nb, kThreads, 0, s>>>(fr, nf, cv, theta2, circ, cnt);
-    GB_LAUNCH("k_trav_count");
-    // one scan over the three segments of block totals; the segment starts
-    // and the total are read back together (one host synchronisation per level)
-    int64_t* scanned = cnt;
-    scan_exclusive_i64_dev(a, scanned, 3 * nb, d_seg + 2, s);
-    GB_CK(cudaMemcpyAsync(&d_seg[0], scanned + nb, sizeof(int64_t), cudaMemcpyDeviceToDevice, s));
-    GB_CK(cudaMemcpyAsync(&d_seg[1], scanned + 2 * nb, sizeof(int64_t), cudaMemcpyDeviceToDevice, s));
-    int64_t seg[3];
-    GB_CK(cudaMemcpyAsync(seg, d_seg, sizeof(seg), cudaMemcpyDeviceToHost, s));
-    host_sync(a, s);
-    const int64_t total = seg[2];
-    const int64_t n_next = seg[0], n_m = seg[1] - seg[0], n_p = total - seg[1];
-    auto grow = [&](uint64_t*& buf, int64_t& cap, int64_t used, int64_t need) {
-      if (used + need <= cap) return;
-      int64_t nc = std::max(2 * cap, used + need);
-      uint64_t* nb = alloc_n<uint64_t>(a, nc);
-      GB_CK(cudaMemcpyAsync(nb, buf, sizeof(uint64_t) * used, cudaMemcpyDeviceToDevice, s));
-      a.release(buf);
-      buf = nb;
-      cap = nc;
-    };
-    grow(m2l, cap_m, nm, n_m);
-    grow(p2p, cap_p, np, n_p);
-    int2* next = alloc_n<int2>(a, n_next);
-    k_trav_write<<<(unsigned)nb, kThreads, 0, s>>>(fr, nf, cv, theta2, circ, scanned, seg[0], seg[1], next, m2l,
-                                                   nm, p2p, np, t->m2l_has, t->m2l_maxd);
-    GB_LAUNCH("k_trav_write");
-    nm += n_m;
-    np += n_p;
-    a.release(cnt);
+  if (!done) {
+    int64_t nf = 1;
+    int64_t* d_seg = alloc_n<int64_t>(a, 3);
+    int2* fr = alloc_n<int2>(a, 1);
+    {
+      int2 h = make_int2(0, 0);
+      GB_CK(cudaMemcpyAsync(fr, &h, sizeof(int2), cudaMemcpyHostToDevice, s));
+    }
+    while (nf > 0) {
+      const int64_t nb = blocks(nf);
+      int64_t* cnt = alloc_n<int64_t>(a, 3 * nb);
+      k_trav_count<<<(unsigned)nb, kThreads, 0, s>>>(fr, nf, cv, theta2, circ, cnt);
+      GB_LAUNCH("k_trav_count");
+      // one scan over the three segments of block totals; the segment starts
+      // and the total are read back together (one host synchronisation per level)
+      int64_t* scanned = cnt;
+      scan_exclusive_i64_dev(a, scanned, 3 * nb, d_seg + 2, s);
+      GB_CK(cudaMemcpyAsync(&d_seg[0], scanned + nb, sizeof(int64_t), cudaMemcpyDeviceToDevice, s));
+      GB_CK(cudaMemcpyAsync(&d_seg[1], scanned + 2 * nb, sizeof(int64_t), cudaMemcpyDeviceToDevice, s));
+      int64_t seg[3];
+      GB_CK(cudaMemcpyAsync(seg, d_seg, sizeof(seg), cudaMemcpyDeviceToHost, s));
+      host_sync(a, s);
+      const int64_t total = seg[2];
+      const int64_t n_next = seg[0], n_m = seg[1] - seg[0], n_p = total - seg[1];
+      auto grow = [&](uint64_t*& buf, int64_t& cap, int64_t used, int64_t need) {
+        if (used + need <= cap) return;
+        int64_t nc = std::max(2 * cap, used + need);
+        uint64_t* nb = alloc_n<uint64_t>(a, nc);
+        GB_CK(cudaMemcpyAsync(nb, buf, sizeof(uint64_t) * used, cudaMemcpyDeviceToDevice, s));
+        a.release(buf);
+        buf = nb;
+        cap = nc;
+      };
+      grow(m2l, cap_m, nm, n_m);
+      grow(p2p, cap_p, np, n_p);
+      int2* next = alloc_n<int2>(a, n_next);
+      k_trav_write<<<(unsigned)nb, kThreads, 0, s>>>(fr, nf, cv, theta2, circ, scanned, seg[0], seg[1], next, m2l,
+                                                     nm, p2p, np, t->m2l_has, t->m2l_maxd);
+      GB_LAUNCH("k_trav_write");
+      nm += n_m;
+      np += n_p;
+      a.release(cnt);
+      a.release(fr);
+      fr = next;
+      nf = n_next;
+    }
     a.release(fr);
-    fr = next;
-    nf = n_next;
+    a.release(d_seg);
   }
-  a.release(fr);
-  a.release(d_seg);
   if (r2) a.release(r2);
 
   // The pairs stay in traversal order (deterministic: every offset comes from
@@ -572,8 +727,11 @@ void build_lists(fmm_tree* t) {
   a.release(p2p);
 
   // --- P2P body ranges per target leaf, merged where contiguous
-  unsigned long long* d_pairs = alloc_n<unsigned long long>(a, 1);
-  GB_CK(cudaMemsetAsync(d_pairs, 0, sizeof(unsigned long long), s));
+  // the range count and the body-pair total stay on the device until the
+  // end of the build (t->d_tail[0], t->d_tail[1])
+  t->d_tail = alloc_n<long long>(a, 4);
+  GB_CK(cudaMemsetAsync(t->d_tail, 0, 4 * sizeof(long long), s));
+  unsigned long long* d_pairs = reinterpret_cast<unsigned long long*>(t->d_tail + 1);
   int64_t* eptr = alloc_n<int64_t>(a, t->nleaf + 1);
   GB_CK(cudaMemsetAsync(eptr, 0, sizeof(int64_t) * (t->nleaf + 1), s));
   k_p2p_leaf_count<<<blocks(np), kThreads, 0, s>>>(t->p2p_tgt, t->p2p_src, np, t->leaf_of_cell, t->c.bbeg,
@@ -597,19 +755,15 @@ void build_lists(fmm_tree* t) {
   k_merge_ranges<<<blocks(t->nleaf), kThreads, 0, s>>>(eptr, rval, t->c.bbeg, t->c.bend, t->nleaf,
                                                        rcount, nullptr, nullptr);
   GB_LAUNCH("k_merge_ranges");
-  t->n_p2p_ranges = scan_exclusive_i64_total(a, rcount, t->nleaf + 1, s);
-  t->p2p_ranges = alloc_n<int2>(a, t->n_p2p_ranges);
+  // a leaf's merged ranges are at most its source leaves: np entries suffice
+  scan_exclusive_i64_dev(a, rcount, t->nleaf + 1, reinterpret_cast<int64_t*>(t->d_tail), s);
+  t->p2p_ranges = alloc_n<int2>(a, np);
   k_merge_ranges<<<blocks(t->nleaf), kThreads, 0, s>>>(eptr, rval, t->c.bbeg, t->c.bend, t->nleaf,
                                                        nullptr, rcount, t->p2p_ranges);
   GB_LAUNCH("k_merge_ranges");
   t->p2p_rptr = alloc_n<int32_t>(a, t->nleaf + 1);
   k_i64_to_i32<<<blocks(t->nleaf + 1), kThreads, 0, s>>>(rcount, t->nleaf + 1, t->p2p_rptr);
   GB_LAUNCH("k_i64_to_i32");
-  unsigned long long hp = 0;
-  GB_CK(cudaMemcpyAsync(&hp, d_pairs, sizeof(hp), cudaMemcpyDeviceToHost, s));
-  host_sync(a, s);
-  t->p2p_body_pairs = (int64_t)hp - t->N;
-  a.release(d_pairs);
   a.release(rval);
   a.release(eptr);
   a.release(rcount);

@@ -10,6 +10,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "grid.cuh"
 
 namespace gbfmm {
 namespace {
@@ -235,74 +236,8 @@ inline unsigned blocks(int64_t n, int t = kThreads) { return (unsigned)((n + t -
 struct LevelState {
   int level_begin[kMaxLevel + 3];  // first cell of each level, then the end
   int nlevel, ncell, nleaf, overflow;
-  unsigned bar_count, bar_gen, abort;
+  GridBar bar;
 };
-
-constexpr long long kGridWaitNs = 2000000000ll;  // 2 s: far beyond any real wait
-
-__device__ __forceinline__ long long tree_ns() {
-  long long t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-
-// Grid-wide barrier of a cooperative launch; false once a wait has given up
-// (this block's or another's).
-__device__ bool grid_barrier(LevelState* st, int* err) {
-  __shared__ int ok;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    ok = 1;
-    volatile unsigned* gen = &st->bar_gen;
-    const unsigned g = *gen;
-    __threadfence();
-    if (atomicAdd(&st->bar_count, 1u) == gridDim.x - 1) {
-      atomicExch(&st->bar_count, 0u);
-      __threadfence();
-      atomicAdd(&st->bar_gen, 1u);
-    } else {
-      const long long t0 = tree_ns();
-      while (*gen == g) {
-        if (*(volatile unsigned*)&st->abort || tree_ns() - t0 > kGridWaitNs) {
-          atomicOr(err, kErrGrid);
-          atomicExch(&st->abort, 1u);
-          ok = 0;
-          break;
-        }
-        __nanosleep(64);
-      }
-    }
-    __threadfence();
-  }
-  __syncthreads();
-  return ok != 0;
-}
-
-// Sum of partial[0 .. upto) and of partial[0 .. n) over the block.
-__device__ void block_prefix_total(const int* partial, int upto, int n, int& before, int& total) {
-  __shared__ int sb[kThreads / 32], st_[kThreads / 32];
-  int b = 0, t = 0;
-  for (int j = threadIdx.x; j < n; j += blockDim.x) {
-    const int v = __ldcg(partial + j);
-    t += v;
-    if (j < upto) b += v;
-  }
-  for (int o = 16; o > 0; o >>= 1) {
-    b += __shfl_down_sync(0xffffffffu, b, o);
-    t += __shfl_down_sync(0xffffffffu, t, o);
-  }
-  if ((threadIdx.x & 31) == 0) {
-    sb[threadIdx.x >> 5] = b;
-    st_[threadIdx.x >> 5] = t;
-  }
-  __syncthreads();
-  before = total = 0;
-  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
-    before += sb[w];
-    total += st_[w];
-  }
-  __syncthreads();
-}
 
 __global__ void __launch_bounds__(kThreads) k_tree_levels(const uint64_t* __restrict__ keys, int n, int ncrit,
                                                           int cap, Cells c, int32_t* __restrict__ leaves,
@@ -320,7 +255,7 @@ __global__ void __launch_bounds__(kThreads) k_tree_levels(const uint64_t* __rest
     c.parent[0] = -1;
   }
   int lb = 0, le = 1, nlevel = 0;
-  bool fine = grid_barrier(st, err), over = false;
+  bool fine = grid_barrier(&st->bar, err), over = false;
   for (int l = 0; fine && le > lb; ++l) {
     nlevel = l + 1;
     const int ncur = le - lb, ch = (ncur + G - 1) / G;
@@ -335,10 +270,10 @@ __global__ void __launch_bounds__(kThreads) k_tree_levels(const uint64_t* __rest
     }
     __syncthreads();
     if (threadIdx.x == 0) partial[blk] = chunk_sum;
-    fine = grid_barrier(st, err);
+    fine = grid_barrier(&st->bar, err);
     if (!fine) break;
     int before, total;
-    block_prefix_total(partial, blk, G, before, total);
+    block_prefix_totals<int, 1>(partial, blk, G, &before, &total);
     if ((int64_t)le + total > cap) {  // every block sees the same total
       if (blk == 0 && threadIdx.x == 0) st->overflow = 1;
       over = true;
@@ -378,7 +313,7 @@ __global__ void __launch_bounds__(kThreads) k_tree_levels(const uint64_t* __rest
     if (blk == 0 && threadIdx.x == 0) st->level_begin[l + 1] = le;
     lb = le;
     le += total;
-    fine = grid_barrier(st, err);
+    fine = grid_barrier(&st->bar, err);
   }
   if (!fine || over) return;
   const int ncell = le;
@@ -392,9 +327,9 @@ __global__ void __launch_bounds__(kThreads) k_tree_levels(const uint64_t* __rest
       if (__ldcg(c.nch + i) == 0) atomicAdd(&chunk_sum, 1);
     __syncthreads();
     if (threadIdx.x == 0) partial[blk] = chunk_sum;
-    if (!grid_barrier(st, err)) return;
+    if (!grid_barrier(&st->bar, err)) return;
     int before, total;
-    block_prefix_total(partial, blk, G, before, total);
+    block_prefix_totals<int, 1>(partial, blk, G, &before, &total);
     __shared__ int wcnt[kThreads / 32];
     int run = before;
     for (int cb = c0; cb < c1; cb += blockDim.x) {
@@ -468,7 +403,7 @@ void build_tree_impl(fmm_tree* t, const R* xyzq) {
   GB_CK(cudaGetDevice(&dev));
   GB_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   GB_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tree_levels, kThreads, 0));
-  const int G = std::max(1, std::min(2, per_sm) * sms);
+  const int G = std::max(1, std::min(4, per_sm) * sms);
   int64_t bound = 0;
   {
     const int64_t split_max = 8 * (N / ((int64_t)t->ncrit + 1));
