@@ -111,6 +111,7 @@ void create_tree(fmm_tree* t, const R* xyzq) {
   t->p2p_nbig_host = nitem[1];
   t->n_p2p_ranges = tail[0];
   t->p2p_body_pairs = tail[1] - t->N;
+  if (tail[2]) fail(FMM_ERR_RANGE, "translation operator overflows the working precision");
   t->lim = Lim{t->N, t->ncell, t->nleaf, t->Kp, t->ntile, t->nentry, t->nclass, t->n_p2p_ranges, t->check_rec};
   t->build_syncs = a.nsync;
   if (timing)

@@ -917,7 +917,7 @@ void build_m2l_quad_chunks(fmm_tree* t, int per, const std::vector<int32_t>& qpt
   GB_CK(cudaMemcpyAsync(t->m2l_chunks, ch.data(), sizeof(int4) * ch.size(), cudaMemcpyHostToDevice, s));
   GB_CK(cudaMemcpyAsync(t->tile_cptr, cptr.data(), sizeof(int32_t) * cptr.size(), cudaMemcpyHostToDevice, s));
   t->m2l_part = alloc_n<float>(a, (size_t)t->nchunk * kQuad * kTile * t->Kp);
-  host_sync(a, s);
+  // no wait: a copy from pageable memory has read its source when it returns
 }
 
 void build_m2l_chunks(fmm_tree* t, int per) {
@@ -956,7 +956,7 @@ void build_m2l_chunks(fmm_tree* t, int per) {
   GB_CK(cudaMemcpyAsync(t->m2l_chunks, ch.data(), sizeof(int4) * ch.size(), cudaMemcpyHostToDevice, s));
   GB_CK(cudaMemcpyAsync(t->tile_cptr, cptr.data(), sizeof(int32_t) * cptr.size(), cudaMemcpyHostToDevice, s));
   t->m2l_part = alloc_n<float>(a, (size_t)t->nchunk * kTile * t->Kp);
-  host_sync(a, s);
+  // no wait: a copy from pageable memory has read its source when it returns
 }
 
 }  // namespace gbfmm

@@ -55,34 +55,42 @@ __device__ __forceinline__ cd hget(const cd* X, int n, int m) {
   return v;
 }
 
-// Regular harmonics, degrees < P, into the m >= 0 triangle (one thread).
+// Regular harmonics, degrees < P, into the m >= 0 triangle.  Thread m < P
+// of the block forms column m: the diagonal term by m steps of
+// Ups_m^m = -(x + i y) Ups_{m-1}^{m-1} / (2m), then the recurrence up the
+// column.  Every entry takes the same operations as in a serial sweep of the
+// triangle, so the values do not depend on the block size.
 __device__ void regular_tri(double x, double y, double z, int P, cd* U) {
+  const int m = threadIdx.x;
+  if (m >= P) return;
   const double r2 = x * x + y * y + z * z;
-  U[0] = {1.0, 0.0};
-  for (int m = 1; m < P; ++m) U[tri(m, m)] = cscale(cmul(U[tri(m - 1, m - 1)], {-x, -y}), 1.0 / (2.0 * m));
-  for (int m = 0; m < P; ++m)
-    for (int n = m + 1; n < P; ++n) {
-      cd a = U[tri(n - 1, m)];
-      cd b = n - 2 >= m ? U[tri(n - 2, m)] : cd{0.0, 0.0};
-      double f = 1.0 / ((double)(n + m) * (double)(n - m));
-      U[tri(n, m)] = {((2.0 * n - 1.0) * z * a.re - r2 * b.re) * f, ((2.0 * n - 1.0) * z * a.im - r2 * b.im) * f};
-    }
+  cd d{1.0, 0.0};
+  for (int k = 1; k <= m; ++k) d = cscale(cmul(d, {-x, -y}), 1.0 / (2.0 * k));
+  U[tri(m, m)] = d;
+  for (int n = m + 1; n < P; ++n) {
+    cd a = U[tri(n - 1, m)];
+    cd b = n - 2 >= m ? U[tri(n - 2, m)] : cd{0.0, 0.0};
+    double f = 1.0 / ((double)(n + m) * (double)(n - m));
+    U[tri(n, m)] = {((2.0 * n - 1.0) * z * a.re - r2 * b.re) * f, ((2.0 * n - 1.0) * z * a.im - r2 * b.im) * f};
+  }
 }
 
-// Irregular harmonics, degrees < P, into the m >= 0 triangle (one thread).
+// Irregular harmonics, degrees < P, into the m >= 0 triangle; thread m < P
+// forms column m (as regular_tri).
 __device__ void irregular_tri(double x, double y, double z, int P, cd* T) {
+  const int m = threadIdx.x;
+  if (m >= P) return;
   const double r2 = x * x + y * y + z * z;
   const double ir2 = 1.0 / r2;
-  T[0] = {1.0 / sqrt(r2), 0.0};
-  for (int m = 1; m < P; ++m)
-    T[tri(m, m)] = cscale(cmul(T[tri(m - 1, m - 1)], {x, y}), -(2.0 * m - 1.0) * ir2);
-  for (int m = 0; m < P; ++m)
-    for (int n = m + 1; n < P; ++n) {
-      cd a = T[tri(n - 1, m)];
-      cd b = n - 2 >= m ? T[tri(n - 2, m)] : cd{0.0, 0.0};
-      double c1 = (2.0 * n - 1.0) * z, c2 = (double)(n + m - 1) * (double)(n - m - 1);
-      T[tri(n, m)] = {(c1 * a.re - c2 * b.re) * ir2, (c1 * a.im - c2 * b.im) * ir2};
-    }
+  cd d{1.0 / sqrt(r2), 0.0};
+  for (int k = 1; k <= m; ++k) d = cscale(cmul(d, {x, y}), -(2.0 * k - 1.0) * ir2);
+  T[tri(m, m)] = d;
+  for (int n = m + 1; n < P; ++n) {
+    cd a = T[tri(n - 1, m)];
+    cd b = n - 2 >= m ? T[tri(n - 2, m)] : cd{0.0, 0.0};
+    double c1 = (2.0 * n - 1.0) * z, c2 = (double)(n + m - 1) * (double)(n - m - 1);
+    T[tri(n, m)] = {(c1 * a.re - c2 * b.re) * ir2, (c1 * a.im - c2 * b.im) * ir2};
+  }
 }
 
 __device__ __forceinline__ int ridx(int n, int m, int part) { return n * n + (m == 0 ? 0 : 2 * m - 1 + part); }
@@ -138,10 +146,8 @@ __global__ void k_build_ops(int kind, int p, int Kp, const double* __restrict__ 
   const double* g = geom + 5 * (int64_t)op;
   const int P = kind == kM2L ? 2 * p - 1 : p;
   const int eA = (int)g[3], eB = (int)g[4];
-  if (threadIdx.x == 0) {
-    if (kind == kM2L) irregular_tri(g[0], g[1], g[2], P, X);
-    else regular_tri(g[0], g[1], g[2], P, X);
-  }
+  if (kind == kM2L) irregular_tri(g[0], g[1], g[2], P, X);
+  else regular_tri(g[0], g[1], g[2], P, X);
   // the M2L scale factors, one exponent per (output degree, input degree)
   for (int w = threadIdx.x; w < kMaxP * kMaxP; w += blockDim.x) {
     const int a = w / kMaxP, c = w % kMaxP;
@@ -226,7 +232,7 @@ constexpr int kPatternBits = 14;  // (reach + 1)^6 = 15625 patterns < 2^14
 constexpr int kTargetKeyExtra = 5 + 3 + kPatternBits;  // level, octant, pattern
 
 __global__ void k_target_keys(const int32_t* __restrict__ has, CellView c, int ncell, int cbits,
-                              uint64_t* __restrict__ key, unsigned long long* __restrict__ count) {
+                              uint64_t* __restrict__ key) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= ncell) return;
   if (has[i]) {
@@ -241,7 +247,6 @@ __global__ void k_target_keys(const int32_t* __restrict__ has, CellView c, int n
     const uint64_t oct = ((co[0] & 1) << 2) | ((co[1] & 1) << 1) | (co[2] & 1);
     key[i] = ((uint64_t)l << (3 + kPatternBits + cbits)) | (oct << (kPatternBits + cbits)) | (pat << cbits) |
              (uint32_t)i;
-    atomicAdd(count, 1ull);
   } else {
     key[i] = ~0ull;
   }
@@ -472,7 +477,7 @@ __global__ void k_m2l_geom(const int32_t* __restrict__ desc, int n, double* __re
 
 // Single-precision M2L operators (the same entries as k_build_ops).  FP64
 // runs at a small fraction of the FP32 rate on this GPU, so only the
-// harmonics are computed in double (one thread, as above); each is then held
+// harmonics are computed in double (a thread per column, as above); each is then held
 // as a pair of floats (hi + lo, about 48 bits), and the per-entry work -- the
 // sum of the +m and -m parts, the power-of-two scale and the TF32 split --
 // runs in FP32 on those pairs.  A pair's low part that underflows only drops
@@ -506,7 +511,7 @@ __global__ void k_build_m2l_f32(int p, int Kp, const double* __restrict__ geom, 
   const int ntri = P * (P + 1) / 2;
   float4* Xf = reinterpret_cast<float4*>(X + ntri);  // (re hi, re lo, im hi, im lo)
   const int eA = (int)g[3], eB = (int)g[4];
-  if (threadIdx.x == 0) irregular_tri(g[0], g[1], g[2], P, X);
+  irregular_tri(g[0], g[1], g[2], P, X);
   float* o = ops + (int64_t)op * Kp * Kp;
   float* olo = ops_lo ? ops_lo + (int64_t)op * Kp * Kp : nullptr;
   for (int i = threadIdx.x; i < Kp * Kp; i += blockDim.x) {
@@ -603,21 +608,14 @@ void build_m2l_plan(fmm_tree* t) {
   // found the largest class offset)
   int32_t* has = t->m2l_has;
   uint64_t* tkey = alloc_n<uint64_t>(a, t->ncell);
-  unsigned long long* d_cnt = alloc_n<unsigned long long>(a, 2);  // target count, largest offset
-  GB_CK(cudaMemsetAsync(d_cnt, 0, sizeof(unsigned long long), s));
   // 2^cbits > ncell, so a real key never equals the all-ones key of a non-target
   int cbits = 1;
   while ((1ll << cbits) <= (int64_t)t->ncell) ++cbits;
-  k_target_keys<<<blocks(t->ncell), kThreads, 0, s>>>(has, cv, t->ncell, cbits, tkey, d_cnt);
+  k_target_keys<<<blocks(t->ncell), kThreads, 0, s>>>(has, cv, t->ncell, cbits, tkey);
   GB_LAUNCH("k_target_keys");
-  // the largest offset of the translation classes is read back together
-  // with the target count (one host synchronisation)
-  GB_CK(cudaMemcpyAsync(d_cnt + 1, t->m2l_maxd, sizeof(unsigned long long), cudaMemcpyDeviceToDevice, s));
   radix_sort_keys(a, tkey, t->ncell, cbits + kTargetKeyExtra, s);
-  unsigned long long hc[2] = {0, 0};
-  GB_CK(cudaMemcpyAsync(hc, d_cnt, sizeof(hc), cudaMemcpyDeviceToHost, s));
-  host_sync(a, s);
-  const unsigned long long ntgt = hc[0], maxd = hc[1];
+  // the target count and the largest class offset came with the traversal
+  const unsigned long long ntgt = (unsigned long long)t->m2l_ntgt, maxd = t->m2l_maxd_host;
   t->ntile = (int)((ntgt + kTile - 1) / kTile);
   const int64_t padded = (int64_t)t->ntile * kTile;
   t->tile_tgt = alloc_n<int32_t>(a, padded);
@@ -625,7 +623,6 @@ void build_m2l_plan(fmm_tree* t) {
   k_target_rank<<<blocks(padded), kThreads, 0, s>>>(tkey, (int64_t)ntgt, padded, cbits, t->tile_tgt, rank_of);
   GB_LAUNCH("k_target_rank");
   a.release(tkey);
-  a.release(d_cnt);
 
   // --- translation classes
   int b = 1;
@@ -745,8 +742,9 @@ void build_operators(fmm_tree* t) {
   const bool f64 = t->precision == 64;
   const size_t rs = f64 ? sizeof(double) : sizeof(float);
   const int p = t->p, Kp = t->Kp;
-  int* bad = alloc_n<int>(a, 1);
-  GB_CK(cudaMemsetAsync(bad, 0, sizeof(int), s));
+  // an operator entry out of the float range sets this flag; it is read back
+  // at the end of the build (FMM_ERR_RANGE)
+  int* bad = reinterpret_cast<int*>(t->d_tail + 2);
   // M2M / L2L: 8 octants, child offset (c_C - c_P)/R_P = (bx, by, bz) - 1/2
   double hgeom[8 * 5];
   for (int o = 0; o < 8; ++o) {
@@ -790,12 +788,7 @@ void build_operators(fmm_tree* t) {
     GB_LAUNCH("k_build_ops m2l");
     a.release(geom);
   }
-  int hbad = 0;
-  GB_CK(cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, s));
-  host_sync(a, s);
-  a.release(bad);
   a.release(g8);
-  if (hbad) fail(FMM_ERR_RANGE, "translation operator overflows the working precision");
 }
 
 }  // namespace gbfmm

@@ -241,12 +241,34 @@ __global__ void __launch_bounds__(kThreads) k_trav_write(const int2* __restrict_
 // it).  If a level would overflow a buffer every block stops before writing
 // it and st->overflow is set.
 struct TravState {
-  long long nm, np;
+  long long nm, np, ntgt;  // M2L and P2P entries, cells that take M2L
   int nlevel, overflow;
   GridBar bar;
 };
 
-__global__ void __launch_bounds__(kThreads) k_traverse(CellView c, double theta2, int circ, int2* F0, int2* F1,
+// Cells flagged in has[0 .. n) into *count (read through L2: the flags were
+// set by other blocks of the launch, or by an earlier launch).
+__device__ __forceinline__ void count_flags(const int32_t* has, int64_t n, long long* count) {
+  __shared__ long long wsum[kThreads / 32];
+  long long c = 0;
+  for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < n; i += (int64_t)gridDim.x * kThreads)
+    c += __ldcg(has + i) != 0;
+  for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(0xffffffffu, c, o);
+  if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = c;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < kThreads / 32; ++w) c += wsum[w];
+    if (c) atomicAdd(reinterpret_cast<unsigned long long*>(count), (unsigned long long)c);
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) k_count_flags(const int32_t* __restrict__ has, int64_t n,
+                                                          TravState* __restrict__ st) {
+  count_flags(has, n, &st->ntgt);
+}
+
+__global__ void __launch_bounds__(kThreads) k_traverse(CellView c, int ncell, double theta2, int circ, int2* F0,
+                                                       int2* F1,
                                                        long long capF, uint64_t* __restrict__ m2l, long long cap_m,
                                                        uint64_t* __restrict__ p2p, long long cap_p,
                                                        int32_t* __restrict__ m2l_has,
@@ -320,6 +342,7 @@ __global__ void __launch_bounds__(kThreads) k_traverse(CellView c, double theta2
   }
   if (!fine) return;
   block_maxd(dm, m2l_maxd);
+  if (!over) count_flags(m2l_has, ncell, &st->ntgt);
   if (blk == 0 && threadIdx.x == 0 && !over) {
     st->nm = nm;
     st->np = np;
@@ -365,17 +388,17 @@ __global__ void k_p2p_leaf_scatter(const int32_t* __restrict__ tgt, const int32_
   val[ptr[l] + atomicAdd(&cursor[l], 1)] = src[i];
 }
 
-// One block per leaf: its sources ordered by body begin, from `in` to `out`.
-// Up to kSegSort entries a bitonic sort in shared memory; longer lists (none
-// at the workloads here) rank each entry by counting the smaller ones.
+// Each leaf's sources ordered by body begin, from `in` to `out` (the keys
+// are distinct: the sources' body ranges are disjoint).  A block of four
+// warps takes four leaves: a list of at most 32 entries is sorted by its
+// warp (bitonic, in registers); longer ones by the whole block, one after
+// another: up to kSegSort entries a bitonic sort in shared memory, beyond
+// that (none at the workloads here) each entry ranked by counting the
+// smaller ones.
 constexpr int kSegSort = 1024;
-__global__ void k_p2p_leaf_sort(const int64_t* __restrict__ ptr, int nleaf, const int32_t* __restrict__ bbeg,
-                                const int32_t* __restrict__ in, int32_t* __restrict__ out) {
-  __shared__ int sk[kSegSort], sv[kSegSort];
-  const int l = blockIdx.x;
-  if (l >= nleaf) return;
-  const int64_t b = ptr[l];
-  const int L = (int)(ptr[l + 1] - b);
+constexpr int kLeavesPerSortBlock = 4;
+__device__ void sort_long_list(int64_t b, int L, const int32_t* __restrict__ bbeg, const int32_t* __restrict__ in,
+                               int32_t* __restrict__ out, int* sk, int* sv) {
   if (L <= kSegSort) {
     int n2 = 1;
     while (n2 < L) n2 <<= 1;
@@ -411,6 +434,42 @@ __global__ void k_p2p_leaf_sort(const int64_t* __restrict__ ptr, int nleaf, cons
       for (int j = 0; j < L; ++j) r += bbeg[in[b + j]] < key;
       out[b + r] = v;
     }
+  }
+}
+__global__ void k_p2p_leaf_sort(const int64_t* __restrict__ ptr, int nleaf, const int32_t* __restrict__ bbeg,
+                                const int32_t* __restrict__ in, int32_t* __restrict__ out) {
+  __shared__ int sk[kSegSort], sv[kSegSort];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  {
+    const int l = blockIdx.x * kLeavesPerSortBlock + w;
+    if (l < nleaf) {
+      const int64_t b = ptr[l];
+      const int L = (int)(ptr[l + 1] - b);
+      if (L <= 32) {
+        int v = lane < L ? in[b + lane] : -1;
+        int k = lane < L ? bbeg[v] : INT_MAX;
+        for (int sz = 2; sz <= 32; sz <<= 1)
+          for (int j = sz >> 1; j > 0; j >>= 1) {
+            const int pk = __shfl_xor_sync(0xffffffffu, k, j), pv = __shfl_xor_sync(0xffffffffu, v, j);
+            const bool up = (lane & sz) == 0, lower = (lane & j) == 0;
+            // the lower lane of an ascending pair keeps the smaller key
+            if ((lower == up) ? (pk < k) : (pk > k)) {
+              k = pk;
+              v = pv;
+            }
+          }
+        if (lane < L) out[b + lane] = v;
+      }
+    }
+  }
+  for (int q = 0; q < kLeavesPerSortBlock; ++q) {
+    const int l = blockIdx.x * kLeavesPerSortBlock + q;
+    if (l >= nleaf) return;
+    const int64_t b = ptr[l];
+    const int L = (int)(ptr[l + 1] - b);
+    if (L <= 32) continue;
+    sort_long_list(b, L, bbeg, in, out, sk, sv);
+    __syncthreads();
   }
 }
 
@@ -639,17 +698,20 @@ void build_lists(fmm_tree* t) {
     GB_CK(cudaMemsetAsync(d_st, 0, sizeof(TravState), s));
     long long capF_ = capF, cap_m_ = cap_m, cap_p_ = cap_p;
     int* err = a.err;
-    void* args[] = {(void*)&cv,     (void*)&theta2, (void*)&circ,       (void*)&F0,         (void*)&F1,
+    const int ncell = t->ncell;
+    void* args[] = {(void*)&cv,     (void*)&ncell,  (void*)&theta2, (void*)&circ, (void*)&F0, (void*)&F1,
                     (void*)&capF_,  (void*)&m2l,    (void*)&cap_m_,     (void*)&p2p,        (void*)&cap_p_,
                     (void*)&t->m2l_has, (void*)&t->m2l_maxd, (void*)&partial, (void*)&d_st, (void*)&err};
     GB_CK(cudaLaunchCooperativeKernel((const void*)k_traverse, dim3(G), dim3(kThreads), args, 0, s));
     GB_LAUNCH("k_traverse");
     TravState h;
     GB_CK(cudaMemcpyAsync(&h, d_st, sizeof(TravState), cudaMemcpyDeviceToHost, s));
+    GB_CK(cudaMemcpyAsync(&t->m2l_maxd_host, t->m2l_maxd, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
     check_scan_error(a, s);  // synchronises; a grid wait past its limit is FMM_ERR_TIMEOUT
     if (!h.overflow) {
       nm = h.nm;
       np = h.np;
+      t->m2l_ntgt = h.ntgt;
       done = true;
     }
     a.release(d_st);
@@ -705,6 +767,17 @@ void build_lists(fmm_tree* t) {
     }
     a.release(fr);
     a.release(d_seg);
+    // the M2L cells and the largest class offset
+    TravState* d_st = alloc_n<TravState>(a, 1);
+    GB_CK(cudaMemsetAsync(d_st, 0, sizeof(TravState), s));
+    k_count_flags<<<blocks(t->ncell), kThreads, 0, s>>>(t->m2l_has, t->ncell, d_st);
+    GB_LAUNCH("k_count_flags");
+    TravState h;
+    GB_CK(cudaMemcpyAsync(&h, d_st, sizeof(TravState), cudaMemcpyDeviceToHost, s));
+    GB_CK(cudaMemcpyAsync(&t->m2l_maxd_host, t->m2l_maxd, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+    host_sync(a, s);
+    t->m2l_ntgt = h.ntgt;
+    a.release(d_st);
   }
   if (r2) a.release(r2);
 
@@ -745,7 +818,8 @@ void build_lists(fmm_tree* t) {
                                                      rtmp);
   GB_LAUNCH("k_p2p_leaf_scatter");
   int32_t* rval = alloc_n<int32_t>(a, np);
-  k_p2p_leaf_sort<<<(unsigned)t->nleaf, 128, 0, s>>>(eptr, (int)t->nleaf, t->c.bbeg, rtmp, rval);
+  k_p2p_leaf_sort<<<(unsigned)((t->nleaf + kLeavesPerSortBlock - 1) / kLeavesPerSortBlock), 32 * kLeavesPerSortBlock, 0,
+                    s>>>(eptr, (int)t->nleaf, t->c.bbeg, rtmp, rval);
   GB_LAUNCH("k_p2p_leaf_sort");
   a.release(cursor);
   a.release(rtmp);
