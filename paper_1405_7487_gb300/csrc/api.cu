@@ -81,8 +81,10 @@ void create_tree(fmm_tree* t, const R* xyzq) {
   }
   a.release(t->m2l_has);
   a.release(t->m2l_maxd);
+  a.release(t->m2l_off);
   t->m2l_has = nullptr;
   t->m2l_maxd = nullptr;
+  t->m2l_off = nullptr;
   mark(FMM_PH_BUILD_PLAN, 1);
   mark(FMM_PH_BUILD_OPS, 0);
   if (!fitted) build_operators(t);

@@ -139,6 +139,7 @@ struct fmm_tree {
   int64_t n_p2p = 0, n_m2l = 0, n_p2p_ranges = 0, p2p_body_pairs = 0;
   int32_t *p2p_tgt = nullptr, *p2p_src = nullptr, *m2l_tgt = nullptr, *m2l_src = nullptr;
   int32_t* m2l_has = nullptr;             // per cell: takes M2L (traversal, for the plan)
+  uint32_t* m2l_off = nullptr;            // per M2L entry: packed class offset (traversal, for the plan)
   long long* d_tail = nullptr;            // read back at the end of the build: P2P ranges, body pairs + N,
                                           // operator range flag
   int64_t m2l_ntgt = 0;                   // cells that take M2L (from the traversal)

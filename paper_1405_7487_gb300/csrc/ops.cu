@@ -391,6 +391,21 @@ __global__ void k_class_mark(const int32_t* __restrict__ tgt, const int32_t* __r
   if (mark[k] == 0) mark[k] = 1;
 }
 
+// The same from the traversal's packed class offsets (no gathers of the
+// cells); used while every offset stays within +-127.
+__global__ void k_class_mark_packed(const uint32_t* __restrict__ off, int64_t n, int b, int64_t maxd,
+                                    int64_t* __restrict__ mark, uint32_t* __restrict__ pkey) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const uint32_t w = off[i];
+  const int64_t dl = (int64_t)(w >> 24) - 32;
+  const int64_t d0 = (int8_t)(w >> 16), d1 = (int8_t)(w >> 8), d2 = (int8_t)w;
+  const uint64_t k = ((uint64_t)(dl + kMaxLevel) << (3 * b)) | ((uint64_t)(d0 + maxd) << (2 * b)) |
+                     ((uint64_t)(d1 + maxd) << b) | (uint64_t)(d2 + maxd);
+  pkey[i] = (uint32_t)k;
+  if (mark[k] == 0) mark[k] = 1;
+}
+
 // After the scan: class id of every pair.
 __global__ void k_class_lookup(const int32_t* __restrict__ tgt, const int32_t* __restrict__ src, int64_t n,
                                CellView c, int b, int64_t maxd, const int64_t* __restrict__ excl,
@@ -639,9 +654,14 @@ void build_m2l_plan(fmm_tree* t) {
     key_excl = alloc_n<int64_t>(a, nkey);
     pkey = alloc_n<uint32_t>(a, nm);
     GB_CK(cudaMemsetAsync(key_excl, 0, sizeof(int64_t) * nkey, s));
-    k_class_mark<<<blocks(nm), kThreads, 0, s>>>(t->m2l_tgt, t->m2l_src, nm, cv, b, (int64_t)maxd, key_excl,
-                                                 pkey);
-    GB_LAUNCH("k_class_mark");
+    if (t->m2l_off && maxd <= 127) {
+      k_class_mark_packed<<<blocks(nm), kThreads, 0, s>>>(t->m2l_off, nm, b, (int64_t)maxd, key_excl, pkey);
+      GB_LAUNCH("k_class_mark_packed");
+    } else {
+      k_class_mark<<<blocks(nm), kThreads, 0, s>>>(t->m2l_tgt, t->m2l_src, nm, cv, b, (int64_t)maxd, key_excl,
+                                                   pkey);
+      GB_LAUNCH("k_class_mark");
+    }
     const int64_t ncls = scan_exclusive_i64_total(a, key_excl, nkey, s);
     t->nclass = (int)ncls;
     t->class_desc = alloc_n<int32_t>(a, 4 * ncls);

@@ -133,20 +133,39 @@ __global__ void __launch_bounds__(kThreads) k_trav_count(const int2* __restrict_
     for (int j = 0; j < 3; ++j) cnt[(int64_t)j * gridDim.x + blockIdx.x] = tot[j];
 }
 
+// A directed pair list as two arrays (target, source).
+struct PairList {
+  int32_t *tgt, *src;
+  __device__ __forceinline__ void put(int64_t i, int t, int sr) const {
+    tgt[i] = t;
+    src[i] = sr;
+  }
+};
+
 __device__ __forceinline__ uint64_t pair_key(int tgt, int src) {
   return ((uint64_t)(uint32_t)tgt << 32) | (uint32_t)src;
 }
 
 // M2L pair {A, B}: marks both cells as M2L cells (read first: a cell has
 // many M2L pairs) and returns the largest |offset| component in units of the
-// smaller cell's half side (the class offsets of the plan).
-__device__ __forceinline__ unsigned mark_m2l(const CellView& c, int A, int B, int32_t* __restrict__ m2l_has) {
+// smaller cell's half side (the class offsets of the plan).  w[0] and w[1]
+// receive the packed class offsets of the entries (target B, source A) and
+// (target A, source B): bits 24..29 the level difference (source minus
+// target) + 32, then the offset (source centre minus target centre) per
+// axis as an 8-bit two's complement value, valid while every offset of the
+// tree stays within +-127.
+__device__ __forceinline__ unsigned mark_m2l(const CellView& c, int A, int B, int32_t* __restrict__ m2l_has,
+                                             uint32_t w[2]) {
   const int la = c.level[A], lb = c.level[B], sh = kMaxLevel - (la > lb ? la : lb);
   const int co[2][3] = {{c.ix[A], c.iy[A], c.iz[A]}, {c.ix[B], c.iy[B], c.iz[B]}};
   unsigned dm = 0;
+  w[0] = (uint32_t)(la - lb + 32) << 24;
+  w[1] = (uint32_t)(lb - la + 32) << 24;
   for (int d = 0; d < 3; ++d) {
     const int64_t o = (((2ll * co[0][d] + 1) << (kMaxLevel - la)) - ((2ll * co[1][d] + 1) << (kMaxLevel - lb))) >> sh;
     dm = max(dm, (unsigned)(o < 0 ? -o : o));
+    w[0] |= ((uint32_t)o & 0xffu) << (16 - 8 * d);
+    w[1] |= ((uint32_t)(-o) & 0xffu) << (16 - 8 * d);
   }
   if (!m2l_has[A]) m2l_has[A] = 1;
   if (!m2l_has[B]) m2l_has[B] = 1;
@@ -155,10 +174,11 @@ __device__ __forceinline__ unsigned mark_m2l(const CellView& c, int A, int B, in
 
 // The outputs of pair {A, B} (decision k) at next[o..], m2l[om..], p2p[op..].
 __device__ __forceinline__ void write_pair(const CellView& c, int A, int B, int k, int64_t o, int64_t om, int64_t op,
-                                           int2* __restrict__ next, uint64_t* __restrict__ m2l,
-                                           uint64_t* __restrict__ p2p) {
+                                           int2* __restrict__ next, PairList m2l, PairList p2p,
+                                           uint32_t* __restrict__ m2l_off,
+                                           const uint32_t w[2]) {
   switch (k) {
-    case 0: p2p[op] = pair_key(A, A); break;
+    case 0: p2p.put(op, A, A); break;
     case 1: {
       const int a0 = c.cbeg[A], na = c.nch[A];
       for (int x = 0; x < na; ++x)
@@ -166,12 +186,14 @@ __device__ __forceinline__ void write_pair(const CellView& c, int A, int B, int 
       break;
     }
     case 2:
-      m2l[om] = pair_key(B, A);
-      m2l[om + 1] = pair_key(A, B);
+      m2l.put(om, B, A);
+      m2l.put(om + 1, A, B);
+      m2l_off[om] = w[0];
+      m2l_off[om + 1] = w[1];
       break;
     case 3:
-      p2p[op] = pair_key(B, A);
-      p2p[op + 1] = pair_key(A, B);
+      p2p.put(op, B, A);
+      p2p.put(op + 1, A, B);
       break;
     case 4: {
       const int a0 = c.cbeg[A], na = c.nch[A];
@@ -209,26 +231,28 @@ __device__ __forceinline__ void block_maxd(unsigned dm, unsigned long long* __re
 __global__ void __launch_bounds__(kThreads) k_trav_write(const int2* __restrict__ fr, int64_t n, CellView c,
                                                          double theta2, int circ, const int64_t* __restrict__ off,
                                                          int64_t base_m, int64_t base_p, int2* __restrict__ next,
-                                                         uint64_t* __restrict__ m2l, int64_t m2l_at,
-                                                         uint64_t* __restrict__ p2p, int64_t p2p_at,
+                                                         PairList m2l, int64_t m2l_at, PairList p2p,
+                                                         int64_t p2p_at,
                                                          int32_t* __restrict__ m2l_has,
-                                                         unsigned long long* __restrict__ m2l_maxd) {
+                                                         unsigned long long* __restrict__ m2l_maxd,
+                                                         uint32_t* __restrict__ m2l_off) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   int A = 0, B = 0, k = -1, v[3] = {0, 0, 0}, tot[3];
   unsigned dm = 0;
+  uint32_t w[2] = {0, 0};
   if (i < n) {
     A = fr[i].x;
     B = fr[i].y;
     k = decide(c, A, B, theta2, circ);
     pair_counts(c, A, B, k, v[0], v[1], v[2]);
-    if (k == 2) dm = mark_m2l(c, A, B, m2l_has);
+    if (k == 2) dm = mark_m2l(c, A, B, m2l_has, w);
   }
   block_scan3(v, tot);
   block_maxd(dm, m2l_maxd);
   if (i >= n) return;
   const int nb = gridDim.x;
   write_pair(c, A, B, k, off[blockIdx.x] + v[0], m2l_at + off[nb + blockIdx.x] - base_m + v[1],
-             p2p_at + off[2 * nb + blockIdx.x] - base_p + v[2], next, m2l, p2p);
+             p2p_at + off[2 * nb + blockIdx.x] - base_p + v[2], next, m2l, p2p, m2l_off, w);
 }
 
 // The whole traversal in one cooperative launch, while the frontier and the
@@ -269,10 +293,11 @@ __global__ void __launch_bounds__(kThreads) k_count_flags(const int32_t* __restr
 
 __global__ void __launch_bounds__(kThreads) k_traverse(CellView c, int ncell, double theta2, int circ, int2* F0,
                                                        int2* F1,
-                                                       long long capF, uint64_t* __restrict__ m2l, long long cap_m,
-                                                       uint64_t* __restrict__ p2p, long long cap_p,
+                                                       long long capF, PairList m2l, long long cap_m, PairList p2p,
+                                                       long long cap_p,
                                                        int32_t* __restrict__ m2l_has,
                                                        unsigned long long* __restrict__ m2l_maxd,
+                                                       uint32_t* __restrict__ m2l_off,
                                                        long long* __restrict__ partial, TravState* st,
                                                        int* __restrict__ err) {
   const int G = gridDim.x, blk = blockIdx.x;
@@ -320,16 +345,17 @@ __global__ void __launch_bounds__(kThreads) k_traverse(CellView c, int ncell, do
     for (long long base = f0; base < f1; base += kThreads) {
       const long long i = base + threadIdx.x;
       int A = 0, B = 0, k = -1, v[3] = {0, 0, 0}, tot[3];
+      uint32_t w[2] = {0, 0};
       if (i < f1) {
         const int2 pr = __ldcg(cur + i);
         A = pr.x;
         B = pr.y;
         k = decide(c, A, B, theta2, circ);
         pair_counts(c, A, B, k, v[0], v[1], v[2]);
-        if (k == 2) dm = max(dm, mark_m2l(c, A, B, m2l_has));
+        if (k == 2) dm = max(dm, mark_m2l(c, A, B, m2l_has, w));
       }
       block_scan3(v, tot);
-      if (i < f1) write_pair(c, A, B, k, run[0] + v[0], run[1] + v[1], run[2] + v[2], nxt, m2l, p2p);
+      if (i < f1) write_pair(c, A, B, k, run[0] + v[0], run[1] + v[1], run[2] + v[2], nxt, m2l, p2p, m2l_off, w);
       for (int j = 0; j < 3; ++j) run[j] += tot[j];
     }
     fine = grid_barrier(&st->bar, err);
@@ -390,13 +416,16 @@ __global__ void k_p2p_leaf_scatter(const int32_t* __restrict__ tgt, const int32_
 
 // Each leaf's sources ordered by body begin, from `in` to `out` (the keys
 // are distinct: the sources' body ranges are disjoint).  A block of four
-// warps takes four leaves: a list of at most 32 entries is sorted by its
-// warp (bitonic, in registers); longer ones by the whole block, one after
-// another: up to kSegSort entries a bitonic sort in shared memory, beyond
-// that (none at the workloads here) each entry ranked by counting the
-// smaller ones.
+// warps takes four leaves.  A list of at most kWarpRank entries is sorted by
+// its warp: the keys go to the warp's part of shared memory and each entry's
+// place is the number of smaller keys (every lane reads the same key at a
+// time, so the reads are broadcasts).  Longer lists are sorted by the whole
+// block, one after another: up to kSegSort entries a bitonic sort in shared
+// memory, beyond that (none at the workloads here) each entry ranked by
+// counting the smaller ones in global memory.
 constexpr int kSegSort = 1024;
 constexpr int kLeavesPerSortBlock = 4;
+constexpr int kWarpRank = kSegSort / kLeavesPerSortBlock;
 __device__ void sort_long_list(int64_t b, int L, const int32_t* __restrict__ bbeg, const int32_t* __restrict__ in,
                                int32_t* __restrict__ out, int* sk, int* sv) {
   if (L <= kSegSort) {
@@ -445,29 +474,31 @@ __global__ void k_p2p_leaf_sort(const int64_t* __restrict__ ptr, int nleaf, cons
     if (l < nleaf) {
       const int64_t b = ptr[l];
       const int L = (int)(ptr[l + 1] - b);
-      if (L <= 32) {
-        int v = lane < L ? in[b + lane] : -1;
-        int k = lane < L ? bbeg[v] : INT_MAX;
-        for (int sz = 2; sz <= 32; sz <<= 1)
-          for (int j = sz >> 1; j > 0; j >>= 1) {
-            const int pk = __shfl_xor_sync(0xffffffffu, k, j), pv = __shfl_xor_sync(0xffffffffu, v, j);
-            const bool up = (lane & sz) == 0, lower = (lane & j) == 0;
-            // the lower lane of an ascending pair keeps the smaller key
-            if ((lower == up) ? (pk < k) : (pk > k)) {
-              k = pk;
-              v = pv;
-            }
-          }
-        if (lane < L) out[b + lane] = v;
+      if (L <= kWarpRank) {
+        int* k = sk + w * kWarpRank;
+        int* v = sv + w * kWarpRank;
+        for (int i = lane; i < L; i += 32) {
+          const int x = in[b + i];
+          v[i] = x;
+          k[i] = bbeg[x];
+        }
+        __syncwarp();
+        for (int i = lane; i < L; i += 32) {
+          const int key = k[i];
+          int r = 0;
+          for (int j = 0; j < L; ++j) r += k[j] < key;
+          out[b + r] = v[i];
+        }
       }
     }
   }
+  __syncthreads();
   for (int q = 0; q < kLeavesPerSortBlock; ++q) {
     const int l = blockIdx.x * kLeavesPerSortBlock + q;
     if (l >= nleaf) return;
     const int64_t b = ptr[l];
     const int L = (int)(ptr[l + 1] - b);
-    if (L <= 32) continue;
+    if (L <= kWarpRank) continue;
     sort_long_list(b, L, bbeg, in, out, sk, sv);
     __syncthreads();
   }
@@ -681,8 +712,10 @@ void build_lists(fmm_tree* t) {
   const int64_t budget = std::max<int64_t>(1ll << 23, 64 * t->N);
   int64_t cap_m = budget / 2, cap_p = budget / 10;
   const int64_t capF = budget / 5;
-  uint64_t* m2l = alloc_n<uint64_t>(a, cap_m);
-  uint64_t* p2p = alloc_n<uint64_t>(a, cap_p);
+  // the lists are written in place and kept at this capacity (no copy)
+  PairList m2l{alloc_n<int32_t>(a, cap_m), alloc_n<int32_t>(a, cap_m)};
+  PairList p2p{alloc_n<int32_t>(a, cap_p), alloc_n<int32_t>(a, cap_p)};
+  t->m2l_off = alloc_n<uint32_t>(a, cap_m);  // packed class offsets, kept for the plan
   int64_t nm = 0, np = 0;
   bool done = false;
   {
@@ -701,7 +734,8 @@ void build_lists(fmm_tree* t) {
     const int ncell = t->ncell;
     void* args[] = {(void*)&cv,     (void*)&ncell,  (void*)&theta2, (void*)&circ, (void*)&F0, (void*)&F1,
                     (void*)&capF_,  (void*)&m2l,    (void*)&cap_m_,     (void*)&p2p,        (void*)&cap_p_,
-                    (void*)&t->m2l_has, (void*)&t->m2l_maxd, (void*)&partial, (void*)&d_st, (void*)&err};
+                    (void*)&t->m2l_has, (void*)&t->m2l_maxd, (void*)&t->m2l_off, (void*)&partial, (void*)&d_st,
+                    (void*)&err};
     GB_CK(cudaLaunchCooperativeKernel((const void*)k_traverse, dim3(G), dim3(kThreads), args, 0, s));
     GB_LAUNCH("k_traverse");
     TravState h;
@@ -743,20 +777,31 @@ void build_lists(fmm_tree* t) {
       host_sync(a, s);
       const int64_t total = seg[2];
       const int64_t n_next = seg[0], n_m = seg[1] - seg[0], n_p = total - seg[1];
-      auto grow = [&](uint64_t*& buf, int64_t& cap, int64_t used, int64_t need) {
-        if (used + need <= cap) return;
-        int64_t nc = std::max(2 * cap, used + need);
-        uint64_t* nb = alloc_n<uint64_t>(a, nc);
-        GB_CK(cudaMemcpyAsync(nb, buf, sizeof(uint64_t) * used, cudaMemcpyDeviceToDevice, s));
+      auto grow1 = [&](int32_t*& buf, int64_t nc, int64_t used) {
+        int32_t* nb = alloc_n<int32_t>(a, nc);
+        GB_CK(cudaMemcpyAsync(nb, buf, sizeof(int32_t) * used, cudaMemcpyDeviceToDevice, s));
         a.release(buf);
         buf = nb;
+      };
+      auto grow = [&](PairList& l, int64_t& cap, int64_t used, int64_t need) {
+        if (used + need <= cap) return;
+        const int64_t nc = std::max(2 * cap, used + need);
+        grow1(l.tgt, nc, used);
+        grow1(l.src, nc, used);
         cap = nc;
       };
+      if (nm + n_m > cap_m) {
+        const int64_t nc = std::max(2 * cap_m, nm + n_m);
+        uint32_t* no = alloc_n<uint32_t>(a, nc);
+        GB_CK(cudaMemcpyAsync(no, t->m2l_off, sizeof(uint32_t) * nm, cudaMemcpyDeviceToDevice, s));
+        a.release(t->m2l_off);
+        t->m2l_off = no;
+      }
       grow(m2l, cap_m, nm, n_m);
       grow(p2p, cap_p, np, n_p);
       int2* next = alloc_n<int2>(a, n_next);
       k_trav_write<<<(unsigned)nb, kThreads, 0, s>>>(fr, nf, cv, theta2, circ, scanned, seg[0], seg[1], next, m2l,
-                                                     nm, p2p, np, t->m2l_has, t->m2l_maxd);
+                                                     nm, p2p, np, t->m2l_has, t->m2l_maxd, t->m2l_off);
       GB_LAUNCH("k_trav_write");
       nm += n_m;
       np += n_p;
@@ -786,18 +831,10 @@ void build_lists(fmm_tree* t) {
   // source).  Nothing on the evaluation path depends on that order.
   t->n_m2l = nm;
   t->n_p2p = np;
-  t->m2l_tgt = alloc_n<int32_t>(a, nm);
-  t->m2l_src = alloc_n<int32_t>(a, nm);
-  t->p2p_tgt = alloc_n<int32_t>(a, np);
-  t->p2p_src = alloc_n<int32_t>(a, np);
-  if (nm) {
-    k_unpack_pairs<<<blocks(nm), kThreads, 0, s>>>(m2l, nm, t->m2l_tgt, t->m2l_src);
-    GB_LAUNCH("k_unpack_pairs");
-  }
-  k_unpack_pairs<<<blocks(np), kThreads, 0, s>>>(p2p, np, t->p2p_tgt, t->p2p_src);
-  GB_LAUNCH("k_unpack_pairs");
-  a.release(m2l);
-  a.release(p2p);
+  t->m2l_tgt = m2l.tgt;
+  t->m2l_src = m2l.src;
+  t->p2p_tgt = p2p.tgt;
+  t->p2p_src = p2p.src;
 
   // --- P2P body ranges per target leaf, merged where contiguous
   // the range count and the body-pair total stay on the device until the
