@@ -114,6 +114,7 @@ void create_tree(fmm_tree* t, const R* xyzq) {
   t->n_p2p_ranges = tail[0];
   t->p2p_body_pairs = tail[1] - t->N;
   if (tail[2]) fail(FMM_ERR_RANGE, "translation operator overflows the working precision");
+  if (t->m2l_engine == 1) finish_m2l_chunks(t, tail[3]);
   t->lim = Lim{t->N, t->ncell, t->nleaf, t->Kp, t->ntile, t->nentry, t->nclass, t->n_p2p_ranges, t->check_rec};
   t->build_syncs = a.nsync;
   if (timing)

@@ -141,7 +141,8 @@ struct fmm_tree {
   int32_t* m2l_has = nullptr;             // per cell: takes M2L (traversal, for the plan)
   uint32_t* m2l_off = nullptr;            // per M2L entry: packed class offset (traversal, for the plan)
   long long* d_tail = nullptr;            // read back at the end of the build: P2P ranges, body pairs + N,
-                                          // operator range flag
+                                          // operator range flag, M2L chunks
+  int64_t m2l_part_per_chunk = 0;         // floats of one chunk's partial sums
   int64_t m2l_ntgt = 0;                   // cells that take M2L (from the traversal)
   unsigned long long m2l_maxd_host = 0;   // largest M2L class offset component (from the traversal)
   unsigned long long* m2l_maxd = nullptr;  // largest M2L class offset component (traversal, for the plan)

@@ -69,5 +69,8 @@ template <class R> void launch_l2l_fit(fmm_tree* t, int level, cudaStream_t s);
 template <class R> void launch_m2l_fit(fmm_tree* t, cudaStream_t s);
 void launch_split_tf32(fmm_tree* t, cudaStream_t s);
 void build_m2l_chunks(fmm_tree* t, int per);
+// after the build's last read-back (chunk count in t->d_tail[3]): the count
+// and the partial buffer
+void finish_m2l_chunks(fmm_tree* t, int64_t nchunk);
 
 }  // namespace gbfmm

@@ -811,53 +811,136 @@ __global__ void k_quad_fill(const int32_t* __restrict__ tile_eptr, int ntile, co
   qcls[j] = c;  // the entries of one quad entry all write the same class
 }
 
-__global__ void k_quad_ptr(const int64_t* __restrict__ qid, int nquad, int nclass, int64_t total,
-                           int32_t* __restrict__ qptr) {
+// Chunk list of a plan from the entry pointers of its groups (quads, or
+// tiles for the single-tile engine): chunks of at most `per` entries, chunk
+// j of every group before chunk j + 1 of any (the operators of a class are
+// then still in L2 when the next group asks for them), and each group's
+// first partial slot.  One block; the count goes to *nchunk.
+__global__ void __launch_bounds__(1024) k_chunk_list(const int32_t* __restrict__ gptr, int ngroup, int per,
+                                                     int4* __restrict__ chunks, int32_t* __restrict__ cptr,
+                                                     long long* __restrict__ nchunk) {
+  __shared__ int wsum[32];
+  __shared__ int s_base, s_max;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  auto nc_of = [&](int g) { return (gptr[g + 1] - gptr[g] + per - 1) / per; };
+  // block-wide exclusive prefix of v (thread order); the tile's total in *tot
+  auto scan = [&](int v, int* tot) {
+    int inc = v;
+    for (int o = 1; o < 32; o <<= 1) {
+      const int u = __shfl_up_sync(0xffffffffu, inc, o);
+      if (lane >= o) inc += u;
+    }
+    if (lane == 31) wsum[w] = inc;
+    __syncthreads();
+    int before = 0, all = 0;
+    for (int q = 0; q < nw; ++q) {
+      before += q < w ? wsum[q] : 0;
+      all += wsum[q];
+    }
+    __syncthreads();
+    *tot = all;
+    return before + inc - v;
+  };
+  if (threadIdx.x == 0) {
+    s_base = 0;
+    s_max = 0;
+  }
+  __syncthreads();
+  // each group's first slot, and the most chunks of one group
+  int run = 0;
+  for (int g0 = 0; g0 < ngroup; g0 += blockDim.x) {
+    const int g = g0 + threadIdx.x;
+    const int nc = g < ngroup ? nc_of(g) : 0;
+    if (nc) atomicMax(&s_max, nc);
+    int tot;
+    const int ex = scan(nc, &tot);
+    if (g < ngroup) cptr[g] = run + ex;
+    run += tot;
+  }
+  if (threadIdx.x == 0) cptr[ngroup] = run;
+  __syncthreads();
+  const int maxc = s_max;
+  int at = 0;
+  for (int j = 0; j < maxc; ++j)
+    for (int g0 = 0; g0 < ngroup; g0 += blockDim.x) {
+      const int g = g0 + threadIdx.x;
+      const bool has = g < ngroup && nc_of(g) > j;
+      int tot;
+      const int ex = scan(has ? 1 : 0, &tot);
+      if (has) {
+        const int e = gptr[g] + j * per;
+        chunks[at + ex] = make_int4(g, e, min(e + per, gptr[g + 1]), cptr[g] + j);
+      }
+      at += tot;
+    }
+  if (threadIdx.x == 0) *nchunk = at;
+}
+
+// The quad ptr from the scanned (quad, class) table; its total is on the device.
+__global__ void k_quad_ptr_dev(const int64_t* __restrict__ qid, int nquad, int nclass,
+                               const int64_t* __restrict__ total, int32_t* __restrict__ qptr) {
   const int q = blockIdx.x * blockDim.x + threadIdx.x;
   if (q > nquad) return;
-  qptr[q] = (int32_t)(q < nquad ? qid[(int64_t)q * nclass] : total);
+  qptr[q] = (int32_t)(q < nquad ? qid[(int64_t)q * nclass] : *total);
 }
 
 }  // namespace
 
-void build_m2l_quad_chunks(fmm_tree* t, int per, const std::vector<int32_t>& qptr);
+// The chunk list on the device from group entry pointers; the chunk count is
+// read back with the build's last read-back (t->d_tail[3]), and the partial
+// buffer is allocated then (finish_m2l_chunks).
+void build_chunk_list(fmm_tree* t, const int32_t* d_gptr, int ngroup, int per, int64_t max_chunks) {
+  Arena& a = t->arena;
+  cudaStream_t s = t->stream;
+  t->m2l_chunks = alloc_n<int4>(a, std::max<int64_t>(1, max_chunks));
+  t->tile_cptr = alloc_n<int32_t>(a, ngroup + 1);
+  k_chunk_list<<<1, 1024, 0, s>>>(d_gptr, ngroup, per, t->m2l_chunks, t->tile_cptr, t->d_tail + 3);
+  GB_LAUNCH("k_chunk_list");
+}
 
 // Quad plan: the class lists of tiles 4q .. 4q + 3 (each sorted by class)
 // merged into quad entries, cut into chunks of at most `per` quad entries.
-void build_m2l_quads(fmm_tree* t, int per, const std::vector<int32_t>& eptr) {
+void build_m2l_quads(fmm_tree* t, int per) {
   Arena& a = t->arena;
   cudaStream_t s = t->stream;
   const int nquad = (t->ntile + kQuad - 1) / kQuad;
   const int64_t nk = (int64_t)nquad * t->nclass;
-  std::vector<int32_t> qptr(nquad + 1, 0);
+  t->m2l_quad = true;
+  t->m2l_part_per_chunk = (int64_t)kQuad * kTile * t->Kp;
+  // a quad entry holds at least one tile entry, and a quad's chunks are at
+  // most its entries / per + 1
+  const int64_t max_chunks = (t->nentry + per - 1) / per + nquad;
+  int32_t* d_qptr = alloc_n<int32_t>(a, nquad + 1);
   if (nk > 0 && nk <= (1ll << 22) && t->nentry > 0) {
     int64_t* qid = alloc_n<int64_t>(a, nk);
+    int64_t* nq = alloc_n<int64_t>(a, 1);
     GB_CK(cudaMemsetAsync(qid, 0, sizeof(int64_t) * nk, s));
     const unsigned nb = (unsigned)((t->nentry + 255) / 256);
     k_quad_mark<<<nb, 256, 0, s>>>(t->tile_eptr, t->ntile, t->entry_class, (int)t->nentry, t->nclass, qid);
     GB_LAUNCH("k_quad_mark");
-    const int64_t nq = scan_exclusive_i64_total(a, qid, nk, s);
-    t->quad_class = alloc_n<int32_t>(a, nq);
-    t->quad_entry = alloc_n<int4>(a, nq);
-    GB_CK(cudaMemsetAsync(t->quad_entry, 0xff, sizeof(int4) * nq, s));
+    scan_exclusive_i64_dev(a, qid, nk, nq, s);
+    t->quad_class = alloc_n<int32_t>(a, t->nentry);
+    t->quad_entry = alloc_n<int4>(a, t->nentry);
+    GB_CK(cudaMemsetAsync(t->quad_entry, 0xff, sizeof(int4) * t->nentry, s));  // -1: no entry of that tile
     k_quad_fill<<<nb, 256, 0, s>>>(t->tile_eptr, t->ntile, t->entry_class, (int)t->nentry, t->nclass, qid,
                                    t->quad_class, reinterpret_cast<int32_t*>(t->quad_entry));
     GB_LAUNCH("k_quad_fill");
-    int32_t* d_qptr = alloc_n<int32_t>(a, nquad + 1);
-    k_quad_ptr<<<(unsigned)((nquad + 256) / 256), 256, 0, s>>>(qid, nquad, t->nclass, nq, d_qptr);
-    GB_LAUNCH("k_quad_ptr");
-    GB_CK(cudaMemcpyAsync(qptr.data(), d_qptr, sizeof(int32_t) * (nquad + 1), cudaMemcpyDeviceToHost, s));
-    host_sync(a, s);
+    k_quad_ptr_dev<<<(unsigned)((nquad + 256) / 256), 256, 0, s>>>(qid, nquad, t->nclass, nq, d_qptr);
+    GB_LAUNCH("k_quad_ptr_dev");
+    build_chunk_list(t, d_qptr, nquad, per, max_chunks);
+    a.release(nq);
     a.release(qid);
     a.release(d_qptr);
-    build_m2l_quad_chunks(t, per, qptr);
     return;
   }
-  std::vector<int32_t> ecls(t->nentry);
+  // a class table too large for the device marks: the quad entries merged on
+  // the host from the tiles' class lists
+  std::vector<int32_t> eptr(t->ntile + 1), ecls(t->nentry);
+  GB_CK(cudaMemcpyAsync(eptr.data(), t->tile_eptr, sizeof(int32_t) * (t->ntile + 1), cudaMemcpyDeviceToHost, s));
   if (t->nentry)
     GB_CK(cudaMemcpyAsync(ecls.data(), t->entry_class, sizeof(int32_t) * t->nentry, cudaMemcpyDeviceToHost, s));
   host_sync(a, s);
-  std::vector<int32_t> qcls;
+  std::vector<int32_t> qcls, qptr(nquad + 1, 0);
   std::vector<int4> qent;
   qcls.reserve(t->nentry);
   qent.reserve(t->nentry);
@@ -886,46 +969,14 @@ void build_m2l_quads(fmm_tree* t, int per, const std::vector<int32_t>& eptr) {
     GB_CK(cudaMemcpyAsync(t->quad_class, qcls.data(), sizeof(int32_t) * qcls.size(), cudaMemcpyHostToDevice, s));
     GB_CK(cudaMemcpyAsync(t->quad_entry, qent.data(), sizeof(int4) * qent.size(), cudaMemcpyHostToDevice, s));
   }
-  build_m2l_quad_chunks(t, per, qptr);
-}
-
-// Chunks of at most `per` quad entries of every quad, launched chunk j of
-// every quad before chunk j + 1 of any (operators shared in L2), and the
-// partial buffer.
-void build_m2l_quad_chunks(fmm_tree* t, int per, const std::vector<int32_t>& qptr) {
-  Arena& a = t->arena;
-  cudaStream_t s = t->stream;
-  const int nquad = (int)qptr.size() - 1;
-  std::vector<int32_t> cptr(nquad + 1, 0);
-  int maxc = 0;
-  for (int q = 0; q < nquad; ++q) {
-    const int nc = (qptr[q + 1] - qptr[q] + per - 1) / per;
-    cptr[q + 1] = cptr[q] + nc;
-    maxc = std::max(maxc, nc);
-  }
-  std::vector<int4> ch;
-  ch.reserve(cptr[nquad]);
-  for (int j = 0; j < maxc; ++j)
-    for (int q = 0; q < nquad; ++q) {
-      const int e = qptr[q] + j * per;
-      if (e < qptr[q + 1]) ch.push_back(make_int4(q, e, std::min(e + per, qptr[q + 1]), cptr[q] + j));
-    }
-  t->m2l_quad = true;
-  t->nchunk = (int)ch.size();
-  t->m2l_chunks = alloc_n<int4>(a, ch.size());
-  t->tile_cptr = alloc_n<int32_t>(a, cptr.size());
-  GB_CK(cudaMemcpyAsync(t->m2l_chunks, ch.data(), sizeof(int4) * ch.size(), cudaMemcpyHostToDevice, s));
-  GB_CK(cudaMemcpyAsync(t->tile_cptr, cptr.data(), sizeof(int32_t) * cptr.size(), cudaMemcpyHostToDevice, s));
-  t->m2l_part = alloc_n<float>(a, (size_t)t->nchunk * kQuad * kTile * t->Kp);
-  // no wait: a copy from pageable memory has read its source when it returns
+  // a copy from pageable memory has read its source when it returns
+  GB_CK(cudaMemcpyAsync(d_qptr, qptr.data(), sizeof(int32_t) * (nquad + 1), cudaMemcpyHostToDevice, s));
+  build_chunk_list(t, d_qptr, nquad, per, max_chunks);
+  a.release(d_qptr);
 }
 
 void build_m2l_chunks(fmm_tree* t, int per) {
   Arena& a = t->arena;
-  cudaStream_t s = t->stream;
-  std::vector<int32_t> eptr(t->ntile + 1);
-  GB_CK(cudaMemcpyAsync(eptr.data(), t->tile_eptr, sizeof(int32_t) * (t->ntile + 1), cudaMemcpyDeviceToHost, s));
-  host_sync(a, s);
   t->M_lo = alloc_n<float>(a, 2 * (size_t)t->ncell * t->Kp);
   if (t->nclass > 0) {
     const int64_t rows = (int64_t)t->nclass * t->Kp;
@@ -933,30 +984,17 @@ void build_m2l_chunks(fmm_tree* t, int per) {
     make_ops_map(&t->m2l_ops_map[1], t->m2l_ops_lo, rows, t->Kp);
   }
   if (t->Kp <= kQuadMaxKp && !m2l_single_tile_forced()) {
-    build_m2l_quads(t, per, eptr);
+    build_m2l_quads(t, per);
     return;
   }
-  std::vector<int32_t> cptr(t->ntile + 1, 0);
-  int maxc = 0;
-  for (int tile = 0; tile < t->ntile; ++tile) {
-    const int nc = (eptr[tile + 1] - eptr[tile] + per - 1) / per;
-    cptr[tile + 1] = cptr[tile] + nc;
-    maxc = std::max(maxc, nc);
-  }
-  std::vector<int4> ch;
-  ch.reserve(cptr[t->ntile]);
-  for (int j = 0; j < maxc; ++j)
-    for (int tile = 0; tile < t->ntile; ++tile) {
-      const int e = eptr[tile] + j * per;
-      if (e < eptr[tile + 1]) ch.push_back(make_int4(tile, e, std::min(e + per, eptr[tile + 1]), cptr[tile] + j));
-    }
-  t->nchunk = (int)ch.size();
-  t->m2l_chunks = alloc_n<int4>(a, ch.size());
-  t->tile_cptr = alloc_n<int32_t>(a, cptr.size());
-  GB_CK(cudaMemcpyAsync(t->m2l_chunks, ch.data(), sizeof(int4) * ch.size(), cudaMemcpyHostToDevice, s));
-  GB_CK(cudaMemcpyAsync(t->tile_cptr, cptr.data(), sizeof(int32_t) * cptr.size(), cudaMemcpyHostToDevice, s));
-  t->m2l_part = alloc_n<float>(a, (size_t)t->nchunk * kTile * t->Kp);
-  // no wait: a copy from pageable memory has read its source when it returns
+  t->m2l_part_per_chunk = (int64_t)kTile * t->Kp;
+  build_chunk_list(t, t->tile_eptr, t->ntile, per, (t->nentry + per - 1) / per + t->ntile);
+}
+
+// After the build's last read-back: the chunk count and the partial buffer.
+void finish_m2l_chunks(fmm_tree* t, int64_t nchunk) {
+  t->nchunk = (int)nchunk;
+  t->m2l_part = alloc_n<float>(t->arena, (size_t)std::max<int64_t>(1, nchunk) * t->m2l_part_per_chunk);
 }
 
 }  // namespace gbfmm
