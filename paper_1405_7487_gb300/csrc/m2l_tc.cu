@@ -815,17 +815,25 @@ __global__ void k_quad_fill(const int32_t* __restrict__ tile_eptr, int ntile, co
 // tiles for the single-tile engine): chunks of at most `per` entries, chunk
 // j of every group before chunk j + 1 of any (the operators of a class are
 // then still in L2 when the next group asks for them), and each group's
-// first partial slot.  One block; the count goes to *nchunk.
-__global__ void __launch_bounds__(1024) k_chunk_list(const int32_t* __restrict__ gptr, int ngroup, int per,
-                                                     int4* __restrict__ chunks, int32_t* __restrict__ cptr,
-                                                     long long* __restrict__ nchunk) {
+// first partial slot.  k_chunk_rounds (one block): each group's chunk count
+// nc and first slot, and the first position of round j, the rounds holding
+// #{groups with nc > j} chunks each (nround >= the largest nc, counts in
+// hist[0 .. nround], zeroed).  k_chunk_place: thread g places its chunks,
+// its position within a round taken by an atomic counter; the order within
+// a round changes nothing but which block runs a chunk (each chunk writes
+// its own partial slot).
+__global__ void __launch_bounds__(1024) k_chunk_rounds(const int32_t* __restrict__ gptr, int ngroup, int per,
+                                                       int nround, int32_t* __restrict__ cptr,
+                                                       int* __restrict__ hist, int* __restrict__ round_at,
+                                                       long long* __restrict__ nchunk) {
   __shared__ int wsum[32];
-  __shared__ int s_base, s_max;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  auto nc_of = [&](int g) { return (gptr[g + 1] - gptr[g] + per - 1) / per; };
-  // block-wide exclusive prefix of v (thread order); the tile's total in *tot
-  auto scan = [&](int v, int* tot) {
-    int inc = v;
+  int run = 0;
+  for (int g0 = 0; g0 < ngroup; g0 += blockDim.x) {
+    const int g = g0 + threadIdx.x;
+    const int nc = g < ngroup ? (gptr[g + 1] - gptr[g] + per - 1) / per : 0;
+    if (nc) atomicAdd(&hist[min(nc, nround)], 1);
+    int inc = nc;
     for (int o = 1; o < 32; o <<= 1) {
       const int u = __shfl_up_sync(0xffffffffu, inc, o);
       if (lane >= o) inc += u;
@@ -838,42 +846,35 @@ __global__ void __launch_bounds__(1024) k_chunk_list(const int32_t* __restrict__
       all += wsum[q];
     }
     __syncthreads();
-    *tot = all;
-    return before + inc - v;
-  };
+    if (g < ngroup) cptr[g] = run + before + inc - nc;
+    run += all;
+  }
+  __syncthreads();
   if (threadIdx.x == 0) {
-    s_base = 0;
-    s_max = 0;
-  }
-  __syncthreads();
-  // each group's first slot, and the most chunks of one group
-  int run = 0;
-  for (int g0 = 0; g0 < ngroup; g0 += blockDim.x) {
-    const int g = g0 + threadIdx.x;
-    const int nc = g < ngroup ? nc_of(g) : 0;
-    if (nc) atomicMax(&s_max, nc);
-    int tot;
-    const int ex = scan(nc, &tot);
-    if (g < ngroup) cptr[g] = run + ex;
-    run += tot;
-  }
-  if (threadIdx.x == 0) cptr[ngroup] = run;
-  __syncthreads();
-  const int maxc = s_max;
-  int at = 0;
-  for (int j = 0; j < maxc; ++j)
-    for (int g0 = 0; g0 < ngroup; g0 += blockDim.x) {
-      const int g = g0 + threadIdx.x;
-      const bool has = g < ngroup && nc_of(g) > j;
-      int tot;
-      const int ex = scan(has ? 1 : 0, &tot);
-      if (has) {
-        const int e = gptr[g] + j * per;
-        chunks[at + ex] = make_int4(g, e, min(e + per, gptr[g + 1]), cptr[g] + j);
-      }
-      at += tot;
+    cptr[ngroup] = run;
+    *nchunk = run;
+    // groups with nc > j = sum of hist[c], c > j
+    int above = 0;
+    for (int c = 1; c <= nround; ++c) above += hist[c];
+    int at = 0;
+    for (int j = 0; j < nround; ++j) {
+      round_at[j] = at;
+      at += above;
+      above -= hist[j + 1];
     }
-  if (threadIdx.x == 0) *nchunk = at;
+  }
+}
+
+__global__ void k_chunk_place(const int32_t* __restrict__ gptr, int ngroup, int per, const int32_t* __restrict__ cptr,
+                              const int* __restrict__ round_at, int* __restrict__ round_fill,
+                              int4* __restrict__ chunks) {
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= ngroup) return;
+  const int nc = (gptr[g + 1] - gptr[g] + per - 1) / per;
+  for (int j = 0; j < nc; ++j) {
+    const int e = gptr[g] + j * per;
+    chunks[round_at[j] + atomicAdd(&round_fill[j], 1)] = make_int4(g, e, min(e + per, gptr[g + 1]), cptr[g] + j);
+  }
 }
 
 // The quad ptr from the scanned (quad, class) table; its total is on the device.
@@ -894,8 +895,19 @@ void build_chunk_list(fmm_tree* t, const int32_t* d_gptr, int ngroup, int per, i
   cudaStream_t s = t->stream;
   t->m2l_chunks = alloc_n<int4>(a, std::max<int64_t>(1, max_chunks));
   t->tile_cptr = alloc_n<int32_t>(a, ngroup + 1);
-  k_chunk_list<<<1, 1024, 0, s>>>(d_gptr, ngroup, per, t->m2l_chunks, t->tile_cptr, t->d_tail + 3);
-  GB_LAUNCH("k_chunk_list");
+  // a group holds at most nclass entries (one per class)
+  const int nround = (t->nclass + per - 1) / per + 1;
+  int* work = alloc_n<int>(a, 3 * (size_t)nround + 1);  // hist[0 .. nround], round_at, round_fill
+  GB_CK(cudaMemsetAsync(work, 0, sizeof(int) * (3 * (size_t)nround + 1), s));
+  int *hist = work, *round_at = work + nround + 1, *round_fill = round_at + nround;
+  k_chunk_rounds<<<1, 1024, 0, s>>>(d_gptr, ngroup, per, nround, t->tile_cptr, hist, round_at, t->d_tail + 3);
+  GB_LAUNCH("k_chunk_rounds");
+  if (ngroup > 0) {
+    k_chunk_place<<<(unsigned)((ngroup + 255) / 256), 256, 0, s>>>(d_gptr, ngroup, per, t->tile_cptr, round_at,
+                                                                  round_fill, t->m2l_chunks);
+    GB_LAUNCH("k_chunk_place");
+  }
+  a.release(work);
 }
 
 // Quad plan: the class lists of tiles 4q .. 4q + 3 (each sorted by class)

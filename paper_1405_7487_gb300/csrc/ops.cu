@@ -227,14 +227,18 @@ struct CellView {
 // domain still holds below and above the cell: interior cells and cells at
 // the same place on the boundary have the same set of translation offsets,
 // so tiles of them need fewer distinct operators (fewer, fuller entries).
+// The key holds (level, octant, pattern); the cell goes with it as the value
+// of a stable sort whose input is in cell order, which orders equal keys by
+// cell.  Cells that take no M2L get key 2^kTargetKeyBits (last).
 constexpr int kPatternReach = 4;
 constexpr int kPatternBits = 14;  // (reach + 1)^6 = 15625 patterns < 2^14
-constexpr int kTargetKeyExtra = 5 + 3 + kPatternBits;  // level, octant, pattern
+constexpr int kTargetKeyBits = 5 + 3 + kPatternBits;  // level, octant, pattern
 
-__global__ void k_target_keys(const int32_t* __restrict__ has, CellView c, int ncell, int cbits,
-                              uint64_t* __restrict__ key) {
+__global__ void k_target_keys(const int32_t* __restrict__ has, CellView c, int ncell, uint64_t* __restrict__ key,
+                              int32_t* __restrict__ cell) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= ncell) return;
+  cell[i] = i;
   if (has[i]) {
     const int l = c.level[i];
     const int side = (1 << l) - 1;
@@ -245,19 +249,18 @@ __global__ void k_target_keys(const int32_t* __restrict__ has, CellView c, int n
       pat = pat * ((kPatternReach + 1) * (kPatternReach + 1)) + (uint64_t)(lo * (kPatternReach + 1) + hi);
     }
     const uint64_t oct = ((co[0] & 1) << 2) | ((co[1] & 1) << 1) | (co[2] & 1);
-    key[i] = ((uint64_t)l << (3 + kPatternBits + cbits)) | (oct << (kPatternBits + cbits)) | (pat << cbits) |
-             (uint32_t)i;
+    key[i] = ((uint64_t)l << (3 + kPatternBits)) | (oct << kPatternBits) | pat;
   } else {
-    key[i] = ~0ull;
+    key[i] = 1ull << kTargetKeyBits;
   }
 }
 
-__global__ void k_target_rank(const uint64_t* __restrict__ key, int64_t ntgt, int64_t padded, int cbits,
+__global__ void k_target_rank(const int32_t* __restrict__ sorted_cell, int64_t ntgt, int64_t padded,
                               int32_t* __restrict__ tile_tgt, int32_t* __restrict__ rank_of) {
   const int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (r >= padded) return;
   if (r < ntgt) {
-    const int cell = (int)(key[r] & ((1ull << cbits) - 1));
+    const int cell = sorted_cell[r];
     tile_tgt[r] = cell;
     rank_of[cell] = (int32_t)r;
   } else {
@@ -623,21 +626,20 @@ void build_m2l_plan(fmm_tree* t) {
   // found the largest class offset)
   int32_t* has = t->m2l_has;
   uint64_t* tkey = alloc_n<uint64_t>(a, t->ncell);
-  // 2^cbits > ncell, so a real key never equals the all-ones key of a non-target
-  int cbits = 1;
-  while ((1ll << cbits) <= (int64_t)t->ncell) ++cbits;
-  k_target_keys<<<blocks(t->ncell), kThreads, 0, s>>>(has, cv, t->ncell, cbits, tkey);
+  int32_t* tcell = alloc_n<int32_t>(a, t->ncell);
+  k_target_keys<<<blocks(t->ncell), kThreads, 0, s>>>(has, cv, t->ncell, tkey, tcell);
   GB_LAUNCH("k_target_keys");
-  radix_sort_keys(a, tkey, t->ncell, cbits + kTargetKeyExtra, s);
+  radix_sort_pairs(a, tkey, tcell, t->ncell, kTargetKeyBits + 1, s);
   // the target count and the largest class offset came with the traversal
   const unsigned long long ntgt = (unsigned long long)t->m2l_ntgt, maxd = t->m2l_maxd_host;
   t->ntile = (int)((ntgt + kTile - 1) / kTile);
   const int64_t padded = (int64_t)t->ntile * kTile;
   t->tile_tgt = alloc_n<int32_t>(a, padded);
   int32_t* rank_of = alloc_n<int32_t>(a, t->ncell);
-  k_target_rank<<<blocks(padded), kThreads, 0, s>>>(tkey, (int64_t)ntgt, padded, cbits, t->tile_tgt, rank_of);
+  k_target_rank<<<blocks(padded), kThreads, 0, s>>>(tcell, (int64_t)ntgt, padded, t->tile_tgt, rank_of);
   GB_LAUNCH("k_target_rank");
   a.release(tkey);
+  a.release(tcell);
 
   // --- translation classes
   int b = 1;

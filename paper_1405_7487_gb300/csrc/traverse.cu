@@ -297,7 +297,7 @@ __global__ void __launch_bounds__(kThreads) k_traverse(CellView c, int ncell, do
                                                        long long cap_p,
                                                        int32_t* __restrict__ m2l_has,
                                                        unsigned long long* __restrict__ m2l_maxd,
-                                                       uint32_t* __restrict__ m2l_off,
+                                                       uint32_t* __restrict__ m2l_off, int2* __restrict__ info,
                                                        long long* __restrict__ partial, TravState* st,
                                                        int* __restrict__ err) {
   const int G = gridDim.x, blk = blockIdx.x;
@@ -311,11 +311,18 @@ __global__ void __launch_bounds__(kThreads) k_traverse(CellView c, int ncell, do
     ++nlevel;
     const long long ch = (nf + G - 1) / G;
     const long long f0 = min(blk * ch, nf), f1 = min((blk + 1) * ch, nf);
+    // count: the decision, the three counts and (M2L) the packed class offset
+    // of each pair are kept in info[i] for the write pass, which then needs
+    // no cell data but for splits
     long long cnt[3] = {0, 0, 0};
     for (long long i = f0 + threadIdx.x; i < f1; i += kThreads) {
       const int2 pr = __ldcg(cur + i);
+      const int k = decide(c, pr.x, pr.y, theta2, circ);
       int v[3];
-      pair_counts(c, pr.x, pr.y, decide(c, pr.x, pr.y, theta2, circ), v[0], v[1], v[2]);
+      pair_counts(c, pr.x, pr.y, k, v[0], v[1], v[2]);
+      uint32_t w[2] = {0, 0};
+      if (k == 2) dm = max(dm, mark_m2l(c, pr.x, pr.y, m2l_has, w));
+      info[i] = make_int2(k | (v[0] << 3) | (v[1] << 10) | (v[2] << 12), (int)w[0]);
       for (int j = 0; j < 3; ++j) cnt[j] += v[j];
     }
     {
@@ -348,11 +355,17 @@ __global__ void __launch_bounds__(kThreads) k_traverse(CellView c, int ncell, do
       uint32_t w[2] = {0, 0};
       if (i < f1) {
         const int2 pr = __ldcg(cur + i);
+        const int2 in = info[i];
         A = pr.x;
         B = pr.y;
-        k = decide(c, A, B, theta2, circ);
-        pair_counts(c, A, B, k, v[0], v[1], v[2]);
-        if (k == 2) dm = max(dm, mark_m2l(c, A, B, m2l_has, w));
+        k = in.x & 7;
+        v[0] = (in.x >> 3) & 127;
+        v[1] = (in.x >> 10) & 3;
+        v[2] = (in.x >> 12) & 3;
+        w[0] = (uint32_t)in.y;
+        // the entry (target A, source B): level difference and offsets negated
+        w[1] = (64u - (w[0] >> 24)) << 24;
+        for (int d = 0; d < 3; ++d) w[1] |= ((uint32_t)(-(int)(int8_t)(w[0] >> (16 - 8 * d))) & 0xffu) << (16 - 8 * d);
       }
       block_scan3(v, tot);
       if (i < f1) write_pair(c, A, B, k, run[0] + v[0], run[1] + v[1], run[2] + v[2], nxt, m2l, p2p, m2l_off, w);
@@ -728,14 +741,15 @@ void build_lists(fmm_tree* t) {
     int2* F1 = alloc_n<int2>(a, capF);
     long long* partial = alloc_n<long long>(a, 3 * (size_t)G);
     TravState* d_st = alloc_n<TravState>(a, 1);
+    int2* info = alloc_n<int2>(a, capF);
     GB_CK(cudaMemsetAsync(d_st, 0, sizeof(TravState), s));
     long long capF_ = capF, cap_m_ = cap_m, cap_p_ = cap_p;
     int* err = a.err;
     const int ncell = t->ncell;
     void* args[] = {(void*)&cv,     (void*)&ncell,  (void*)&theta2, (void*)&circ, (void*)&F0, (void*)&F1,
                     (void*)&capF_,  (void*)&m2l,    (void*)&cap_m_,     (void*)&p2p,        (void*)&cap_p_,
-                    (void*)&t->m2l_has, (void*)&t->m2l_maxd, (void*)&t->m2l_off, (void*)&partial, (void*)&d_st,
-                    (void*)&err};
+                    (void*)&t->m2l_has, (void*)&t->m2l_maxd, (void*)&t->m2l_off, (void*)&info, (void*)&partial,
+                    (void*)&d_st, (void*)&err};
     GB_CK(cudaLaunchCooperativeKernel((const void*)k_traverse, dim3(G), dim3(kThreads), args, 0, s));
     GB_LAUNCH("k_traverse");
     TravState h;
@@ -748,6 +762,7 @@ void build_lists(fmm_tree* t) {
       t->m2l_ntgt = h.ntgt;
       done = true;
     }
+    a.release(info);
     a.release(d_st);
     a.release(partial);
     a.release(F1);
