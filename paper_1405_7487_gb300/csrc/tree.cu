@@ -28,92 +28,67 @@ struct Body4<double> {
   using type = double4_32a;
 };
 
+// Block-wide min of r[0..2] and max of r[3..6], into thread 0's r.
+template <class R>
+__device__ __forceinline__ void block_minmax7(R r[7]) {
+  for (int o = 16; o > 0; o >>= 1)
+    for (int k = 0; k < 7; ++k) {
+      const R v = __shfl_down_sync(0xffffffffu, r[k], o);
+      r[k] = k < 3 ? fmin(r[k], v) : fmax(r[k], v);
+    }
+  __shared__ R sh[kThreads / 32][7];
+  const int w = threadIdx.x >> 5;
+  if ((threadIdx.x & 31) == 0)
+    for (int k = 0; k < 7; ++k) sh[w][k] = r[k];
+  __syncthreads();
+  if (threadIdx.x == 0)
+    for (int ww = 1; ww < (int)(blockDim.x >> 5); ++ww)
+      for (int k = 0; k < 7; ++k) r[k] = k < 3 ? fmin(r[k], sh[ww][k]) : fmax(r[k], sh[ww][k]);
+}
+
 // Per-block min/max of each axis and a non-finite flag.  Minima and maxima
 // are exact in the input's own precision, so the single-precision path
 // reduces in FP32 (no FP64 per body) and widens each thread's result.
 template <class R>
 __global__ void k_bbox_partial(const R* __restrict__ xyzq, int64_t n, double* __restrict__ part) {
-  R lr[3] = {(R)INFINITY, (R)INFINITY, (R)INFINITY}, hr[3] = {-(R)INFINITY, -(R)INFINITY, -(R)INFINITY};
-  bool bad_r = false;
+  // r: min x, y, z, max x, y, z, non-finite flag
+  R r[7] = {(R)INFINITY, (R)INFINITY, (R)INFINITY, -(R)INFINITY, -(R)INFINITY, -(R)INFINITY, (R)0};
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     const R x = xyzq[4 * i], y = xyzq[4 * i + 1], z = xyzq[4 * i + 2], q = xyzq[4 * i + 3];
     if (!(isfinite(x) && isfinite(y) && isfinite(z) && isfinite(q))) {
-      bad_r = true;
+      r[6] = (R)1;
       continue;
     }
-    lr[0] = fmin(lr[0], x); hr[0] = fmax(hr[0], x);
-    lr[1] = fmin(lr[1], y); hr[1] = fmax(hr[1], y);
-    lr[2] = fmin(lr[2], z); hr[2] = fmax(hr[2], z);
+    r[0] = fmin(r[0], x); r[3] = fmax(r[3], x);
+    r[1] = fmin(r[1], y); r[4] = fmax(r[4], y);
+    r[2] = fmin(r[2], z); r[5] = fmax(r[5], z);
   }
-  double lo[3], hi[3], bad = bad_r ? 1.0 : 0.0;
-  for (int a = 0; a < 3; ++a) {
-    lo[a] = (double)lr[a];
-    hi[a] = (double)hr[a];
-  }
-  for (int o = 16; o > 0; o >>= 1) {
-    for (int a = 0; a < 3; ++a) {
-      lo[a] = fmin(lo[a], __shfl_down_sync(0xffffffffu, lo[a], o));
-      hi[a] = fmax(hi[a], __shfl_down_sync(0xffffffffu, hi[a], o));
-    }
-    bad = fmax(bad, __shfl_down_sync(0xffffffffu, bad, o));
-  }
-  __shared__ double s[kThreads / 32][7];
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  if (lane == 0) {
-    for (int a = 0; a < 3; ++a) {
-      s[w][a] = lo[a];
-      s[w][3 + a] = hi[a];
-    }
-    s[w][6] = bad;
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double r[7];
-    for (int k = 0; k < 7; ++k) r[k] = s[0][k];
-    for (int ww = 1; ww < kThreads / 32; ++ww) {
-      for (int a = 0; a < 3; ++a) {
-        r[a] = fmin(r[a], s[ww][a]);
-        r[3 + a] = fmax(r[3 + a], s[ww][3 + a]);
-      }
-      r[6] = fmax(r[6], s[ww][6]);
-    }
-    for (int k = 0; k < 7; ++k) part[7 * blockIdx.x + k] = r[k];
-  }
+  block_minmax7(r);
+  if (threadIdx.x == 0)
+    for (int k = 0; k < 7; ++k) part[7 * blockIdx.x + k] = (double)r[k];  // exact
 }
 
 // Root cube: centre (lo+hi)/2, half side H = max_axis (hi-lo)/2 * (1 + 2^-20)
 // (H = 0.5 if all bodies coincide), corner = centre - H.  Explicitly rounded
-// double operations: no fused multiply-add may change the keys.
+// double operations: no fused multiply-add may change the keys.  The
+// partials hold values of the input's precision R, so they are reduced in R.
+template <class R>
 __global__ void k_bbox_final(const double* __restrict__ part, int nb, double* __restrict__ root,
                              int* __restrict__ nonfinite) {
   // min/max are exact, so the reduction order does not matter
-  __shared__ double sh[kThreads / 32][7];
-  double r[7] = {INFINITY, INFINITY, INFINITY, -INFINITY, -INFINITY, -INFINITY, 0.0};
+  R rr[7] = {(R)INFINITY, (R)INFINITY, (R)INFINITY, -(R)INFINITY, -(R)INFINITY, -(R)INFINITY, (R)0};
   for (int b = threadIdx.x; b < nb; b += blockDim.x) {
     for (int a = 0; a < 3; ++a) {
-      r[a] = fmin(r[a], part[7 * b + a]);
-      r[3 + a] = fmax(r[3 + a], part[7 * b + 3 + a]);
+      rr[a] = fmin(rr[a], (R)part[7 * b + a]);
+      rr[3 + a] = fmax(rr[3 + a], (R)part[7 * b + 3 + a]);
     }
-    r[6] = fmax(r[6], part[7 * b + 6]);
+    rr[6] = fmax(rr[6], (R)part[7 * b + 6]);
   }
-  for (int o = 16; o > 0; o >>= 1)
-    for (int k = 0; k < 7; ++k) {
-      const double v = __shfl_down_sync(0xffffffffu, r[k], o);
-      r[k] = k < 3 ? fmin(r[k], v) : fmax(r[k], v);
-    }
-  const int warp = threadIdx.x >> 5;
-  if ((threadIdx.x & 31) == 0)
-    for (int k = 0; k < 7; ++k) sh[warp][k] = r[k];
-  __syncthreads();
+  block_minmax7(rr);
   if (threadIdx.x != 0) return;
-  for (int w = 1; w < (int)(blockDim.x >> 5); ++w) {
-    for (int a = 0; a < 3; ++a) {
-      r[a] = fmin(r[a], sh[w][a]);
-      r[3 + a] = fmax(r[3 + a], sh[w][3 + a]);
-    }
-    r[6] = fmax(r[6], sh[w][6]);
-  }
+  double r[7];
+  for (int k = 0; k < 7; ++k) r[k] = (double)rr[k];
   *nonfinite = r[6] != 0.0;
   double h = 0.0;
   for (int a = 0; a < 3; ++a) {
@@ -201,9 +176,12 @@ struct Octants {
 // Lanes d = 0..7 of an aligned group of eight lanes take octant d of cell
 // `cell` (valid false: no cell).  The cell arrays are read through L2: the
 // cooperative level kernel reads cells that other blocks wrote.
+// bnd: where octant d starts, per cell (8 entries a cell, relative to the
+// level's first cell lb): the count pass writes it (saved = false), the write
+// pass reads it back instead of searching again (saved = true).
 __device__ __forceinline__ Octants octants_at(const uint64_t* __restrict__ keys, const int32_t* bbeg,
                                               const int32_t* bend, int cell, int d, bool valid, int level,
-                                              int ncrit) {
+                                              int ncrit, int* bnd, int lb, bool saved) {
   Octants o;
   o.c = cell;
   o.d = d;
@@ -212,7 +190,15 @@ __device__ __forceinline__ Octants octants_at(const uint64_t* __restrict__ keys,
   o.e = valid ? __ldcg(bend + cell) : 0;
   o.split = valid && o.e - o.s > ncrit && level < kMaxLevel;
   o.b = o.s;
-  if (o.split && d > 0) o.b = lower_digit(keys, o.s, o.e, 3 * (kMaxLevel - level - 1), d);
+  if (o.split && d > 0) {
+    int* at = bnd + 8 * (int64_t)(cell - lb) + d;
+    if (saved) {
+      o.b = *at;
+    } else {
+      o.b = lower_digit(keys, o.s, o.e, 3 * (kMaxLevel - level - 1), d);
+      *at = o.b;
+    }
+  }
   o.nb = __shfl_down_sync(0xffffffffu, o.b, 1, 8);
   if (d == 7) o.nb = o.e;
   const unsigned m = __ballot_sync(0xffffffffu, o.split && o.nb > o.b);
@@ -242,7 +228,8 @@ struct LevelState {
 __global__ void __launch_bounds__(kThreads) k_tree_levels(const uint64_t* __restrict__ keys, int n, int ncrit,
                                                           int cap, Cells c, int32_t* __restrict__ leaves,
                                                           int32_t* __restrict__ leaf_of, int* __restrict__ partial,
-                                                          LevelState* __restrict__ st, int* __restrict__ err) {
+                                                          int* __restrict__ bnd, LevelState* __restrict__ st,
+                                                          int* __restrict__ err) {
   __shared__ int pass_cnt[kThreads / 8];
   __shared__ int chunk_sum;
   const int G = gridDim.x, blk = blockIdx.x;
@@ -265,7 +252,7 @@ __global__ void __launch_bounds__(kThreads) k_tree_levels(const uint64_t* __rest
     __syncthreads();
     for (int cb = c0; cb < c1; cb += kThreads / 8) {
       const int cell = cb + slot;
-      const Octants o = octants_at(keys, c.bbeg, c.bend, cell, lane8, cell < c1, l, ncrit);
+      const Octants o = octants_at(keys, c.bbeg, c.bend, cell, lane8, cell < c1, l, ncrit, bnd, lb, false);
       if (o.valid && lane8 == 0) atomicAdd(&chunk_sum, __popc(o.group));
     }
     __syncthreads();
@@ -283,7 +270,7 @@ __global__ void __launch_bounds__(kThreads) k_tree_levels(const uint64_t* __rest
     int run = le + before;
     for (int cb = c0; cb < c1; cb += kThreads / 8) {
       const int cell = cb + slot;
-      const Octants o = octants_at(keys, c.bbeg, c.bend, cell, lane8, cell < c1, l, ncrit);
+      const Octants o = octants_at(keys, c.bbeg, c.bend, cell, lane8, cell < c1, l, ncrit, bnd, lb, true);
       const int nchild = __popc(o.group);
       if (lane8 == 0) pass_cnt[slot] = o.valid ? nchild : 0;
       __syncthreads();
@@ -373,7 +360,7 @@ void build_tree_impl(fmm_tree* t, const R* xyzq) {
   int* d_bad = alloc_n<int>(a, 1);
   k_bbox_partial<R><<<nb, kThreads, 0, s>>>(xyzq, N, part);
   GB_LAUNCH("k_bbox_partial");
-  k_bbox_final<<<1, kThreads, 0, s>>>(part, nb, t->d_root, d_bad);
+  k_bbox_final<R><<<1, kThreads, 0, s>>>(part, nb, t->d_root, d_bad);
   GB_LAUNCH("k_bbox_final");
   // --- keys and stable sort (ties keep input order: LSD radix is stable and
   // the initial order is the input order).  The root cube stays on the
@@ -417,6 +404,7 @@ void build_tree_impl(fmm_tree* t, const R* xyzq) {
   int64_t cap = std::min<int64_t>(bound, 8 * ((N + t->ncrit - 1) / t->ncrit) + 4096);
   int* partial = alloc_n<int>(a, G);
   LevelState* d_st = alloc_n<LevelState>(a, 1);
+  int* bnd = nullptr;  // octant starts of one level's cells (at most cap cells)
   LevelState hst;
   double hroot[13];
   int hbad = 0;
@@ -426,11 +414,13 @@ void build_tree_impl(fmm_tree* t, const R* xyzq) {
     for (auto f : fields) *f = alloc_n<int32_t>(a, cap);
     t->leaves = alloc_n<int32_t>(a, cap);
     t->leaf_of_cell = alloc_n<int32_t>(a, cap);
+    bnd = alloc_n<int>(a, 8 * (size_t)cap);
     GB_CK(cudaMemsetAsync(d_st, 0, sizeof(LevelState), s));
     const int n32 = (int)N, ncrit = t->ncrit, cap32 = (int)cap;
     int* err = a.err;
     void* args[] = {(void*)&keys, (void*)&n32, (void*)&ncrit, (void*)&cap32, (void*)&c,
-                    (void*)&t->leaves, (void*)&t->leaf_of_cell, (void*)&partial, (void*)&d_st, (void*)&err};
+                    (void*)&t->leaves, (void*)&t->leaf_of_cell, (void*)&partial, (void*)&bnd, (void*)&d_st,
+                    (void*)&err};
     GB_CK(cudaLaunchCooperativeKernel((const void*)k_tree_levels, dim3(G), dim3(kThreads), args, 0, s));
     GB_LAUNCH("k_tree_levels");
     GB_CK(cudaMemcpyAsync(&hst, d_st, sizeof(LevelState), cudaMemcpyDeviceToHost, s));
@@ -445,8 +435,10 @@ void build_tree_impl(fmm_tree* t, const R* xyzq) {
     for (auto f : fields) a.release(*f);
     a.release(t->leaves);
     a.release(t->leaf_of_cell);
+    a.release(bnd);
     cap = bound;
   }
+  a.release(bnd);
   a.release(partial);
   a.release(d_st);
   a.release(part);
@@ -559,7 +551,7 @@ extern "C" int fmm_root_keys_noalloc(const float* xyzq, int64_t n, double* root,
   const int nb = (int)std::min<int64_t>(kNoAllocBlocks, (n + kThreads - 1) / kThreads);
   int* flag = nonfinite ? nonfinite : reinterpret_cast<int*>(scratch + kNoAllocBlocks * 7);
   k_bbox_partial<float><<<nb, kThreads, 0, s>>>(xyzq, n, scratch);
-  k_bbox_final<<<1, kThreads, 0, s>>>(scratch, nb, root, flag);
+  k_bbox_final<float><<<1, kThreads, 0, s>>>(scratch, nb, root, flag);
   if (keys) k_keys<float><<<(unsigned)((n + kThreads - 1) / kThreads), kThreads, 0, s>>>(xyzq, n, root, keys, nullptr);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) {
