@@ -43,7 +43,7 @@ L2_FLUSH_BYTES = 512 << 20  # > 129 MB L2
 # DRAM bytes (read + write) per launch of the dominant kernel from one ncu
 # capture (profiles/k_m2l_tc4_cube1m_p10_dram.md): workload, N, kernel.
 # Entries are dropped when the kernel changes.
-DRAM_TRAFFIC = {("cube1m_p10", 1048576, "k_m2l_tc4"): 419_200_000 + 600_150_000}
+DRAM_TRAFFIC = {("cube1m_p10", 1048576, "k_m2l_tc4"): 401_603_584 + 601_194_752}
 CPU_SAMPLE_N = 65536
 ISO_STEPS = 5  # serial-phase steps behind the per-kernel ("isolated") figures
 
