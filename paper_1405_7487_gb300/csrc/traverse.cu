@@ -298,6 +298,10 @@ __global__ void __launch_bounds__(kThreads) k_traverse(CellView c, int ncell, do
                                                        int32_t* __restrict__ m2l_has,
                                                        unsigned long long* __restrict__ m2l_maxd,
                                                        uint32_t* __restrict__ m2l_off, int2* __restrict__ info,
+                                                       const int32_t* __restrict__ leaf_of,
+                                                       const int32_t* __restrict__ bbeg,
+                                                       const int32_t* __restrict__ bend, int64_t* __restrict__ leaf_cnt,
+                                                       unsigned long long* __restrict__ body_pairs,
                                                        long long* __restrict__ partial, TravState* st,
                                                        int* __restrict__ err) {
   const int G = gridDim.x, blk = blockIdx.x;
@@ -306,6 +310,7 @@ __global__ void __launch_bounds__(kThreads) k_traverse(CellView c, int ncell, do
   long long nf = 1, nm = 0, np = 0;
   int nlevel = 0;
   unsigned dm = 0;
+  unsigned long long bp = 0;  // this thread's body pairs
   bool fine = grid_barrier(&st->bar, err), over = false;
   while (fine && nf > 0) {
     ++nlevel;
@@ -368,7 +373,18 @@ __global__ void __launch_bounds__(kThreads) k_traverse(CellView c, int ncell, do
         for (int d = 0; d < 3; ++d) w[1] |= ((uint32_t)(-(int)(int8_t)(w[0] >> (16 - 8 * d))) & 0xffu) << (16 - 8 * d);
       }
       block_scan3(v, tot);
-      if (i < f1) write_pair(c, A, B, k, run[0] + v[0], run[1] + v[1], run[2] + v[2], nxt, m2l, p2p, m2l_off, w);
+      if (i < f1) {
+        write_pair(c, A, B, k, run[0] + v[0], run[1] + v[1], run[2] + v[2], nxt, m2l, p2p, m2l_off, w);
+        // P2P: each target leaf's count of sources (self excluded) and the body pairs
+        if (k == 0) {
+          const unsigned long long na = bend[A] - bbeg[A];
+          bp += na * na;
+        } else if (k == 3) {
+          bp += 2ull * (unsigned long long)(bend[A] - bbeg[A]) * (unsigned long long)(bend[B] - bbeg[B]);
+          atomicAdd(reinterpret_cast<unsigned long long*>(leaf_cnt + leaf_of[A]), 1ull);
+          atomicAdd(reinterpret_cast<unsigned long long*>(leaf_cnt + leaf_of[B]), 1ull);
+        }
+      }
       for (int j = 0; j < 3; ++j) run[j] += tot[j];
     }
     fine = grid_barrier(&st->bar, err);
@@ -381,7 +397,11 @@ __global__ void __launch_bounds__(kThreads) k_traverse(CellView c, int ncell, do
   }
   if (!fine) return;
   block_maxd(dm, m2l_maxd);
-  if (!over) count_flags(m2l_has, ncell, &st->ntgt);
+  if (!over) {
+    count_flags(m2l_has, ncell, &st->ntgt);
+    for (int o = 16; o > 0; o >>= 1) bp += __shfl_down_sync(0xffffffffu, bp, o);
+    if ((threadIdx.x & 31) == 0 && bp) atomicAdd(body_pairs, bp);
+  }
   if (blk == 0 && threadIdx.x == 0 && !over) {
     st->nm = nm;
     st->np = np;
@@ -517,37 +537,46 @@ __global__ void k_p2p_leaf_sort(const int64_t* __restrict__ ptr, int nleaf, cons
   }
 }
 
-// Merge adjacent body ranges of one target leaf; count pass (out == null)
-// or write pass.
-__global__ void k_merge_ranges(const int64_t* __restrict__ eptr, const int32_t* __restrict__ val,
-                               const int32_t* __restrict__ bbeg, const int32_t* __restrict__ bend,
-                               int nleaf, int64_t* __restrict__ count,
-                               const int64_t* __restrict__ out_off, int2* __restrict__ out) {
-  const int l = blockIdx.x * blockDim.x + threadIdx.x;
+// Merge adjacent body ranges of one target leaf (its sources in body order);
+// count pass (out == null) or write pass.  A warp per leaf, 32 sources at a
+// time: a source starts a merged range unless its body range begins where
+// the previous one ended, and ends one unless the next begins where it ends.
+constexpr int kMergeWarps = 8;
+__global__ void __launch_bounds__(32 * kMergeWarps)
+    k_merge_ranges(const int64_t* __restrict__ eptr, const int32_t* __restrict__ val,
+                   const int32_t* __restrict__ bbeg, const int32_t* __restrict__ bend, int nleaf,
+                   int64_t* __restrict__ count, const int64_t* __restrict__ out_off, int2* __restrict__ out) {
+  const int lane = threadIdx.x & 31;
+  const int l = blockIdx.x * kMergeWarps + (threadIdx.x >> 5);
   if (l >= nleaf) return;
   const int64_t e0 = eptr[l], e1 = eptr[l + 1];
-  int64_t m = 0;
-  int cb = -1, ce = -1;
-  int64_t o = out ? out_off[l] : 0;
-  for (int64_t e = e0; e < e1; ++e) {
-    const int s = val[e];
-    const int b = bbeg[s], en = bend[s];
-    if (cb >= 0 && b == ce) {
-      ce = en;
-    } else {
-      if (cb >= 0) {
-        if (out) out[o + m] = make_int2(cb, ce);
-        ++m;
-      }
-      cb = b;
-      ce = en;
+  const int64_t o = out ? out_off[l] : 0;
+  int64_t runs = 0;  // merged ranges started before this group of 32
+  int prev_end = -1;  // body end of the source before this group
+  for (int64_t g = e0; g < e1; g += 32) {
+    const int64_t e = g + lane;
+    const bool ok = e < e1;
+    int b = 0, en = 0, nb = -2;
+    if (ok) {
+      const int sr = val[e];
+      b = bbeg[sr];
+      en = bend[sr];
+      if (e + 1 < e1) nb = bbeg[val[e + 1]];
     }
+    int pe = __shfl_up_sync(0xffffffffu, en, 1);
+    if (lane == 0) pe = prev_end;
+    const bool start = ok && b != pe;
+    const bool last = ok && nb != en;
+    const unsigned sm = __ballot_sync(0xffffffffu, start);
+    const int64_t k = runs + __popc(sm & ((2u << lane) - 1u)) - 1;  // this source's range
+    if (out) {
+      if (start) out[o + k].x = b;
+      if (last) out[o + k].y = en;
+    }
+    runs += __popc(sm);
+    prev_end = __shfl_sync(0xffffffffu, en, 31);
   }
-  if (cb >= 0) {
-    if (out) out[o + m] = make_int2(cb, ce);
-    ++m;
-  }
-  if (count) count[l] = m;
+  if (count && lane == 0) count[l] = runs;
 }
 
 __global__ void k_i64_to_i32(const int64_t* __restrict__ a, int64_t n, int32_t* __restrict__ b) {
@@ -722,6 +751,14 @@ void build_lists(fmm_tree* t) {
   // each); then one read-back.  Otherwise the per-level launches below take
   // over, with one read-back per level (the marks already made are kept:
   // they are a subset of the final ones).
+  // per target leaf its count of sources (then their offsets), and the body
+  // pairs; the range count and the body-pair total stay on the device until
+  // the end of the build (t->d_tail[0], t->d_tail[1])
+  t->d_tail = alloc_n<long long>(a, 4);
+  GB_CK(cudaMemsetAsync(t->d_tail, 0, 4 * sizeof(long long), s));
+  unsigned long long* d_pairs = reinterpret_cast<unsigned long long*>(t->d_tail + 1);
+  int64_t* eptr = alloc_n<int64_t>(a, t->nleaf + 1);
+  GB_CK(cudaMemsetAsync(eptr, 0, sizeof(int64_t) * (t->nleaf + 1), s));
   const int64_t budget = std::max<int64_t>(1ll << 23, 64 * t->N);
   int64_t cap_m = budget / 2, cap_p = budget / 10;
   const int64_t capF = budget / 5;
@@ -748,8 +785,9 @@ void build_lists(fmm_tree* t) {
     const int ncell = t->ncell;
     void* args[] = {(void*)&cv,     (void*)&ncell,  (void*)&theta2, (void*)&circ, (void*)&F0, (void*)&F1,
                     (void*)&capF_,  (void*)&m2l,    (void*)&cap_m_,     (void*)&p2p,        (void*)&cap_p_,
-                    (void*)&t->m2l_has, (void*)&t->m2l_maxd, (void*)&t->m2l_off, (void*)&info, (void*)&partial,
-                    (void*)&d_st, (void*)&err};
+                    (void*)&t->m2l_has, (void*)&t->m2l_maxd, (void*)&t->m2l_off, (void*)&info,
+                    (void*)&t->leaf_of_cell, (void*)&t->c.bbeg, (void*)&t->c.bend, (void*)&eptr, (void*)&d_pairs,
+                    (void*)&partial, (void*)&d_st, (void*)&err};
     GB_CK(cudaLaunchCooperativeKernel((const void*)k_traverse, dim3(G), dim3(kThreads), args, 0, s));
     GB_LAUNCH("k_traverse");
     TravState h;
@@ -769,6 +807,9 @@ void build_lists(fmm_tree* t) {
     a.release(F0);
   }
   if (!done) {
+    // the single launch may have counted some levels before it stopped
+    GB_CK(cudaMemsetAsync(eptr, 0, sizeof(int64_t) * (t->nleaf + 1), s));
+    GB_CK(cudaMemsetAsync(d_pairs, 0, sizeof(unsigned long long), s));
     int64_t nf = 1;
     int64_t* d_seg = alloc_n<int64_t>(a, 3);
     int2* fr = alloc_n<int2>(a, 1);
@@ -851,17 +892,14 @@ void build_lists(fmm_tree* t) {
   t->p2p_tgt = p2p.tgt;
   t->p2p_src = p2p.src;
 
-  // --- P2P body ranges per target leaf, merged where contiguous
-  // the range count and the body-pair total stay on the device until the
-  // end of the build (t->d_tail[0], t->d_tail[1])
-  t->d_tail = alloc_n<long long>(a, 4);
-  GB_CK(cudaMemsetAsync(t->d_tail, 0, 4 * sizeof(long long), s));
-  unsigned long long* d_pairs = reinterpret_cast<unsigned long long*>(t->d_tail + 1);
-  int64_t* eptr = alloc_n<int64_t>(a, t->nleaf + 1);
-  GB_CK(cudaMemsetAsync(eptr, 0, sizeof(int64_t) * (t->nleaf + 1), s));
-  k_p2p_leaf_count<<<blocks(np), kThreads, 0, s>>>(t->p2p_tgt, t->p2p_src, np, t->leaf_of_cell, t->c.bbeg,
-                                                   t->c.bend, eptr, d_pairs);
-  GB_LAUNCH("k_p2p_leaf_count");
+  // --- P2P body ranges per target leaf, merged where contiguous.  The
+  // single-launch traversal counted each leaf's sources and the body pairs
+  // already; the per-level one leaves it to k_p2p_leaf_count.
+  if (!done) {
+    k_p2p_leaf_count<<<blocks(np), kThreads, 0, s>>>(t->p2p_tgt, t->p2p_src, np, t->leaf_of_cell, t->c.bbeg,
+                                                     t->c.bend, eptr, d_pairs);
+    GB_LAUNCH("k_p2p_leaf_count");
+  }
   scan_exclusive_i64(a, eptr, t->nleaf + 1, s);
   int32_t* cursor = alloc_n<int32_t>(a, t->nleaf);
   GB_CK(cudaMemsetAsync(cursor, 0, sizeof(int32_t) * t->nleaf, s));
@@ -878,14 +916,15 @@ void build_lists(fmm_tree* t) {
   // per leaf: the number of merged ranges, then the ranges
   int64_t* rcount = alloc_n<int64_t>(a, t->nleaf + 1);
   GB_CK(cudaMemsetAsync(rcount, 0, sizeof(int64_t) * (t->nleaf + 1), s));
-  k_merge_ranges<<<blocks(t->nleaf), kThreads, 0, s>>>(eptr, rval, t->c.bbeg, t->c.bend, t->nleaf,
-                                                       rcount, nullptr, nullptr);
+  const unsigned mblocks = (unsigned)((t->nleaf + kMergeWarps - 1) / kMergeWarps);
+  k_merge_ranges<<<mblocks, 32 * kMergeWarps, 0, s>>>(eptr, rval, t->c.bbeg, t->c.bend, t->nleaf, rcount,
+                                                      nullptr, nullptr);
   GB_LAUNCH("k_merge_ranges");
   // a leaf's merged ranges are at most its source leaves: np entries suffice
   scan_exclusive_i64_dev(a, rcount, t->nleaf + 1, reinterpret_cast<int64_t*>(t->d_tail), s);
   t->p2p_ranges = alloc_n<int2>(a, np);
-  k_merge_ranges<<<blocks(t->nleaf), kThreads, 0, s>>>(eptr, rval, t->c.bbeg, t->c.bend, t->nleaf,
-                                                       nullptr, rcount, t->p2p_ranges);
+  k_merge_ranges<<<mblocks, 32 * kMergeWarps, 0, s>>>(eptr, rval, t->c.bbeg, t->c.bend, t->nleaf, nullptr,
+                                                      rcount, t->p2p_ranges);
   GB_LAUNCH("k_merge_ranges");
   t->p2p_rptr = alloc_n<int32_t>(a, t->nleaf + 1);
   k_i64_to_i32<<<blocks(t->nleaf + 1), kThreads, 0, s>>>(rcount, t->nleaf + 1, t->p2p_rptr);
