@@ -293,16 +293,15 @@ void root_and_keys(Tree& t, std::vector<uint64_t>& key_in) {
   t.H = h * (1.0 + std::ldexp(1.0, -20));
   if (t.H == 0.0) t.H = 0.5;
   for (int a = 0; a < 3; ++a) t.r0[a] = t.ctr[a] - t.H;
-  const double side = 2.0 * t.H;
-  const double scale = std::ldexp(1.0, MAXLEVEL);
+  // voxels per unit length, 2^21 / (2H), rounded once
+  const double per_len = std::ldexp(1.0, MAXLEVEL) / (2.0 * t.H);
   const int64_t kmax = (1ll << MAXLEVEL) - 1;
   key_in.resize(N);
   for (int64_t i = 0; i < N; ++i) {
     uint64_t k3[3];
     for (int a = 0; a < 3; ++a) {
       double d = t.xyz[3 * i + a] - t.r0[a];
-      double f = d / side;
-      double s = f * scale;
+      double s = d * per_len;
       double fl = std::floor(s);
       int64_t k = (int64_t)fl;
       if (k < 0) k = 0;

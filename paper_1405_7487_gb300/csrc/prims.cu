@@ -345,46 +345,84 @@ __global__ void k_rs_hist(const uint64_t* __restrict__ keys, int64_t n, int shif
   counts[(int64_t)threadIdx.x * ntile + blockIdx.x] = h[threadIdx.x];
 }
 
+// Stable scatter of one tile.  Each key's place within the tile (its digit's
+// start in the tile + its rank among the tile's keys of that digit) is found
+// in rounds of 256 keys; the keys are first placed in shared memory in that
+// order, then written out in order, so that neighbouring threads write
+// neighbouring slots of one digit's run (coalesced).
 __global__ void k_rs_scatter(const uint64_t* __restrict__ kin, const int32_t* __restrict__ vin,
                              uint64_t* __restrict__ kout, int32_t* __restrict__ vout, int64_t n,
                              int shift, int ntile, const int64_t* __restrict__ offs) {
-  __shared__ int64_t base_d[kRadix];
+  __shared__ int64_t gbase[kRadix];     // digit's first global slot for this tile
+  __shared__ int lstart[kRadix];        // digit's first slot within the tile
+  __shared__ int lrun[kRadix];          // keys of the digit placed so far
   __shared__ int wcnt[kSortThreads / 32][kRadix];
-  __shared__ int rtot[kRadix];
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  base_d[threadIdx.x] = offs[(int64_t)threadIdx.x * ntile + blockIdx.x];
+  __shared__ int wsum[kSortThreads / 32];
+  __shared__ uint64_t sk[kSortTile];
+  __shared__ int32_t sv[kSortTile];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, t = threadIdx.x;
   const int64_t tbase = (int64_t)blockIdx.x * kSortTile;
-  for (int r = 0; r < kSortRounds; ++r) {
-    for (int w = 0; w < kSortThreads / 32; ++w) wcnt[w][threadIdx.x] = 0;
+  const int tn = (int)(n - tbase < kSortTile ? n - tbase : kSortTile);  // keys in this tile
+  {
+    // this tile's count of digit t: the distance to the next (digit, tile)
+    // slot of the scanned, digit-major table (the last one ends at n)
+    const int64_t at = (int64_t)t * ntile + blockIdx.x;
+    const int64_t start = offs[at];
+    const int64_t next = at + 1 < (int64_t)kRadix * ntile ? offs[at + 1] : n;
+    gbase[t] = start;
+    const int c = (int)(next - start);
+    // exclusive scan of the counts over the digits
+    int inc = c;
+    for (int o = 1; o < 32; o <<= 1) {
+      const int u = __shfl_up_sync(0xffffffffu, inc, o);
+      if (lane >= o) inc += u;
+    }
+    if (lane == 31) wsum[wid] = inc;
     __syncthreads();
-    const int64_t k = tbase + (int64_t)r * kSortThreads + threadIdx.x;
-    const bool valid = k < n;
-    uint64_t key = valid ? kin[k] : 0;
-    int32_t val = (valid && vin) ? vin[k] : 0;
+    int before = 0;
+    for (int q = 0; q < wid; ++q) before += wsum[q];
+    lstart[t] = before + inc - c;
+    lrun[t] = 0;
+  }
+  for (int r = 0; r < kSortRounds; ++r) {
+    for (int w = 0; w < kSortThreads / 32; ++w) wcnt[w][t] = 0;
+    __syncthreads();
+    const int li = r * kSortThreads + t;
+    const bool valid = li < tn;
+    const uint64_t key = valid ? kin[tbase + li] : 0;
+    const int32_t val = (valid && vin) ? vin[tbase + li] : 0;
     const int d = valid ? (int)((key >> shift) & 0xff) : kRadix;
     const unsigned peers = __match_any_sync(0xffffffffu, d);
     const int rank = __popc(peers & ((1u << lane) - 1u));
     const int leader = __ffs(peers) - 1;
     if (valid && lane == leader) wcnt[wid][d] = __popc(peers);
     __syncthreads();
+    int rtot;
     {
       int run = 0;
       for (int w = 0; w < kSortThreads / 32; ++w) {
-        int c = wcnt[w][threadIdx.x];
-        wcnt[w][threadIdx.x] = run;
+        const int c = wcnt[w][t];
+        wcnt[w][t] = run;
         run += c;
       }
-      rtot[threadIdx.x] = run;
+      rtot = run;
     }
     __syncthreads();
     if (valid) {
-      const int64_t pos = base_d[d] + wcnt[wid][d] + rank;
-      kout[pos] = key;
-      if (vout) vout[pos] = val;
+      const int pos = lstart[d] + lrun[d] + wcnt[wid][d] + rank;
+      sk[pos] = key;
+      sv[pos] = val;
     }
     __syncthreads();
-    base_d[threadIdx.x] += rtot[threadIdx.x];
-    __syncthreads();
+    lrun[t] += rtot;
+  }
+  __syncthreads();
+  for (int i = t; i < tn; i += kSortThreads) {
+    const uint64_t key = sk[i];
+    const int d = (int)((key >> shift) & 0xff);
+    const int64_t pos = gbase[d] + (i - lstart[d]);
+    kout[pos] = key;
+    if (vout) vout[pos] = sv[i];
   }
 }
 

@@ -113,21 +113,22 @@ __device__ __forceinline__ uint64_t spread_bits(uint64_t v) {
   return v;
 }
 
-// Integer coordinate k = min(floor((x - corner) / (2H) * 2^21), 2^21 - 1) per
-// axis, interleaved x-major into a 63-bit key; idx (the identity permutation
-// the sort starts from) is written when it is not null.
+// Integer coordinate k = min(floor((x - corner) * S), 2^21 - 1) per axis,
+// S = 2^21 / (2H) rounded once, interleaved x-major into a 63-bit key; idx
+// (the identity permutation the sort starts from) is written when it is not
+// null.  Each operation is an explicitly rounded double operation, as in the
+// oracle, so the keys agree bit for bit.
 template <class R>
 __global__ void k_keys(const R* __restrict__ xyzq, int64_t n, const double* __restrict__ root,
                        uint64_t* __restrict__ keys, int32_t* __restrict__ idx) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= n) return;
-  const double side = __dadd_rn(root[9], root[9]);
+  const double S = __ddiv_rn(2097152.0, __dadd_rn(root[9], root[9]));
   uint64_t key = 0;
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
     double d = __dsub_rn((double)xyzq[4 * i + a], root[10 + a]);
-    double s = __dmul_rn(__ddiv_rn(d, side), 2097152.0);
-    double f = floor(s);
+    double f = floor(__dmul_rn(d, S));
     int64_t k = (int64_t)f;
     k = k < 0 ? 0 : (k > 2097151 ? 2097151 : k);
     key |= spread_bits((uint64_t)k) << (2 - a);

@@ -185,7 +185,8 @@ def _brute_tree(x, ncrit):
     H = max(float(v) for v in (hi - lo) * 0.5) * (1.0 + 2.0 ** -20)
     H = 0.5 if H == 0.0 else H
     corner = ctr - H
-    k = np.floor(((x[:, :3] - corner) / (2.0 * H)) * 2.0 ** 21)
+    per_len = 2.0 ** 21 / (2.0 * H)  # voxels per unit length, rounded once
+    k = np.floor((x[:, :3] - corner) * per_len)
     k = np.clip(k, 0, 2 ** 21 - 1).astype(np.int64)
     keys = []
     for kx, ky, kz in k.tolist():
