@@ -327,6 +327,238 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
   }
 }
 
+// Single-tile engine that folds after every entry (Kp <= 256, so that two
+// accumulators of tmem_cols columns fit the 512 TMEM columns).  The MMAs of
+// one entry accumulate in A (columns 0 ..), restarting at the entry's first
+// k-step; when they are done (bar_acc), four fold warps add A into B
+// (columns tmem_cols ..) with FP32 adds in registers and tell the MMA thread
+// that A is free (bar_free), and the last fold's B is the chunk's partial.
+// Each FP32 accumulation inside the tensor core then spans one entry's
+// k-steps instead of the chunk's, which is what sets the single-precision
+// error floor at high orders; the cost is that an entry's MMAs wait for the
+// fold of the one before.  Warps 0-3 produce as in k_m2l_tc, warp 4 issues
+// the MMAs, warps 5-8 fold and write the partial.
+constexpr int kThreadsFold = 288;
+
+__device__ __forceinline__ void mbar_arrive1(uint32_t bar) {
+  asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.shared::cta.b64 st, [%0];\n}\n" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]), "=r"(v[8]),
+        "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+      : "r"(taddr)
+      : "memory");
+}
+
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&v)[16]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};\n" ::"r"(
+          taddr),
+      "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]), "r"(v[8]), "r"(v[9]),
+      "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15])
+      : "memory");
+}
+
+__global__ void __launch_bounds__(kThreadsFold, 1)
+    k_m2l_tc_fold(const __grid_constant__ CUtensorMap tm_ops_hi, const __grid_constant__ CUtensorMap tm_ops_lo,
+                  const int4* __restrict__ chunks, const int32_t* __restrict__ entry_class,
+                  const int32_t* __restrict__ entry_src, const float* __restrict__ Mhi, const float* __restrict__ Mlo,
+                  int Kp, int nstage, int tmem_cols, float* __restrict__ part, int* __restrict__ err) {
+  extern __shared__ unsigned char smem_raw[];
+  __shared__ uint64_t bar_full[kMaxStages], bar_opfull[kMaxStages], bar_empty[kMaxStages], bar_done, bar_acc,
+      bar_free;
+  __shared__ uint32_t tmem_base;
+  __shared__ volatile int abort_flag;
+
+  const uint32_t raw = smem_u32(smem_raw);
+  const uint32_t base = (raw + 1023u) & ~1023u;
+  const int stageB = Kp * kRowB;
+  const int stage_bytes = 2 * kStageA + 2 * stageB;
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int4 ch = chunks[blockIdx.x];
+  const int e0 = ch.y, e1 = ch.z;
+  const int nkb = (Kp + kKB - 1) / kKB;
+  const int ne = e1 - e0;
+  const int nit = ne * nkb;
+
+  if (tid == 0) {
+    abort_flag = 0;
+    for (int s = 0; s < nstage; ++s) {
+      mbar_init(smem_u32(&bar_full[s]), kProducers);
+      mbar_init(smem_u32(&bar_opfull[s]), 1);
+      mbar_init(smem_u32(&bar_empty[s]), 1);
+    }
+    mbar_init(smem_u32(&bar_done), 1);
+    mbar_init(smem_u32(&bar_acc), 1);
+    mbar_init(smem_u32(&bar_free), 4);  // one arrival per fold warp
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  if (warp == 4) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(&tmem_base)),
+                 "r"(2 * tmem_cols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+  const uint32_t tmem = tmem_base;
+
+  if (warp < 4) {
+    // ---------------------------------------------------------- producers
+    // (as in k_m2l_tc)
+    const int r = tid;
+    const int c8 = r & 7, r8 = r >> 3;
+    const uint32_t b_bytes = 2u * (uint32_t)stageB;
+    int src[8], nsrc[8];
+    int cls = 0, ncls = 0;
+    int tma_issued = 0;
+    auto fetch = [&](int e, int (&to)[8], int& tc) {
+#pragma unroll
+      for (int i = 0; i < 8; ++i) to[i] = __ldg(entry_src + (int64_t)e * kTile + r8 + 16 * i);
+      tc = __ldg(entry_class + e);
+    };
+    if (nit > 0) fetch(e0, nsrc, ncls);
+    for (int it = 0; it < nit; ++it) {
+      const int e = e0 + it / nkb, kb = it % nkb;
+      const int s = it % nstage, round = it / nstage;
+      if (kb == 0) {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) src[i] = nsrc[i];
+        cls = ncls;
+        if (e + 1 < e1) fetch(e + 1, nsrc, ncls);
+      }
+      if (round > 0 && !mbar_wait(smem_u32(&bar_empty[s]), (round - 1) & 1, &abort_flag)) break;
+      const uint32_t sb = base + s * stage_bytes;
+      const int k0 = kb * kKB;
+      if (r == 0) {
+        const uint32_t ob = smem_u32(&bar_opfull[s]);
+        mbar_arrive_expect_tx(ob, b_bytes);
+        tma_load_2d(sb + 2 * kStageA, &tm_ops_hi, k0, cls * Kp, ob);
+        tma_load_2d(sb + 2 * kStageA + stageB, &tm_ops_lo, k0, cls * Kp, ob);
+        tma_issued = it + 1;
+      }
+      const int nch = min(kKB, Kp - k0) / 4;
+      if (c8 < nch) {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          const int row = r8 + 16 * i;
+          const int64_t off = (int64_t)(src[i] >= 0 ? src[i] : 0) * Kp + k0 + 4 * c8;
+          const int bytes = src[i] >= 0 ? 16 : 0;
+          cp_async16(sb + swz(row, c8), Mhi + off, bytes);
+          cp_async16(sb + kStageA + swz(row, c8), Mlo + off, bytes);
+        }
+      }
+      asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];\n" ::"r"(smem_u32(&bar_full[s]))
+                   : "memory");
+    }
+    cp_async_wait<0>();
+    if (r == 0)
+      for (int i = max(0, tma_issued - nstage); i < tma_issued; ++i)
+        if (!mbar_drain(smem_u32(&bar_opfull[i % nstage]), (i / nstage) & 1)) atomicOr(err, kErrDrain);
+  } else if (warp == 4) {
+    // ---------------------------------------------------------------- MMA
+    if (lane == 0) {
+      const uint32_t idesc = idesc_tf32(Kp);
+      bool ok = true;
+      for (int it = 0; it < nit && ok; ++it) {
+        const int j = it / nkb, kb = it % nkb;
+        const int s = it % nstage, round = it / nstage;
+        if (kb == 0 && j > 0) {
+          // A is free once the fold of entry j - 1 has read it
+          if (!mbar_wait(smem_u32(&bar_free), (j - 1) & 1, &abort_flag)) {
+            ok = false;
+            break;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+        }
+        if (!mbar_wait(smem_u32(&bar_full[s]), round & 1, &abort_flag) ||
+            !mbar_wait(smem_u32(&bar_opfull[s]), round & 1, &abort_flag)) {
+          ok = false;
+          break;
+        }
+        fence_async_smem();
+        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+        const uint32_t sb = base + s * stage_bytes;
+        const int nks = min(kKB, Kp - kb * kKB) / 8;
+        for (int ks = 0; ks < nks; ++ks) {
+          const uint32_t off = ks * 32;
+          const uint64_t ah = smem_desc(sb + off), al = smem_desc(sb + kStageA + off);
+          const uint64_t bh = smem_desc(sb + 2 * kStageA + off), bl = smem_desc(sb + 2 * kStageA + stageB + off);
+          const uint32_t first = (kb == 0 && ks == 0) ? 0u : 1u;  // A restarts with each entry
+          mma_tf32(tmem, ah, bh, idesc, first);
+          mma_tf32(tmem, al, bh, idesc, 1u);
+          mma_tf32(tmem, ah, bl, idesc, 1u);
+        }
+        mma_commit(smem_u32(&bar_empty[s]));
+        if (kb == nkb - 1) mma_commit(smem_u32(&bar_acc));  // entry j's sum is in A
+      }
+      if (nit > 0) mma_commit(smem_u32(&bar_done));
+      if (!ok) abort_flag = 1;
+    }
+  } else {
+    // --------------------------------------------------- fold and partial
+    // warp w reaches the TMEM lanes 32 (w % 4) ..; its thread owns tile row
+    // 32 (w % 4) + lane
+    const int q = warp & 3;
+    const uint32_t lanes = (uint32_t)(q * 32) << 16;
+    const uint32_t ta = tmem + lanes, tb = tmem + lanes + (uint32_t)tmem_cols;
+    bool ok = true;
+    for (int j = 0; j < ne; ++j) {
+      if (!mbar_wait(smem_u32(&bar_acc), j & 1, &abort_flag)) {
+        ok = false;
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+      for (int c0 = 0; c0 < Kp; c0 += 16) {
+        uint32_t a[16], b[16];
+        tmem_ld16(ta + (uint32_t)c0, a);
+        if (j > 0) tmem_ld16(tb + (uint32_t)c0, b);
+        asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+        if (j > 0)
+#pragma unroll
+          for (int k = 0; k < 16; ++k) a[k] = __float_as_uint(__uint_as_float(a[k]) + __uint_as_float(b[k]));
+        tmem_st16(tb + (uint32_t)c0, a);
+      }
+      asm volatile("tcgen05.wait::st.sync.aligned;\n" ::: "memory");
+      asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+      __syncwarp();
+      if (lane == 0) mbar_arrive1(smem_u32(&bar_free));
+    }
+    if (ok) {
+      // partial slot ch.w, column-major ([Kp][128])
+      float* pcol = part + (int64_t)ch.w * kTile * Kp + q * 32 + lane;
+      for (int c0 = 0; c0 < Kp; c0 += 16) {
+        uint32_t v[16];
+        if (ne > 0) {
+          tmem_ld16(tb + (uint32_t)c0, v);
+          asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+        } else {
+          for (int k = 0; k < 16; ++k) v[k] = 0u;
+        }
+#pragma unroll
+        for (int k = 0; k < 16; ++k) __stcs(pcol + (int64_t)(c0 + k) * kTile, __uint_as_float(v[k]));
+      }
+    }
+  }
+  // drain: the last commits must land before the TMEM is released
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  if (abort_flag && tid == 0) atomicOr(err, kErrWait);
+  if (warp == 4) {
+    if (abort_flag && nit > 0) {
+      if (!mbar_drain(smem_u32(&bar_done), 0) && lane == 0) atomicOr(err, kErrDrain);
+    }
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(2 * tmem_cols)
+                 : "memory");
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Quad engine (Kp <= 128): one CTA takes four tiles of the same octant
 // together.  The tiles' class lists are merged into quad entries (class, the
@@ -342,6 +574,16 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
 constexpr int kQuad = 4;
 constexpr int kMaxAStages = 6;
 constexpr int kQuadMaxKp = 128;  // four 128-column TMEM accumulators
+
+// The single-tile engine folds after every entry (k_m2l_tc_fold) unless
+// GBFMM_M2L_FOLD=0 (a knob for measuring what the fold costs and gains).
+bool m2l_fold_enabled() {
+  static const bool on = [] {
+    const char* env = getenv("GBFMM_M2L_FOLD");
+    return !(env && atoi(env) == 0);
+  }();
+  return on;
+}
 
 // GBFMM_M2L_SINGLE=1 selects the single-tile engine at every Kp (tuning and
 // cross-checking knob)
@@ -724,14 +966,22 @@ void launch_m2l_tcgen05(fmm_tree* t, cudaStream_t s) {
   const size_t smem = (size_t)nstage * (2 * kStageA + 2 * Kp * kRowB) + 1024;
   // the dynamic size this launch needs (static + dynamic must stay within the
   // 227 KB per-block limit)
-  GB_CK(cudaFuncSetAttribute(k_m2l_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int cols = 32;
   while (cols < Kp) cols <<= 1;
   const int64_t n = (int64_t)t->ncell * Kp;
-  k_m2l_tc<<<t->nchunk, kThreadsTC, smem, s>>>(t->m2l_ops_map[0], t->m2l_ops_map[1], t->m2l_chunks, t->entry_class,
-                                               t->entry_src, t->M_lo + n, t->M_lo, Kp, nstage, cols, t->m2l_part,
-                                               t->dev_err);
-  GB_LAUNCH("k_m2l_tc");
+  if (2 * cols <= 512 && m2l_fold_enabled()) {
+    GB_CK(cudaFuncSetAttribute(k_m2l_tc_fold, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_m2l_tc_fold<<<t->nchunk, kThreadsFold, smem, s>>>(t->m2l_ops_map[0], t->m2l_ops_map[1], t->m2l_chunks,
+                                                        t->entry_class, t->entry_src, t->M_lo + n, t->M_lo, Kp,
+                                                        nstage, cols, t->m2l_part, t->dev_err);
+    GB_LAUNCH("k_m2l_tc_fold");
+  } else {
+    GB_CK(cudaFuncSetAttribute(k_m2l_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_m2l_tc<<<t->nchunk, kThreadsTC, smem, s>>>(t->m2l_ops_map[0], t->m2l_ops_map[1], t->m2l_chunks,
+                                                 t->entry_class, t->entry_src, t->M_lo + n, t->M_lo, Kp, nstage, cols,
+                                                 t->m2l_part, t->dev_err);
+    GB_LAUNCH("k_m2l_tc");
+  }
   k_m2l_reduce<<<t->ntile, 256, 0, s>>>(t->tile_tgt, t->tile_cptr, t->m2l_part, t->K, Kp, (float*)t->L);
   GB_LAUNCH("k_m2l_reduce");
 }
