@@ -434,7 +434,7 @@ def run_sweep(args):
         return None
 
     cmp = {}
-    for e in (1e-2, 1e-3, 1e-4, 1e-5):
+    for e in (1e-2, 1e-3, 1e-4, 1e-5, 1e-6):
         a, b = at_error("f32", e), at_error("f64", e)
         if a is not None and b is not None:
             cmp[f"{e:.0e}"] = {"f32_ms": round(a, 2), "f64_ms": round(b, 2), "f64_over_f32": round(b / a, 2)}
