@@ -146,8 +146,7 @@ __device__ __forceinline__ uint64_t pair_key(int tgt, int src) {
   return ((uint64_t)(uint32_t)tgt << 32) | (uint32_t)src;
 }
 
-// M2L pair {A, B}: marks both cells as M2L cells (read first: a cell has
-// many M2L pairs) and returns the largest |offset| component in units of the
+// M2L pair {A, B}: marks both cells as M2L cells and returns the largest |offset| component in units of the
 // smaller cell's half side (the class offsets of the plan).  w[0] and w[1]
 // receive the packed class offsets of the entries (target B, source A) and
 // (target A, source B): bits 24..29 the level difference (source minus
@@ -167,8 +166,11 @@ __device__ __forceinline__ unsigned mark_m2l(const CellView& c, int A, int B, in
     w[0] |= ((uint32_t)o & 0xffu) << (16 - 8 * d);
     w[1] |= ((uint32_t)(-o) & 0xffu) << (16 - 8 * d);
   }
-  if (!m2l_has[A]) m2l_has[A] = 1;
-  if (!m2l_has[B]) m2l_has[B] = 1;
+  // per target, which level differences (source minus target: below, equal,
+  // above) its M2L sources have, as bits 0, 1, 2 (read first)
+  const int bitA = 1 << (lb < la ? 0 : (lb == la ? 1 : 2)), bitB = 1 << (la < lb ? 0 : (la == lb ? 1 : 2));
+  if (!(m2l_has[A] & bitA)) atomicOr(m2l_has + A, bitA);
+  if (!(m2l_has[B] & bitB)) atomicOr(m2l_has + B, bitB);
   return dm;
 }
 
