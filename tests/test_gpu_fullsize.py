@@ -75,3 +75,28 @@ def test_cube16m_sampled_parity(fmm, orc):
         tp, tf = (TOL64_PHI, TOL64_F) if f64 else (TOL_PHI, TOL_F)
         bp, bf = (1e-9, 1e-8) if f64 else (1e-4, 1e-3)
         assert_match(pg, po, fg, -go, tp, tf, bp, bf)
+
+
+def test_single_tile_fold_accuracy(fmm):
+    """At p = 12 (Kp = 144) the M2L runs on the single-tile engine, which adds
+    each source entry's TMEM sum into a second accumulator instead of
+    accumulating a whole chunk of entries in the tensor core.  The
+    single-precision potential then stays within 1.5e-6 (relative L2) of the
+    FP64 direct sum on 262,144 cube bodies (6.7e-7 measured; 2.5e-6 with
+    16 entries accumulated in TMEM), and the force within 2e-6."""
+    from tests.gpu_helpers import rel
+    n = 262144
+    x = torch.from_numpy(W.cube(n, 2)).cuda()
+    idx = torch.from_numpy(W.sample_targets(n, 4096, seed=7).astype(np.int64)).cuda()
+    T = fmm.Tree(x, 12, 0.4, 64)
+    assert T.stats()["m2l_engine"] == 1
+    pot, force = T.evaluate()
+    pd, fd = fmm.direct_f64(x, idx)
+    torch.cuda.synchronize()
+    ii = idx.cpu().numpy()
+    pg = pot.cpu().numpy()[ii].astype(np.float64)
+    fg = force.cpu().numpy()[ii].astype(np.float64)
+    assert rel(pg, pd.cpu().numpy()) < 1.5e-6
+    assert rel(fg, fd.cpu().numpy()) < 2e-6
+    T.check()
+    T.close()
