@@ -377,6 +377,7 @@ __global__ void __launch_bounds__(kThreads) k_m2l_fit(const int32_t* __restrict_
         for (int q = 0; q < kLB; ++q) an[q] = {(R)0, (R)0};
 #pragma unroll
         for (int q = 0; q + 1 < kLB; ++q) win[q] = trow[-n + q];
+#pragma unroll 4
         for (int m = -n; m <= n; ++m) {
           win[kLB - 1] = trow[m + kLB - 1];
           const cx<R> a = mrow[m];
