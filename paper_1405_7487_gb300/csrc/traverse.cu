@@ -25,6 +25,7 @@
 // same units, and the radius is measured from there.
 #include <algorithm>
 #include <climits>
+#include <cstdlib>
 
 #include "common.cuh"
 #include "grid.cuh"
@@ -761,7 +762,11 @@ void build_lists(fmm_tree* t) {
   unsigned long long* d_pairs = reinterpret_cast<unsigned long long*>(t->d_tail + 1);
   int64_t* eptr = alloc_n<int64_t>(a, t->nleaf + 1);
   GB_CK(cudaMemsetAsync(eptr, 0, sizeof(int64_t) * (t->nleaf + 1), s));
-  const int64_t budget = std::max<int64_t>(1ll << 23, 64 * t->N);
+  int64_t budget = std::max<int64_t>(1ll << 23, 64 * t->N);
+  // GBFMM_TRAVERSE_BUDGET (entries) overrides it: a small value makes the
+  // single launch stop early and the per-level launches take over (the test
+  // of that path)
+  if (const char* env = getenv("GBFMM_TRAVERSE_BUDGET")) budget = std::max<int64_t>(16, atoll(env));
   int64_t cap_m = budget / 2, cap_p = budget / 10;
   const int64_t capF = budget / 5;
   // the lists are written in place and kept at this capacity (no copy)

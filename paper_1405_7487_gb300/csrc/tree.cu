@@ -4,6 +4,7 @@
 // N_crit is the maximum number of bodies per leaf).
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <mutex>
 #include <string>
 #include <utility>
@@ -403,6 +404,8 @@ void build_tree_impl(fmm_tree* t, const R* xyzq) {
   }
   if (bound > 0x7fffffff) bound = 0x7fffffff;
   int64_t cap = std::min<int64_t>(bound, 8 * ((N + t->ncrit - 1) / t->ncrit) + 4096);
+  // GBFMM_TREE_CELLS overrides the first capacity (the test of the retry)
+  if (const char* env = getenv("GBFMM_TREE_CELLS")) cap = std::min<int64_t>(bound, std::max<int64_t>(1, atoll(env)));
   int* partial = alloc_n<int>(a, G);
   LevelState* d_st = alloc_n<LevelState>(a, 1);
   int* bnd = nullptr;  // octant starts of one level's cells (at most cap cells)

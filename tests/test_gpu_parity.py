@@ -493,3 +493,41 @@ def test_m2l_engines_agree(fmm, name):
     assert rel(La, Lb) < 3e-5
     assert rel(pa, pb) < 1e-5 and rel(fa, fb) < 5e-5
     assert A.stats()["device_errors"] == 0
+
+
+@pytest.mark.parametrize("flags_name", ["default", "fitted"])
+def test_fallback_build_paths_identical(fmm, flags_name):
+    """The tree build and the traversal each run as one cooperative launch
+    into buffers sized ahead; when a tree outgrows them, the tree build
+    repeats at its bound and the traversal hands over to per-level launches.
+    Forcing both (tiny first buffers through GBFMM_TREE_CELLS and
+    GBFMM_TRAVERSE_BUDGET) must give the same cells, lists and outputs bit
+    for bit, with more host synchronisations."""
+    import os
+    flags = 0 if flags_name == "default" else fmm.FMM_FLAG_FITTED_CENTRES
+    x_h = W.plummer(60000, 61)
+    x = torch.from_numpy(x_h).cuda()
+
+    def run():
+        T = fmm.Tree(x, 8, 0.5, 32, flags)
+        pot, force = T.evaluate()
+        torch.cuda.synchronize()
+        out = (T.cells(), T.lists(), pot.cpu().numpy(), force.cpu().numpy(), T.stats())
+        T.close()
+        return out
+
+    c0, l0, p0, f0, s0 = run()
+    os.environ["GBFMM_TREE_CELLS"] = "64"
+    os.environ["GBFMM_TRAVERSE_BUDGET"] = "1000"
+    try:
+        c1, l1, p1, f1, s1 = run()
+    finally:
+        del os.environ["GBFMM_TREE_CELLS"]
+        del os.environ["GBFMM_TRAVERSE_BUDGET"]
+    for k in c0:
+        assert np.array_equal(c0[k], c1[k]), k
+    for k in l0:
+        assert np.array_equal(l0[k], l1[k]), k
+    assert np.array_equal(p0, p1) and np.array_equal(f0, f1)
+    assert s1["build_host_syncs"] > s0["build_host_syncs"]
+    assert s0["device_errors"] == 0 and s1["device_errors"] == 0
