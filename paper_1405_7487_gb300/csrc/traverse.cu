@@ -38,7 +38,8 @@ inline unsigned blocks(int64_t n) { return (unsigned)((n + kThreads - 1) / kThre
 
 struct CellView {
   const int32_t *level, *ix, *iy, *iz, *cbeg, *nch;
-  const long long* r2;  // particle-fitted radius (tight MAC or fitted centres): its square per cell, else null
+  const double* rr;     // particle-fitted radius (tight MAC or fitted centres): the correctly rounded
+                        // square root of its exact integer square, per cell, else null
   const int32_t* fc;    // fitted centres: 3 integer coordinates per cell (units H / 2^21), else null
 };
 
@@ -53,8 +54,8 @@ __device__ __forceinline__ bool mac(const CellView& c, int A, int B, double thet
                   fz = (int64_t)c.fc[3 * A + 2] - c.fc[3 * B + 2];
     D2 = fx * fx + fy * fy + fz * fz;
   }
-  if (c.r2) {
-    const double sr = __dadd_rn(__dsqrt_rn((double)c.r2[A]), __dsqrt_rn((double)c.r2[B]));
+  if (c.rr) {
+    const double sr = __dadd_rn(c.rr[A], c.rr[B]);
     return __dmul_rn(theta2, (double)D2) > __dmul_rn(sr, sr);
   }
   const int64_t rs = (1ll << (kMaxLevel - la)) + (1ll << (kMaxLevel - lb));
@@ -721,6 +722,11 @@ void sort_pairs_copy(Arena& a, const int32_t* tgt, const int32_t* src, int64_t n
   a.release(k);
 }
 
+__global__ void k_cell_root(const long long* __restrict__ r2, int n, double* __restrict__ rr) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) rr[i] = __dsqrt_rn((double)r2[i]);
+}
+
 void build_lists(fmm_tree* t) {
   Arena& a = t->arena;
   cudaStream_t s = t->stream;
@@ -738,7 +744,15 @@ void build_lists(fmm_tree* t) {
                                                 t->c.bend, r2);
     GB_LAUNCH("k_cell_r2");
   }
-  CellView cv{t->c.level, t->c.ix, t->c.iy, t->c.iz, t->c.cbeg, t->c.nch, r2, t->fit_c};
+  // the radii's square roots once per cell (the same doubles the per-pair
+  // test took, without two FP64 square roots per candidate pair)
+  double* rr = nullptr;
+  if (r2) {
+    rr = alloc_n<double>(a, t->ncell);
+    k_cell_root<<<blocks(t->ncell), kThreads, 0, s>>>(r2, t->ncell, rr);
+    GB_LAUNCH("k_cell_root");
+  }
+  CellView cv{t->c.level, t->c.ix, t->c.iy, t->c.iz, t->c.cbeg, t->c.nch, rr, t->fit_c};
   const double theta2 = t->theta * t->theta;
   const int circ = (t->flags & FMM_FLAG_CIRCUMSCRIBED) ? 1 : 0;
 
@@ -762,7 +776,11 @@ void build_lists(fmm_tree* t) {
   unsigned long long* d_pairs = reinterpret_cast<unsigned long long*>(t->d_tail + 1);
   int64_t* eptr = alloc_n<int64_t>(a, t->nleaf + 1);
   GB_CK(cudaMemsetAsync(eptr, 0, sizeof(int64_t) * (t->nleaf + 1), s));
-  int64_t budget = std::max<int64_t>(1ll << 23, 64 * t->N);
+  // The MACs with true bounds (circumscribed, particle-fitted) accept fewer
+  // pairs at the same theta: their lists run 3 to 6 times longer (92.6 M M2L
+  // entries for 1 M Plummer bodies with fitted centres, against 25.7 M).
+  const bool long_lists = (t->flags & (FMM_FLAG_CIRCUMSCRIBED | FMM_FLAG_TIGHT_MAC | FMM_FLAG_FITTED_CENTRES)) != 0;
+  int64_t budget = std::max<int64_t>(1ll << 23, (long_lists ? 256 : 64) * t->N);
   // GBFMM_TRAVERSE_BUDGET (entries) overrides it: a small value makes the
   // single launch stop early and the per-level launches take over (the test
   // of that path)
@@ -888,6 +906,7 @@ void build_lists(fmm_tree* t) {
     a.release(d_st);
   }
   if (r2) a.release(r2);
+  if (rr) a.release(rr);
 
   // The pairs stay in traversal order (deterministic: every offset comes from
   // an exclusive scan); only the inspection call sorts a copy by (target,
